@@ -1,0 +1,171 @@
+/*
+ * bcpp -- exact betweenness centrality on one GB300 (sm_103a): plain Brandes and Brandes++.
+ *
+ * C ABI of libbcpp.so.  The computation follows "A Divide-and-Conquer Algorithm for
+ * Betweenness Centrality" (Erdos, Ishakian, Bestavros, Terzi): target-set betweenness
+ * C^S(v) = sum over ordered pairs s != t in S of sigma(s,t|v)/sigma(s,t) (Sec. 3, Eq. 5),
+ * computed either by Brandes' recursion on G (Eq. 6-7) or by Brandes++ (Sec. 4, Alg. 1):
+ * Build_SK (Alg. 2, Dijkstra_SK of Eq. 10), Brandes_SK on the skeleton (Eq. 11-12) and the
+ * Centrality step for non-frontier nodes (Eq. 13).
+ *
+ * Conventions shared by every call
+ *   - Graphs are CSR: row_ptr[n+1] (int64), col[num_arcs] (int32).  Each row is strictly
+ *     increasing (sorted, no repeated arc), no self-loops.  An undirected graph stores every
+ *     edge as two arcs with equal weights.  w == NULL means unit weights; otherwise integer
+ *     weights w >= 1 with max(w) * (n - 1) < 2^31 (weights are the edge lengths of Sec. 3;
+ *     zero weights are rejected because they break the strict distance order the path
+ *     counts rely on).
+ *   - Unless opts->host_buffers is set, every pointer argument is a DEVICE pointer.  With
+ *     host_buffers = 1 every array argument is a HOST pointer instead: the call copies the
+ *     inputs to the device and the result back (end-to-end use).
+ *   - The caller owns all argument buffers.  The context owns its workspace, which is kept
+ *     between calls (grown on demand) and released by bcpp_destroy.
+ *   - Work is queued on the context's stream; every call returns only after its results are
+ *     written (it synchronizes the stream to read the status flags).
+ *   - Distances are int32 (INT32_MAX = unreachable), path counts sigma are exact uint64;
+ *     when a count exceeds 2^64 the results are still written and the call returns
+ *     BCPP_EOVERFLOW_SIGMA (also reported in bcpp_stats.sigma_overflow).
+ *   - Betweenness is FP64.  In BCPP_FP64 mode the per-source dependencies delta are FP64; in
+ *     BCPP_FP32_DELTA mode they are FP32 (sigma stays exact) and only the sum over sources is
+ *     FP64, compensated (Neumaier).
+ *   - Undirected results are halved by default (each unordered pair once); directed results
+ *     are never halved.  The paper assumes 2 <= |S| <= n (Sec. 3); |S| < 2 gives all zeros.
+ */
+#ifndef BCPP_H
+#define BCPP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define BCPP_OK 0
+#define BCPP_EINVAL 1            /* malformed graph, targets, partition or options */
+#define BCPP_ENOMEM 2            /* device or host allocation failed */
+#define BCPP_ECUDA 3             /* a CUDA runtime call failed */
+#define BCPP_ETIMEOUT 4          /* reserved: a bounded device wait expired */
+#define BCPP_EOVERFLOW_SIGMA 5   /* results written, but some path count exceeded 2^64 */
+#define BCPP_ECAPACITY 6         /* a per-batch device list outgrew its bound (see bcpp_strerror) */
+
+/* precision modes */
+#define BCPP_FP64 0
+#define BCPP_FP32_DELTA 1
+
+typedef struct bcpp_ctx bcpp_ctx;
+
+typedef struct {
+    int32_t n;                 /* nodes */
+    int64_t num_arcs;          /* arcs (2 per undirected edge) */
+    const int64_t *row_ptr;    /* [n+1] */
+    const int32_t *col;        /* [num_arcs] */
+    const uint32_t *w;         /* [num_arcs] or NULL (unit weights) */
+    int32_t directed;          /* 0: undirected (symmetric arcs), 1: directed */
+} bcpp_graph;
+
+typedef struct {
+    int32_t precision;         /* BCPP_FP64 (default) or BCPP_FP32_DELTA */
+    int32_t halve_undirected;  /* 1 (default): halve undirected results; 0: ordered-pair sums */
+    int32_t batch;             /* source lanes per batch: 0 = default (32, the only value today) */
+    int32_t ctas_per_sm;       /* resident source batches per SM: 0 = auto */
+    int32_t validate;          /* reserved: the CSR, S and the partition are always checked */
+    int32_t host_buffers;      /* 1: array arguments are host pointers (copied in and out) */
+    int32_t order_sources;     /* 1 (default): batch targets of the same part together (Brandes++) */
+    int32_t reserved;
+} bcpp_opts;
+
+typedef struct {
+    uint32_t sigma_overflow;   /* 1 if some sigma exceeded 2^64 */
+    int32_t skel_nodes;        /* N = |V_sk| (Brandes++), Table 2 */
+    int64_t skel_edges;        /* M = |E_sk| (edges; arcs for directed graphs), Table 2 */
+    int32_t k;                 /* non-empty parts of P' (Brandes++) */
+    int32_t lcs;               /* largest part of P' */
+    int64_t table_entries;     /* sum_i |F_i| |V_i| stored by Dijkstra_SK */
+    float ms_build_sk;         /* Build_SK (frontiers, Dijkstra_SK, skeleton assembly) */
+    float ms_brandes_sk;       /* Brandes_SK or plain Brandes passes */
+    float ms_centrality;       /* Centrality step */
+    float ms_total;            /* whole call, device time */
+    int64_t kernel_launches;   /* kernels this call launched */
+} bcpp_stats;
+
+/* Fill opts with the defaults listed above. */
+void bcpp_default_opts(bcpp_opts *opts);
+
+/* Message for a status code (static string). */
+const char *bcpp_strerror(int status);
+
+/* Create a context bound to a CUDA stream (NULL = legacy default stream) on the current
+ * device.  Returns BCPP_OK and *ctx, or an error and *ctx = NULL. */
+int bcpp_create(bcpp_ctx **ctx, void *cuda_stream);
+
+/* Free the context and its workspace.  NULL is ignored. */
+void bcpp_destroy(bcpp_ctx *ctx);
+
+/* Workspace bytes currently held by the context (device). */
+int64_t bcpp_workspace_bytes(const bcpp_ctx *ctx);
+
+/* CSR build and validation (the input graph G(V,E,W) of Sec. 3).  From m edges
+ * (eu[i], ev[i], weight ew[i] or unit if ew == NULL) build the CSR: row_ptr_out[n+1],
+ * col_out and w_out (w_out may be NULL when ew is NULL) of capacity 2m (undirected: every
+ * edge becomes two arcs) or m (directed); *num_arcs_out (host) receives the arc count.
+ * Rows come out sorted.  BCPP_EINVAL for an endpoint outside [0,n), a self-loop, a repeated
+ * edge (for undirected input also (u,v) given together with (v,u)), or a zero weight. */
+int bcpp_csr_build(bcpp_ctx *ctx, int32_t n, int64_t m, const int32_t *eu, const int32_t *ev,
+                   const uint32_t *ew, int32_t directed, int64_t *row_ptr_out, int32_t *col_out,
+                   uint32_t *w_out, int64_t *num_arcs_out);
+
+/* Check a CSR against the conventions above (sorted strictly increasing rows, heads in
+ * range, no self-loops, weights >= 1 and small enough, symmetric with equal weights when
+ * undirected).  BCPP_OK or BCPP_EINVAL. */
+int bcpp_csr_validate(bcpp_ctx *ctx, const bcpp_graph *g);
+
+/* Plain Brandes with target set S (Sec. 3, Eq. 5-7): bc_out[n] (FP64) receives C^S(v).
+ * S[nS] lists distinct targets in [0,n); nS == 0 (S may be NULL) means S = V.  Every target
+ * is a source; the dependency recursion credits I_{v in S} (Eq. 7).  Unit weights run a
+ * level-synchronous breadth-first search, integer weights an exact bucket order (Dial's
+ * delta-stepping with bucket width 1).  stats may be NULL. */
+int bcpp_brandes(bcpp_ctx *ctx, const bcpp_graph *g, const int32_t *S, int32_t nS,
+                 const bcpp_opts *opts, double *bc_out, bcpp_stats *stats);
+
+/* Brandes++ (Sec. 4, Alg. 1) for target set S with node partition part[n] (values in
+ * [0,k)): targets become singleton parts (P'), Build_SK finds the frontiers and runs
+ * Dijkstra_SK in every part (Alg. 2, Eq. 10), Brandes_SK runs from every target on the
+ * weighted skeleton with multiplicities (Eq. 11-12), and the Centrality step gives the
+ * dependencies of non-frontier nodes (Eq. 13, with the tight-frontier tests stated in the
+ * text of Sec. 4).  Exact: bc_out equals bcpp_brandes on the same S for every partition.
+ * nS == 0 means S = V.  stats (may be NULL) receives N, M, k, LCS of Table 2. */
+int bcpp_brandes_pp(bcpp_ctx *ctx, const bcpp_graph *g, const int32_t *S, int32_t nS,
+                    const int32_t *part, int32_t k, const bcpp_opts *opts, double *bc_out,
+                    bcpp_stats *stats);
+
+/* Full betweenness (S = V of each graph) of num_graphs independent undirected graphs in one
+ * launch.  `arena` is their disjoint union as one CSR (global node ids); graph g owns the
+ * nodes [graph_node_ptr[g], graph_node_ptr[g+1]) (int64, device; a host copy is taken), and
+ * no arc may leave its graph (BCPP_EINVAL otherwise).  bc_out[arena->n] receives every
+ * graph's betweenness in arena order.  With host_buffers, graph_node_ptr is a host array. */
+int bcpp_brandes_batched(bcpp_ctx *ctx, int32_t num_graphs, const int64_t *graph_node_ptr,
+                         const bcpp_graph *arena, const bcpp_opts *opts, double *bc_out,
+                         bcpp_stats *stats);
+
+/* Distances and path counts from nsrc sources (Eq. 2), for bit-exact checks:
+ * dist_out[nsrc * n] (row i = source src[i]) and sigma_out[nsrc * n]. */
+int bcpp_sssp(bcpp_ctx *ctx, const bcpp_graph *g, const int32_t *src, int32_t nsrc,
+              int32_t *dist_out, uint64_t *sigma_out, const bcpp_opts *opts);
+
+/* The skeleton of Build_SK (Sec. 3-4) for inspection, built on P' for the targets S[nS]
+ * (nS == 0: no targets, the partition is used as given): sk_nodes_out[cap n] receives the
+ * skeleton nodes (original ids, increasing), *n_sk_out (host) their count N; the arcs with
+ * their characteristic tuples <weight, multiplicity> go to au/av/aw/amu (capacity cap_arcs,
+ * original node ids; an undirected edge appears as two arcs); *n_arcs_out (host) receives
+ * the arc count even when it exceeds cap_arcs (then BCPP_ECAPACITY and nothing is copied). */
+int bcpp_skeleton(bcpp_ctx *ctx, const bcpp_graph *g, const int32_t *S, int32_t nS,
+                  const int32_t *part, int32_t k, int32_t *sk_nodes_out, int32_t *n_sk_out,
+                  int64_t cap_arcs, int32_t *au, int32_t *av, int32_t *aw, uint64_t *amu,
+                  int64_t *n_arcs_out, const bcpp_opts *opts);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BCPP_H */

@@ -1,0 +1,1278 @@
+// C-ABI entry points of libbcpp (declared in include/bcpp.h) and the host orchestration of
+// plain Brandes, Brandes++ (Alg. 1: Build_SK -> Brandes_SK -> Centrality), batched graphs and
+// the inspection calls.  The context keeps a caching pool of device blocks so that repeated
+// calls of the same size do not allocate.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "csr.cuh"
+#include "lockstep.cuh"
+#include "prims.cuh"
+#include "skeleton.cuh"
+
+using namespace bcpp;
+
+struct PoolBlock {
+    void* p;
+    size_t bytes;
+    bool used;
+};
+
+struct bcpp_ctx {
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    std::vector<PoolBlock> pool;
+    uint32_t* flags = nullptr;       // device [FLAG_COUNT]
+    uint32_t* hflags = nullptr;      // pinned host copy
+    int64_t launches = 0;
+    cudaEvent_t ev[8] = {};
+
+    void* acquire(size_t bytes) {
+        bytes = (bytes + 255) & ~(size_t)255;
+        if (bytes == 0) bytes = 256;
+        int best = -1;
+        for (size_t i = 0; i < pool.size(); i++) {
+            const PoolBlock& b = pool[i];
+            if (!b.used && b.bytes >= bytes && b.bytes <= 2 * bytes + (64u << 20) &&
+                (best < 0 || b.bytes < pool[best].bytes))
+                best = (int)i;
+        }
+        if (best >= 0) {
+            pool[best].used = true;
+            return pool[best].p;
+        }
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            trim();
+            if (cudaMalloc(&p, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+        }
+        pool.push_back({p, bytes, true});
+        return p;
+    }
+    void release(void* p) {
+        if (!p) return;
+        for (auto& b : pool)
+            if (b.p == p) { b.used = false; return; }
+    }
+    void trim() {
+        cudaStreamSynchronize(stream);
+        std::vector<PoolBlock> keep;
+        for (auto& b : pool) {
+            if (b.used) keep.push_back(b);
+            else cudaFree(b.p);
+        }
+        pool.swap(keep);
+    }
+    int64_t held() const {
+        int64_t t = 0;
+        for (auto& b : pool) t += (int64_t)b.bytes;
+        return t;
+    }
+};
+
+namespace {
+
+// RAII device buffer from the context pool
+template <typename T>
+struct DBuf {
+    bcpp_ctx* c = nullptr;
+    T* p = nullptr;
+    int64_t n = 0;
+    DBuf() = default;
+    DBuf(bcpp_ctx* ctx, int64_t count) { alloc(ctx, count); }
+    bool alloc(bcpp_ctx* ctx, int64_t count) {
+        free();
+        c = ctx;
+        n = count;
+        p = (T*)ctx->acquire((size_t)std::max<int64_t>(count, 1) * sizeof(T));
+        return p != nullptr;
+    }
+    void free() {
+        if (c && p) c->release(p);
+        p = nullptr;
+    }
+    ~DBuf() { free(); }
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    explicit operator bool() const { return p != nullptr; }
+};
+
+struct Status {
+    int code = BCPP_OK;
+};
+
+#define CK_CUDA(x)                                   \
+    do {                                             \
+        cudaError_t e__ = (x);                       \
+        if (e__ != cudaSuccess) {                    \
+            cudaGetLastError();                      \
+            return BCPP_ECUDA;                       \
+        }                                            \
+    } while (0)
+#define CK_ALLOC(buf)                                \
+    do {                                             \
+        if (!(buf)) return BCPP_ENOMEM;              \
+    } while (0)
+#define CK_RC(x)                                     \
+    do {                                             \
+        int r__ = (x);                               \
+        if (r__ != BCPP_OK) return r__;              \
+    } while (0)
+
+int sync_flags(bcpp_ctx* c) {
+    CK_CUDA(cudaMemcpyAsync(c->hflags, c->flags, FLAG_COUNT * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    CK_CUDA(cudaStreamSynchronize(c->stream));
+    CK_CUDA(cudaGetLastError());
+    return BCPP_OK;
+}
+
+int reset_flags(bcpp_ctx* c) {
+    CK_CUDA(cudaMemsetAsync(c->flags, 0, FLAG_COUNT * sizeof(uint32_t), c->stream));
+    return BCPP_OK;
+}
+
+template <typename T>
+int to_host(bcpp_ctx* c, T* dst, const T* src, int64_t count) {
+    if (count <= 0) return BCPP_OK;
+    CK_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+    CK_CUDA(cudaStreamSynchronize(c->stream));
+    return BCPP_OK;
+}
+
+template <typename T>
+int to_dev(bcpp_ctx* c, T* dst, const T* src, int64_t count) {
+    if (count <= 0) return BCPP_OK;
+    CK_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    CK_CUDA(cudaStreamSynchronize(c->stream));
+    return BCPP_OK;
+}
+
+__global__ void iota_kernel(int32_t* p, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = (int32_t)i;
+}
+void iota(int32_t* p, int64_t n, cudaStream_t st) {
+    if (n <= 0) return;
+    iota_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, st>>>(p, n);
+}
+
+__global__ void sort_keys_by_part_kernel(const int32_t* S, int64_t nS, const int32_t* part, uint64_t* keys,
+                                         uint32_t* vals) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nS; i += (int64_t)gridDim.x * blockDim.x) {
+        keys[i] = (uint64_t)part[S[i]];
+        vals[i] = (uint32_t)S[i];
+    }
+}
+
+__global__ void i64_from_i32_kernel(const int32_t* in, int64_t* out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[i];
+}
+
+int bits_for(uint64_t maxval) {
+    int b = 0;
+    while (b < 64 && (maxval >> b) != 0) b++;
+    return b;
+}
+
+bcpp_opts opts_or_default(const bcpp_opts* o) {
+    bcpp_opts d;
+    bcpp_default_opts(&d);
+    return o ? *o : d;
+}
+
+int check_graph_struct(const bcpp_graph* g) {
+    if (!g || g->n < 0 || g->num_arcs < 0) return BCPP_EINVAL;
+    if (!g->row_ptr) return BCPP_EINVAL;
+    if (g->num_arcs > 0 && !g->col) return BCPP_EINVAL;
+    return BCPP_OK;
+}
+
+// Validate a CSR; on success *wmax_out = max weight (1 for unit weights).
+int validate_csr(bcpp_ctx* c, const bcpp_graph* g, uint64_t* wmax_out, const int64_t* node_off = nullptr,
+                 int32_t ngraphs = 0) {
+    DBuf<unsigned long long> wmax(c, 1);
+    CK_ALLOC(wmax);
+    CK_CUDA(cudaMemsetAsync(wmax.p, 0, sizeof(unsigned long long), c->stream));
+    csr_check(g->n, g->num_arcs, g->row_ptr, g->col, g->w, g->directed, c->flags, wmax.p, c->stream, node_off,
+              ngraphs);
+    c->launches++;
+    unsigned long long hw = 0;
+    CK_RC(to_host(c, &hw, (const unsigned long long*)wmax.p, 1));
+    CK_RC(sync_flags(c));
+    if (c->hflags[FLAG_INVALID]) return BCPP_EINVAL;
+    if (hw == 0) hw = 1;
+    if (g->n > 1 && (uint64_t)hw * (uint64_t)(g->n - 1) >= (1ull << 31)) return BCPP_EINVAL;
+    if (hw > (1ull << 20)) return BCPP_EINVAL;   // bucket array bound (max weight <= 2^20)
+    *wmax_out = hw;
+    return BCPP_OK;
+}
+
+// Per-slot lockstep workspace.
+struct SlotWs {
+    DBuf<int32_t> d;
+    DBuf<uint64_t> sg;
+    DBuf<char> dl;
+    DBuf<int32_t> order, step_d, step_beg, hdr;
+    DBuf<uint32_t> bm;
+    DBuf<uint8_t> bflag;
+    DBuf<double> bcs, bcc;
+    DBuf<int> counter;
+    LsSlots W{};
+};
+
+int64_t slot_bytes(int64_t cap_n, int nb, bool fp32) {
+    int64_t cap_order = 32 * cap_n + 1024;
+    int64_t bm_words = (cap_n + 31) / 32;
+    return cap_n * 32 * (4 + 8 + (fp32 ? 4 : 8)) + cap_order * 4 + 2 * (cap_n + 4098) * 4 +
+           (int64_t)nb * bm_words * 4 + nb;
+}
+
+// Choose how many slots (resident batches) to run, within the memory budget.
+int choose_slots(bcpp_ctx* c, int nitems, int ctas_per_sm, int64_t per_slot, int64_t per_slot_bc) {
+    int cps = ctas_per_sm > 0 ? ctas_per_sm : 2;
+    int slots = std::min<int64_t>(nitems, (int64_t)cps * c->num_sms);
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    int64_t reusable = 0;
+    for (auto& b : c->pool)
+        if (!b.used) reusable += (int64_t)b.bytes;
+    int64_t budget = (int64_t)((double)(fr + reusable) * 0.80);
+    int64_t each = per_slot + per_slot_bc;
+    if (each > 0) slots = (int)std::min<int64_t>(slots, std::max<int64_t>(1, budget / each));
+    return std::max(1, slots);
+}
+
+int alloc_slots(bcpp_ctx* c, SlotWs& S, int slots, int64_t cap_n, int nb, bool fp32, int64_t cap_bc) {
+    const int64_t cap_order = 32 * cap_n + 1024;
+    const int32_t cap_steps = (int32_t)std::min<int64_t>(cap_order, 4 * (cap_n + 2) + 4096);
+    const int64_t bm_words = (cap_n + 31) / 32;
+    CK_ALLOC(S.d.alloc(c, (int64_t)slots * cap_n * 32));
+    CK_ALLOC(S.sg.alloc(c, (int64_t)slots * cap_n * 32));
+    CK_ALLOC(S.dl.alloc(c, (int64_t)slots * cap_n * 32 * (fp32 ? 4 : 8)));
+    CK_ALLOC(S.order.alloc(c, (int64_t)slots * cap_order));
+    CK_ALLOC(S.step_d.alloc(c, (int64_t)slots * cap_steps));
+    CK_ALLOC(S.step_beg.alloc(c, (int64_t)slots * cap_steps));
+    CK_ALLOC(S.hdr.alloc(c, (int64_t)slots * 4));
+    CK_ALLOC(S.bm.alloc(c, (int64_t)slots * nb * bm_words));
+    CK_ALLOC(S.bflag.alloc(c, (int64_t)slots * nb));
+    CK_ALLOC(S.counter.alloc(c, 1));
+    if (cap_bc > 0) {
+        CK_ALLOC(S.bcs.alloc(c, (int64_t)slots * cap_bc));
+        CK_ALLOC(S.bcc.alloc(c, (int64_t)slots * cap_bc));
+        CK_CUDA(cudaMemsetAsync(S.bcs.p, 0, (size_t)slots * cap_bc * sizeof(double), c->stream));
+        CK_CUDA(cudaMemsetAsync(S.bcc.p, 0, (size_t)slots * cap_bc * sizeof(double), c->stream));
+    }
+    fill_i32(S.d.p, DINF, (int64_t)slots * cap_n * 32, c->stream);
+    c->launches++;
+    CK_CUDA(cudaMemsetAsync(S.bm.p, 0, (size_t)slots * nb * bm_words * sizeof(uint32_t), c->stream));
+    CK_CUDA(cudaMemsetAsync(S.bflag.p, 0, (size_t)slots * nb, c->stream));
+    CK_CUDA(cudaMemsetAsync(S.hdr.p, 0, (size_t)slots * 4 * sizeof(int32_t), c->stream));
+    CK_CUDA(cudaMemsetAsync(S.counter.p, 0, sizeof(int), c->stream));
+    LsSlots& W = S.W;
+    W.d = S.d.p; W.sg = S.sg.p; W.dl = S.dl.p; W.cap_n = cap_n;
+    W.order = S.order.p; W.cap_order = cap_order;
+    W.step_d = S.step_d.p; W.step_beg = S.step_beg.p; W.cap_steps = cap_steps;
+    W.bm = S.bm.p; W.bm_words = bm_words; W.bflag = S.bflag.p;
+    W.bc_sum = cap_bc > 0 ? S.bcs.p : nullptr;
+    W.bc_cmp = cap_bc > 0 ? S.bcc.p : nullptr;
+    W.cap_bc = cap_bc;
+    W.hdr = S.hdr.p;
+    return BCPP_OK;
+}
+
+struct Timer {
+    bcpp_ctx* c;
+    cudaEvent_t a, b;
+    float acc = 0.f;
+    explicit Timer(bcpp_ctx* ctx) : c(ctx) {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+    }
+    ~Timer() {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+    void start() { cudaEventRecord(a, c->stream); }
+    void stop() {
+        cudaEventRecord(b, c->stream);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        acc += ms;
+    }
+};
+
+int finish_status(bcpp_ctx* c, bcpp_stats* st) {
+    CK_RC(sync_flags(c));
+    if (st) st->sigma_overflow = c->hflags[FLAG_SIGMA_OVF] ? 1u : 0u;
+    if (c->hflags[FLAG_INVALID]) return BCPP_EINVAL;
+    if (c->hflags[FLAG_CAPACITY]) return BCPP_ECAPACITY;
+    if (c->hflags[FLAG_SIGMA_OVF]) return BCPP_EOVERFLOW_SIGMA;
+    return BCPP_OK;
+}
+
+// in-CSR (transpose) of a graph with uint32 weights
+struct InCsr {
+    DBuf<int64_t> rp;
+    DBuf<int32_t> col;
+    DBuf<uint32_t> w;
+};
+int build_in_csr(bcpp_ctx* c, const bcpp_graph* g, InCsr& T) {
+    const int32_t n = g->n;
+    CK_ALLOC(T.rp.alloc(c, (int64_t)n + 1));
+    CK_ALLOC(T.col.alloc(c, g->num_arcs));
+    if (g->w) CK_ALLOC(T.w.alloc(c, g->num_arcs));
+    DBuf<int64_t> cnt(c, (int64_t)n + 1), tmp(c, scan_tmp_elems((int64_t)n + 1));
+    CK_ALLOC(cnt); CK_ALLOC(tmp);
+    CK_CUDA(cudaMemsetAsync(cnt.p, 0, ((size_t)n + 1) * sizeof(int64_t), c->stream));
+    csr_transpose_count(n, g->row_ptr, g->col, cnt.p, c->stream);
+    exclusive_scan<int64_t>(cnt.p, T.rp.p, (int64_t)n + 1, nullptr, tmp.p, c->stream, c->launches);
+    CK_CUDA(cudaMemcpyAsync(cnt.p, T.rp.p, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, c->stream));
+    csr_transpose_fill(n, g->row_ptr, g->col, g->w, cnt.p, T.col.p, g->w ? T.w.p : nullptr, c->stream);
+    c->launches += 2;
+    CK_CUDA(cudaGetLastError());
+    return BCPP_OK;
+}
+
+// --------------------------------------------------------------------------- plain Brandes
+int brandes_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, const bcpp_opts& o, double* bc_out,
+                bcpp_stats* st) {
+    CK_RC(check_graph_struct(g));
+    if (nS < 0 || (nS > 0 && !S) || (g->n > 0 && !bc_out)) return BCPP_EINVAL;
+    const int32_t n = g->n;
+    const bool fp32 = o.precision == BCPP_FP32_DELTA;
+    Timer tt(c);
+    tt.start();
+    CK_RC(reset_flags(c));
+    uint64_t wmax = 1;
+    CK_RC(validate_csr(c, g, &wmax));
+    DBuf<uint8_t> in_s;
+    if (nS > 0) {
+        CK_ALLOC(in_s.alloc(c, n));
+        DBuf<uint32_t> cnt(c, n);
+        CK_ALLOC(cnt);
+        CK_CUDA(cudaMemsetAsync(in_s.p, 0, (size_t)std::max(n, 1), c->stream));
+        CK_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)std::max(n, 1) * 4, c->stream));
+        targets_check(S, nS, n, in_s.p, cnt.p, c->flags, c->stream);
+        c->launches++;
+        CK_RC(sync_flags(c));
+        if (c->hflags[FLAG_INVALID]) return BCPP_EINVAL;
+    }
+    const int64_t ns = nS > 0 ? nS : n;
+    if (ns < 2 || n == 0) {
+        if (n > 0) CK_CUDA(cudaMemsetAsync(bc_out, 0, (size_t)n * sizeof(double), c->stream));
+        CK_CUDA(cudaStreamSynchronize(c->stream));
+        return BCPP_OK;
+    }
+    DBuf<int32_t> all;
+    const int32_t* srcs = S;
+    if (nS == 0) {
+        CK_ALLOC(all.alloc(c, n));
+        iota(all.p, n, c->stream);
+        c->launches++;
+        srcs = all.p;
+    }
+    InCsr T;
+    if (g->directed) CK_RC(build_in_csr(c, g, T));
+    // items: batches of 32 targets in the given order
+    const int nitems = (int)((ns + LS_LANES - 1) / LS_LANES);
+    std::vector<LsItem> hitems(nitems);
+    for (int i = 0; i < nitems; i++)
+        hitems[i] = LsItem{0, i * LS_LANES, (int32_t)std::min<int64_t>(LS_LANES, ns - (int64_t)i * LS_LANES), 0};
+    DBuf<LsItem> items(c, nitems);
+    DBuf<int64_t> node_off(c, 2);
+    CK_ALLOC(items); CK_ALLOC(node_off);
+    CK_RC(to_dev(c, items.p, hitems.data(), nitems));
+    const int64_t hoff[2] = {0, n};
+    CK_RC(to_dev(c, node_off.p, hoff, 2));
+    const int nb = g->w ? (int)wmax + 1 : 2;
+    const int slots = choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(n, nb, fp32), (int64_t)n * 16);
+    SlotWs ws;
+    CK_RC(alloc_slots(c, ws, slots, n, nb, fp32, n));
+    LsArena A{};
+    A.rp = g->row_ptr; A.col = g->col; A.w = (const int32_t*)g->w; A.mu = nullptr;
+    if (g->directed) {
+        A.irp = T.rp.p; A.icol = T.col.p; A.iw = g->w ? (const int32_t*)T.w.p : nullptr;
+    } else {
+        A.irp = g->row_ptr; A.icol = g->col; A.iw = (const int32_t*)g->w;
+    }
+    A.imu = nullptr;
+    A.node_off = node_off.p;
+    LsParams P{};
+    P.mode = LS_BRANDES;
+    P.nb = nb;
+    P.srcs = srcs;
+    P.in_s = nS > 0 ? in_s.p : nullptr;
+    P.items_static = 0;
+    P.item_counter = ws.counter.p;
+    P.flags = c->flags;
+    Timer tb(c);
+    tb.start();
+    ls_launch(fp32, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream);
+    c->launches++;
+    CK_CUDA(cudaGetLastError());
+    const bool halve = !g->directed && o.halve_undirected != 0;
+    combine_launch(ws.W.bc_sum, ws.W.bc_cmp, slots, n, n, halve ? 0.5 : 1.0, bc_out, c->stream);
+    c->launches++;
+    tb.stop();
+    int rc = finish_status(c, st);
+    tt.stop();
+    if (st) {
+        st->ms_brandes_sk = tb.acc;
+        st->ms_total = tt.acc;
+    }
+    return rc;
+}
+
+// --------------------------------------------------------------------------- Build_SK
+struct Skeleton {
+    int32_t n = 0, kp = 0, N = 0;
+    int64_t arcs = 0, edges = 0, table_entries = 0;
+    int32_t lcs = 0, k_nonempty = 0;
+    uint64_t wmax_sk = 1, mmax_sk = 1;
+    DBuf<int32_t> partp, pstart, nf, loc, skid, sknode, skbase;
+    DBuf<uint8_t> fr;
+    DBuf<uint32_t> pnodes;
+    DBuf<int64_t> toff, pstart64;
+    DBuf<int32_t> td, tdr;
+    DBuf<uint64_t> ts, tsr;
+    DBuf<int64_t> skrp;
+    DBuf<int32_t> skcol, skw;
+    DBuf<uint64_t> skmu;
+    std::vector<int32_t> h_pstart, h_nf, h_skbase;
+    std::vector<int64_t> h_toff;
+    SkTables tables() const {
+        SkTables T;
+        T.pstart = pstart.p; T.nf = nf.p; T.toff = toff.p;
+        T.td = td.p; T.ts = ts.p;
+        T.tdr = tdr.p ? tdr.p : td.p;
+        T.tsr = tsr.p ? tsr.p : ts.p;
+        return T;
+    }
+};
+
+// part-local CSR over the grouped node order (graph i = part i of P')
+int build_local_csr(bcpp_ctx* c, const Skeleton& K, const int64_t* rp, const int32_t* col, const uint32_t* w,
+                    DBuf<int64_t>& lrp, DBuf<int32_t>& lcol, DBuf<int32_t>& lw) {
+    const int32_t n = K.n;
+    DBuf<int64_t> cnt(c, (int64_t)n + 1), tmp(c, scan_tmp_elems((int64_t)n + 1));
+    CK_ALLOC(cnt); CK_ALLOC(tmp);
+    CK_ALLOC(lrp.alloc(c, (int64_t)n + 1));
+    CK_CUDA(cudaMemsetAsync(cnt.p, 0, ((size_t)n + 1) * sizeof(int64_t), c->stream));
+    sk_local_count(n, K.pnodes.p, rp, col, K.partp.p, cnt.p, c->stream);
+    exclusive_scan<int64_t>(cnt.p, lrp.p, (int64_t)n + 1, nullptr, tmp.p, c->stream, c->launches);
+    int64_t total = 0;
+    CK_RC(to_host(c, &total, lrp.p + n, 1));
+    CK_ALLOC(lcol.alloc(c, total));
+    if (w) CK_ALLOC(lw.alloc(c, total));
+    sk_local_fill(n, K.pnodes.p, rp, col, w, K.partp.p, K.loc.p, lrp.p, lcol.p, w ? lw.p : nullptr, c->stream);
+    c->launches += 2;
+    CK_CUDA(cudaGetLastError());
+    return BCPP_OK;
+}
+
+int build_sk(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS_eff, const int32_t* part, int32_t k,
+             uint64_t wmax, const InCsr* Tin, const bcpp_opts& o, Skeleton& K) {
+    const int32_t n = g->n;
+    const bool fp32 = o.precision == BCPP_FP32_DELTA;
+    (void)fp32;
+    K.n = n;
+    K.kp = k + nS_eff;
+    const int32_t kp = K.kp;
+    CK_ALLOC(K.partp.alloc(c, n));
+    CK_ALLOC(K.fr.alloc(c, n));
+    CK_ALLOC(K.pnodes.alloc(c, n));
+    CK_ALLOC(K.pstart.alloc(c, (int64_t)kp + 1));
+    CK_ALLOC(K.nf.alloc(c, kp));
+    CK_ALLOC(K.loc.alloc(c, n));
+    CK_ALLOC(K.skid.alloc(c, n));
+    // P' and frontiers
+    sk_partition(n, part, k, S, nS_eff, K.partp.p, c->flags, c->stream);
+    CK_CUDA(cudaMemsetAsync(K.fr.p, 0, (size_t)std::max(n, 1), c->stream));
+    sk_frontiers(n, g->row_ptr, g->col, K.partp.p, K.fr.p, c->stream);
+    c->launches += 3;
+    // group nodes by (part, frontiers first), stable in node id
+    {
+        DBuf<uint64_t> keys(c, n), kb(c, n);
+        DBuf<uint32_t> vb(c, n);
+        DBuf<int64_t> hist(c, radix_hist_elems(n)), tmp(c, scan_tmp_elems(radix_hist_elems(n)));
+        CK_ALLOC(keys); CK_ALLOC(kb); CK_ALLOC(vb); CK_ALLOC(hist); CK_ALLOC(tmp);
+        sk_group_keys(n, K.partp.p, K.fr.p, keys.p, K.pnodes.p, c->stream);
+        radix_sort_pairs(keys.p, K.pnodes.p, kb.p, vb.p, n, bits_for(2ull * (uint64_t)kp), hist.p, tmp.p, c->stream,
+                         c->launches);
+        sk_segments(keys.p, n, kp, K.pstart.p, K.nf.p, c->stream);
+        c->launches += 2;
+        CK_CUDA(cudaGetLastError());
+    }
+    K.h_pstart.resize((size_t)kp + 1);
+    K.h_nf.resize(kp);
+    CK_RC(to_host(c, K.h_pstart.data(), K.pstart.p, (int64_t)kp + 1));
+    CK_RC(to_host(c, K.h_nf.data(), K.nf.p, kp));
+    CK_RC(sync_flags(c));
+    if (c->hflags[FLAG_INVALID]) return BCPP_EINVAL;
+    // host: skeleton ids, table offsets, statistics
+    K.h_skbase.resize(kp);
+    K.h_toff.resize((size_t)kp + 1);
+    int64_t N = 0, tofs = 0;
+    int32_t maxpart_tab = 0;
+    K.lcs = 0;
+    K.k_nonempty = 0;
+    for (int32_t i = 0; i < kp; i++) {
+        const int32_t sz = K.h_pstart[i + 1] - K.h_pstart[i];
+        K.h_skbase[i] = (int32_t)N;
+        N += K.h_nf[i];
+        K.h_toff[i] = tofs;
+        if (sz >= 2 && K.h_nf[i] >= 1) {
+            tofs += (int64_t)sz * K.h_nf[i];
+            maxpart_tab = std::max(maxpart_tab, sz);
+        }
+        K.lcs = std::max(K.lcs, sz);
+        K.k_nonempty += sz > 0;
+    }
+    K.h_toff[kp] = tofs;
+    K.N = (int32_t)N;
+    K.table_entries = tofs;
+    CK_ALLOC(K.skbase.alloc(c, kp));
+    CK_ALLOC(K.toff.alloc(c, (int64_t)kp + 1));
+    CK_ALLOC(K.sknode.alloc(c, std::max<int64_t>(N, 1)));
+    CK_RC(to_dev(c, K.skbase.p, K.h_skbase.data(), kp));
+    CK_RC(to_dev(c, K.toff.p, K.h_toff.data(), (int64_t)kp + 1));
+    sk_local_ids(n, K.pnodes.p, K.partp.p, K.pstart.p, K.nf.p, K.skbase.p, K.loc.p, K.skid.p, K.sknode.p, c->stream);
+    c->launches++;
+    CK_ALLOC(K.td.alloc(c, std::max<int64_t>(tofs, 1)));
+    CK_ALLOC(K.ts.alloc(c, std::max<int64_t>(tofs, 1)));
+    if (g->directed) {
+        CK_ALLOC(K.tdr.alloc(c, std::max<int64_t>(tofs, 1)));
+        CK_ALLOC(K.tsr.alloc(c, std::max<int64_t>(tofs, 1)));
+    }
+    CK_ALLOC(K.pstart64.alloc(c, (int64_t)kp + 1));
+    i64_from_i32_kernel<<<(unsigned)std::min<int64_t>(((int64_t)kp + 256) / 256, 8192), 256, 0, c->stream>>>(
+        K.pstart.p, K.pstart64.p, (int64_t)kp + 1);
+    c->launches++;
+    // Dijkstra_SK (Eq. 10) in every part with a table, from every frontier
+    if (tofs > 0) {
+        DBuf<int64_t> lrp, lirp;
+        DBuf<int32_t> lcol, lw, licol, liw;
+        CK_RC(build_local_csr(c, K, g->row_ptr, g->col, g->w, lrp, lcol, lw));
+        if (g->directed) CK_RC(build_local_csr(c, K, Tin->rp.p, Tin->col.p, Tin->w.p, lirp, licol, liw));
+        std::vector<LsItem> hitems;
+        std::vector<int32_t> order_parts;
+        int32_t maxnf = 0;
+        for (int32_t i = 0; i < kp; i++) {
+            const int32_t sz = K.h_pstart[i + 1] - K.h_pstart[i];
+            if (sz >= 2 && K.h_nf[i] >= 1) order_parts.push_back(i);
+        }
+        std::stable_sort(order_parts.begin(), order_parts.end(), [&](int32_t a, int32_t b) {
+            return (K.h_pstart[a + 1] - K.h_pstart[a]) > (K.h_pstart[b + 1] - K.h_pstart[b]);
+        });
+        for (int32_t i : order_parts) {
+            maxnf = std::max(maxnf, K.h_nf[i]);
+            for (int32_t f0 = 0; f0 < K.h_nf[i]; f0 += LS_LANES)
+                hitems.push_back(LsItem{i, f0, std::min(LS_LANES, K.h_nf[i] - f0), f0});
+        }
+        const int nitems = (int)hitems.size();
+        DBuf<LsItem> items(c, nitems);
+        DBuf<int32_t> srcs(c, maxnf);
+        CK_ALLOC(items); CK_ALLOC(srcs);
+        CK_RC(to_dev(c, items.p, hitems.data(), nitems));
+        iota(srcs.p, maxnf, c->stream);
+        c->launches++;
+        const int nb = g->w ? (int)wmax + 1 : 2;
+        const int slots = choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(maxpart_tab, nb, false), 0);
+        for (int dir = 0; dir < (g->directed ? 2 : 1); dir++) {
+            SlotWs ws;
+            CK_RC(alloc_slots(c, ws, slots, maxpart_tab, nb, false, 0));
+            LsArena A{};
+            if (dir == 0) {
+                A.rp = lrp.p; A.col = lcol.p; A.w = g->w ? lw.p : nullptr;
+                A.irp = g->directed ? lirp.p : lrp.p;
+                A.icol = g->directed ? licol.p : lcol.p;
+                A.iw = g->w ? (g->directed ? liw.p : lw.p) : nullptr;
+            } else {
+                A.rp = lirp.p; A.col = licol.p; A.w = g->w ? liw.p : nullptr;
+                A.irp = lrp.p; A.icol = lcol.p; A.iw = g->w ? lw.p : nullptr;
+            }
+            A.node_off = K.pstart64.p;
+            LsParams P{};
+            P.mode = LS_TABLE;
+            P.nb = nb;
+            P.srcs = srcs.p;
+            P.nfront = K.nf.p;
+            P.toff = K.toff.p;
+            P.td = dir == 0 ? K.td.p : K.tdr.p;
+            P.ts = dir == 0 ? K.ts.p : K.tsr.p;
+            P.item_counter = ws.counter.p;
+            P.flags = c->flags;
+            ls_launch(false, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream);
+            c->launches++;
+            CK_CUDA(cudaGetLastError());
+            CK_CUDA(cudaStreamSynchronize(c->stream));
+        }
+    }
+    // skeleton arcs: R with <w,1>, X_i with <d_i, sigma_i>
+    {
+        const SkTables T = K.tables();
+        DBuf<int64_t> cnt(c, N + 1), tmp(c, scan_tmp_elems(N + 1));
+        DBuf<unsigned long long> maxes(c, 2);
+        CK_ALLOC(cnt); CK_ALLOC(tmp); CK_ALLOC(maxes);
+        CK_ALLOC(K.skrp.alloc(c, N + 1));
+        CK_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)(N + 1) * sizeof(int64_t), c->stream));
+        CK_CUDA(cudaMemsetAsync(maxes.p, 0, 2 * sizeof(unsigned long long), c->stream));
+        sk_arcs_count((int32_t)N, K.sknode.p, g->row_ptr, g->col, K.partp.p, K.loc.p, T, cnt.p, c->stream);
+        exclusive_scan<int64_t>(cnt.p, K.skrp.p, N + 1, nullptr, tmp.p, c->stream, c->launches);
+        CK_RC(to_host(c, &K.arcs, K.skrp.p + N, 1));
+        CK_ALLOC(K.skcol.alloc(c, K.arcs));
+        CK_ALLOC(K.skw.alloc(c, K.arcs));
+        CK_ALLOC(K.skmu.alloc(c, K.arcs));
+        sk_arcs_fill((int32_t)N, K.sknode.p, g->row_ptr, g->col, g->w, K.partp.p, K.loc.p, K.skid.p, T, K.skrp.p,
+                     K.skcol.p, K.skw.p, K.skmu.p, maxes.p, c->stream);
+        c->launches += 2;
+        unsigned long long hm[2] = {0, 0};
+        CK_RC(to_host(c, hm, maxes.p, 2));
+        K.wmax_sk = std::max<unsigned long long>(hm[0], 1);
+        K.mmax_sk = std::max<unsigned long long>(hm[1], 1);
+        K.edges = g->directed ? K.arcs : K.arcs / 2;
+    }
+    CK_CUDA(cudaGetLastError());
+    return BCPP_OK;
+}
+
+// --------------------------------------------------------------------------- Brandes++
+int brandes_pp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, const int32_t* part, int32_t k,
+                   const bcpp_opts& o, double* bc_out, bcpp_stats* st) {
+    CK_RC(check_graph_struct(g));
+    const int32_t n = g->n;
+    if (nS < 0 || (nS > 0 && !S) || (n > 0 && (!bc_out || !part)) || k < 0 || (n > 0 && k == 0)) return BCPP_EINVAL;
+    const bool fp32 = o.precision == BCPP_FP32_DELTA;
+    Timer tt(c), tb(c), tbr(c), tce(c);
+    tt.start();
+    CK_RC(reset_flags(c));
+    uint64_t wmax = 1;
+    CK_RC(validate_csr(c, g, &wmax));
+    const int64_t ns = nS > 0 ? nS : n;
+    DBuf<uint8_t> in_s(c, n);
+    CK_ALLOC(in_s);
+    DBuf<int32_t> Sall;
+    const int32_t* Sp = S;
+    if (nS > 0) {
+        DBuf<uint32_t> cnt(c, n);
+        CK_ALLOC(cnt);
+        CK_CUDA(cudaMemsetAsync(in_s.p, 0, (size_t)std::max(n, 1), c->stream));
+        CK_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)std::max(n, 1) * 4, c->stream));
+        targets_check(S, nS, n, in_s.p, cnt.p, c->flags, c->stream);
+        c->launches++;
+    } else {
+        CK_CUDA(cudaMemsetAsync(in_s.p, 1, (size_t)std::max(n, 1), c->stream));
+        CK_ALLOC(Sall.alloc(c, n));
+        iota(Sall.p, n, c->stream);
+        c->launches++;
+        Sp = Sall.p;
+    }
+    CK_RC(sync_flags(c));
+    if (c->hflags[FLAG_INVALID]) return BCPP_EINVAL;
+    if (ns < 2 || n == 0) {
+        if (n > 0) CK_CUDA(cudaMemsetAsync(bc_out, 0, (size_t)n * sizeof(double), c->stream));
+        CK_CUDA(cudaStreamSynchronize(c->stream));
+        return BCPP_OK;
+    }
+    InCsr Tin;
+    if (g->directed) CK_RC(build_in_csr(c, g, Tin));
+    // Step 1: Build_SK on P'
+    tb.start();
+    Skeleton K;
+    CK_RC(build_sk(c, g, Sp, (int32_t)ns, part, k, wmax, g->directed ? &Tin : nullptr, o, K));
+    tb.stop();
+    // Step 2 + 3: Brandes_SK from every target, Centrality of the non-frontier nodes
+    const int32_t N = K.N;
+    // targets in batch order (grouped by their original part when requested), as skeleton ids
+    DBuf<int32_t> tsk(c, ns), tcnt(c, 1);
+    CK_ALLOC(tsk); CK_ALLOC(tcnt);
+    {
+        DBuf<int32_t> Sord;
+        const int32_t* Suse = Sp;
+        if (o.order_sources) {
+            DBuf<uint64_t> keys(c, ns), kb(c, ns);
+            DBuf<uint32_t> vals(c, ns), vb(c, ns);
+            DBuf<int64_t> hist(c, radix_hist_elems(ns)), tmp(c, scan_tmp_elems(radix_hist_elems(ns)));
+            CK_ALLOC(keys); CK_ALLOC(kb); CK_ALLOC(vals); CK_ALLOC(vb); CK_ALLOC(hist); CK_ALLOC(tmp);
+            sort_keys_by_part_kernel<<<(unsigned)std::min<int64_t>((ns + 255) / 256, 8192), 256, 0, c->stream>>>(
+                Sp, ns, part, keys.p, vals.p);
+            c->launches++;
+            radix_sort_pairs(keys.p, vals.p, kb.p, vb.p, ns, bits_for((uint64_t)k), hist.p, tmp.p, c->stream,
+                             c->launches);
+            CK_ALLOC(Sord.alloc(c, ns));
+            CK_CUDA(cudaMemcpyAsync(Sord.p, vals.p, ns * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
+            Suse = Sord.p;
+        }
+        sk_target_ids(Suse, (int32_t)ns, K.skid.p, tsk.p, tcnt.p, c->stream);
+        c->launches++;
+    }
+    int32_t nt = 0;
+    CK_RC(to_host(c, &nt, tcnt.p, 1));
+    DBuf<double> bsum, bcmp;
+    int slots_used = 0;
+    // partial sums live in the lockstep slots; combine at the end
+    SlotWs ws;
+    const bool unit = K.wmax_sk == 1;
+    const bool mult = K.mmax_sk > 1;
+    const int nb = (int)K.wmax_sk + 1;
+    const int nitems = (nt + LS_LANES - 1) / LS_LANES;
+    const int slots = nitems > 0 ? choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(std::max(N, 1), nb, fp32),
+                                                (int64_t)n * 16)
+                                 : 1;
+    CK_RC(alloc_slots(c, ws, slots, std::max(N, 1), nb, fp32, n));
+    slots_used = slots;
+    if (nitems > 0) {
+        DBuf<uint8_t> sk_in_s(c, N);
+        CK_ALLOC(sk_in_s);
+        sk_gather_flags(N, K.sknode.p, in_s.p, sk_in_s.p, c->stream);
+        c->launches++;
+        // skeleton in-arcs for directed graphs
+        DBuf<int64_t> irp;
+        DBuf<int32_t> icol, iw;
+        DBuf<uint64_t> imu;
+        if (g->directed) {
+            DBuf<int64_t> cnt(c, (int64_t)N + 1), tmp(c, scan_tmp_elems((int64_t)N + 1));
+            CK_ALLOC(cnt); CK_ALLOC(tmp);
+            CK_ALLOC(irp.alloc(c, (int64_t)N + 1));
+            CK_ALLOC(icol.alloc(c, K.arcs));
+            CK_ALLOC(iw.alloc(c, K.arcs));
+            CK_ALLOC(imu.alloc(c, K.arcs));
+            CK_CUDA(cudaMemsetAsync(cnt.p, 0, ((size_t)N + 1) * sizeof(int64_t), c->stream));
+            sk_transpose(N, K.skrp.p, K.skcol.p, K.skw.p, K.skmu.p, cnt.p, nullptr, nullptr, nullptr, 0, c->stream);
+            exclusive_scan<int64_t>(cnt.p, irp.p, (int64_t)N + 1, nullptr, tmp.p, c->stream, c->launches);
+            CK_CUDA(cudaMemcpyAsync(cnt.p, irp.p, ((size_t)N + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                                    c->stream));
+            sk_transpose(N, K.skrp.p, K.skcol.p, K.skw.p, K.skmu.p, cnt.p, icol.p, iw.p, imu.p, 1, c->stream);
+            c->launches += 2;
+        }
+        DBuf<int64_t> node_off(c, 2);
+        CK_ALLOC(node_off);
+        const int64_t hoff[2] = {0, N};
+        CK_RC(to_dev(c, node_off.p, hoff, 2));
+        LsArena A{};
+        A.rp = K.skrp.p; A.col = K.skcol.p;
+        A.w = unit ? nullptr : K.skw.p;
+        A.mu = mult ? K.skmu.p : nullptr;
+        if (g->directed) {
+            A.irp = irp.p; A.icol = icol.p; A.iw = unit ? nullptr : iw.p; A.imu = mult ? imu.p : nullptr;
+        } else {
+            A.irp = A.rp; A.icol = A.col; A.iw = A.w; A.imu = A.mu;
+        }
+        A.node_off = node_off.p;
+        // Centrality work units: chunks of 64 non-frontier nodes of parts with frontiers
+        std::vector<CentralityUnit> hunits;
+        for (int32_t i = 0; i < K.kp; i++) {
+            const int32_t sz = K.h_pstart[i + 1] - K.h_pstart[i];
+            if (K.h_nf[i] < 1 || sz <= K.h_nf[i]) continue;
+            for (int32_t v0 = K.h_nf[i]; v0 < sz; v0 += 64) hunits.push_back({i, v0, std::min(sz, v0 + 64), 0});
+        }
+        DBuf<CentralityUnit> units(c, (int64_t)hunits.size());
+        CK_ALLOC(units);
+        CK_RC(to_dev(c, units.p, hunits.data(), (int64_t)hunits.size()));
+        std::vector<LsItem> hitems(nitems);
+        for (int i = 0; i < nitems; i++)
+            hitems[i] = LsItem{0, i * LS_LANES, std::min(LS_LANES, nt - i * LS_LANES), 0};
+        DBuf<LsItem> items(c, nitems);
+        CK_ALLOC(items);
+        CK_RC(to_dev(c, items.p, hitems.data(), nitems));
+        const SkTables T = K.tables();
+        for (int c0 = 0; c0 < nitems; c0 += slots) {
+            const int cn = std::min(slots, nitems - c0);
+            LsParams P{};
+            P.mode = LS_SKEL;
+            P.nb = nb;
+            P.srcs = tsk.p;
+            P.in_s = sk_in_s.p;
+            P.bc_map = K.sknode.p;
+            P.items_static = 1;
+            P.flags = c->flags;
+            tbr.start();
+            ls_launch(fp32, !g->directed, A, P, ws.W, items.p + c0, cn, cn, c->stream);
+            c->launches++;
+            tbr.stop();
+            CK_CUDA(cudaGetLastError());
+            if (!hunits.empty()) {
+                tce.start();
+                centrality_launch(fp32, units.p, (int)hunits.size(), cn, T, K.pnodes.p, K.skbase.p, ws.W.d, ws.W.sg,
+                                  ws.W.dl, ws.W.cap_n, ws.W.bc_sum, ws.W.bc_cmp, ws.W.cap_bc, c->flags, c->stream);
+                c->launches++;
+                tce.stop();
+                CK_CUDA(cudaGetLastError());
+            }
+            ls_reset_launch(ws.W, cn, c->stream);
+            c->launches++;
+        }
+    }
+    const bool halve = !g->directed && o.halve_undirected != 0;
+    combine_launch(ws.W.bc_sum, ws.W.bc_cmp, slots_used, n, n, halve ? 0.5 : 1.0, bc_out, c->stream);
+    c->launches++;
+    int rc = finish_status(c, st);
+    tt.stop();
+    if (st) {
+        st->skel_nodes = K.N;
+        st->skel_edges = K.edges;
+        st->k = K.k_nonempty;
+        st->lcs = K.lcs;
+        st->table_entries = K.table_entries;
+        st->ms_build_sk = tb.acc;
+        st->ms_brandes_sk = tbr.acc;
+        st->ms_centrality = tce.acc;
+        st->ms_total = tt.acc;
+    }
+    return rc;
+}
+
+// --------------------------------------------------------------------------- batched graphs
+int batched_dev(bcpp_ctx* c, int32_t ngraphs, const int64_t* node_ptr_dev, const int64_t* node_ptr_host,
+                const bcpp_graph* g, const bcpp_opts& o, double* bc_out, bcpp_stats* st) {
+    CK_RC(check_graph_struct(g));
+    if (ngraphs < 0 || (g->n > 0 && !bc_out) || g->directed) return BCPP_EINVAL;
+    const int32_t n = g->n;
+    const bool fp32 = o.precision == BCPP_FP32_DELTA;
+    Timer tt(c), tb(c);
+    tt.start();
+    CK_RC(reset_flags(c));
+    std::vector<int64_t> off((size_t)ngraphs + 1);
+    std::memcpy(off.data(), node_ptr_host, off.size() * sizeof(int64_t));
+    if (off[0] != 0 || off[ngraphs] != n) return BCPP_EINVAL;
+    int64_t maxn = 0;
+    for (int32_t i = 0; i < ngraphs; i++) {
+        if (off[i + 1] < off[i]) return BCPP_EINVAL;
+        maxn = std::max(maxn, off[i + 1] - off[i]);
+    }
+    uint64_t wmax = 1;
+    CK_RC(validate_csr(c, g, &wmax));
+    DBuf<int32_t> lcol(c, g->num_arcs);
+    CK_ALLOC(lcol);
+    csr_localize(n, g->row_ptr, g->col, node_ptr_dev, ngraphs, lcol.p, c->flags, c->stream);
+    c->launches++;
+    CK_RC(sync_flags(c));
+    if (c->hflags[FLAG_INVALID]) return BCPP_EINVAL;
+    if (n > 0) CK_CUDA(cudaMemsetAsync(bc_out, 0, (size_t)n * sizeof(double), c->stream));
+    // largest graphs first (work grows about quadratically with the node count)
+    std::vector<int32_t> gorder(ngraphs);
+    std::iota(gorder.begin(), gorder.end(), 0);
+    std::stable_sort(gorder.begin(), gorder.end(),
+                     [&](int32_t a, int32_t b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
+    std::vector<LsItem> hitems;
+    for (int32_t gi : gorder) {
+        const int32_t ng = (int32_t)(off[gi + 1] - off[gi]);
+        if (ng < 2) continue;
+        for (int32_t s0 = 0; s0 < ng; s0 += LS_LANES) hitems.push_back(LsItem{gi, s0, std::min(LS_LANES, ng - s0), 0});
+    }
+    const int nitems = (int)hitems.size();
+    if (nitems == 0) {
+        CK_CUDA(cudaStreamSynchronize(c->stream));
+        return BCPP_OK;
+    }
+    DBuf<LsItem> items(c, nitems);
+    DBuf<int32_t> srcs(c, maxn);
+    CK_ALLOC(items); CK_ALLOC(srcs);
+    CK_RC(to_dev(c, items.p, hitems.data(), nitems));
+    iota(srcs.p, maxn, c->stream);
+    c->launches++;
+    const int nb = g->w ? (int)wmax + 1 : 2;
+    const int slots = choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(maxn, nb, fp32), (int64_t)n * 16);
+    SlotWs ws;
+    CK_RC(alloc_slots(c, ws, slots, maxn, nb, fp32, n));
+    LsArena A{};
+    A.rp = g->row_ptr; A.col = lcol.p; A.w = (const int32_t*)g->w;
+    A.irp = g->row_ptr; A.icol = lcol.p; A.iw = (const int32_t*)g->w;
+    A.node_off = node_ptr_dev;
+    LsParams P{};
+    P.mode = LS_BRANDES;
+    P.nb = nb;
+    P.srcs = srcs.p;
+    P.item_counter = ws.counter.p;
+    P.flags = c->flags;
+    tb.start();
+    ls_launch(fp32, true, A, P, ws.W, items.p, nitems, slots, c->stream);
+    c->launches++;
+    CK_CUDA(cudaGetLastError());
+    combine_launch(ws.W.bc_sum, ws.W.bc_cmp, slots, n, n, o.halve_undirected ? 0.5 : 1.0, bc_out, c->stream);
+    c->launches++;
+    tb.stop();
+    int rc = finish_status(c, st);
+    tt.stop();
+    if (st) {
+        st->ms_brandes_sk = tb.acc;
+        st->ms_total = tt.acc;
+    }
+    return rc;
+}
+
+// --------------------------------------------------------------------------- inspection
+int sssp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* src, int32_t nsrc, int32_t* dist_out,
+             uint64_t* sigma_out, const bcpp_opts& o) {
+    CK_RC(check_graph_struct(g));
+    if (nsrc < 0 || (nsrc > 0 && (!src || !dist_out || !sigma_out))) return BCPP_EINVAL;
+    const int32_t n = g->n;
+    CK_RC(reset_flags(c));
+    uint64_t wmax = 1;
+    CK_RC(validate_csr(c, g, &wmax));
+    if (nsrc == 0 || n == 0) return BCPP_OK;
+    {
+        // sources must lie in range (repeats are fine here)
+        std::vector<int32_t> hs(nsrc);
+        CK_RC(to_host(c, hs.data(), src, nsrc));
+        for (int32_t s : hs)
+            if (s < 0 || s >= n) return BCPP_EINVAL;
+    }
+    InCsr T;
+    if (g->directed) CK_RC(build_in_csr(c, g, T));
+    const int nitems = (nsrc + LS_LANES - 1) / LS_LANES;
+    std::vector<LsItem> hitems(nitems);
+    for (int i = 0; i < nitems; i++) hitems[i] = LsItem{0, i * LS_LANES, std::min(LS_LANES, nsrc - i * LS_LANES), 0};
+    DBuf<LsItem> items(c, nitems);
+    DBuf<int64_t> node_off(c, 2);
+    CK_ALLOC(items); CK_ALLOC(node_off);
+    CK_RC(to_dev(c, items.p, hitems.data(), nitems));
+    const int64_t hoff[2] = {0, n};
+    CK_RC(to_dev(c, node_off.p, hoff, 2));
+    // a batch holds each source at most once: split repeated sources across batches is not
+    // needed because LS_SSSP lanes are independent rows (a repeat only repeats the row)
+    const int nb = g->w ? (int)wmax + 1 : 2;
+    const int slots = choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(n, nb, false), 0);
+    SlotWs ws;
+    CK_RC(alloc_slots(c, ws, slots, n, nb, false, 0));
+    LsArena A{};
+    A.rp = g->row_ptr; A.col = g->col; A.w = (const int32_t*)g->w;
+    if (g->directed) {
+        A.irp = T.rp.p; A.icol = T.col.p; A.iw = g->w ? (const int32_t*)T.w.p : nullptr;
+    } else {
+        A.irp = g->row_ptr; A.icol = g->col; A.iw = (const int32_t*)g->w;
+    }
+    A.node_off = node_off.p;
+    LsParams P{};
+    P.mode = LS_SSSP;
+    P.nb = nb;
+    P.srcs = src;
+    P.dbg_d = dist_out;
+    P.dbg_s = sigma_out;
+    P.dbg_n = n;
+    P.item_counter = ws.counter.p;
+    P.flags = c->flags;
+    ls_launch(false, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream);
+    c->launches++;
+    CK_CUDA(cudaGetLastError());
+    return finish_status(c, nullptr);
+}
+
+int skeleton_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, const int32_t* part, int32_t k,
+                 int32_t* sk_nodes_out, int32_t* n_sk_out, int64_t cap_arcs, int32_t* au, int32_t* av, int32_t* aw,
+                 uint64_t* amu, int64_t* n_arcs_out, const bcpp_opts& o, bool host_out) {
+    CK_RC(check_graph_struct(g));
+    const int32_t n = g->n;
+    if (nS < 0 || (nS > 0 && !S) || (n > 0 && !part) || k < 0 || !n_sk_out || !n_arcs_out) return BCPP_EINVAL;
+    CK_RC(reset_flags(c));
+    uint64_t wmax = 1;
+    CK_RC(validate_csr(c, g, &wmax));
+    if (nS > 0) {
+        DBuf<uint8_t> in_s(c, n);
+        DBuf<uint32_t> cnt(c, n);
+        CK_ALLOC(in_s); CK_ALLOC(cnt);
+        CK_CUDA(cudaMemsetAsync(in_s.p, 0, (size_t)std::max(n, 1), c->stream));
+        CK_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)std::max(n, 1) * 4, c->stream));
+        targets_check(S, nS, n, in_s.p, cnt.p, c->flags, c->stream);
+        c->launches++;
+        CK_RC(sync_flags(c));
+        if (c->hflags[FLAG_INVALID]) return BCPP_EINVAL;
+    }
+    InCsr Tin;
+    if (g->directed) CK_RC(build_in_csr(c, g, Tin));
+    Skeleton K;
+    CK_RC(build_sk(c, g, S, nS, part, k, wmax, g->directed ? &Tin : nullptr, o, K));
+    CK_RC(finish_status(c, nullptr));
+    *n_sk_out = K.N;
+    *n_arcs_out = K.arcs;
+    std::vector<int32_t> sknode(K.N), col(K.arcs), w(K.arcs);
+    std::vector<int64_t> rp((size_t)K.N + 1);
+    std::vector<uint64_t> mu(K.arcs);
+    CK_RC(to_host(c, sknode.data(), K.sknode.p, K.N));
+    CK_RC(to_host(c, rp.data(), K.skrp.p, (int64_t)K.N + 1));
+    CK_RC(to_host(c, col.data(), K.skcol.p, K.arcs));
+    CK_RC(to_host(c, w.data(), K.skw.p, K.arcs));
+    CK_RC(to_host(c, mu.data(), K.skmu.p, K.arcs));
+    std::vector<int32_t> nodes(sknode);
+    std::sort(nodes.begin(), nodes.end());
+    if (K.arcs > cap_arcs) return BCPP_ECAPACITY;
+    std::vector<int32_t> hu(K.arcs), hv(K.arcs);
+    for (int32_t x = 0; x < K.N; x++)
+        for (int64_t p = rp[x]; p < rp[x + 1]; p++) {
+            hu[p] = sknode[x];
+            hv[p] = sknode[col[p]];
+        }
+    auto put = [&](auto* dst, const auto* srcp, int64_t cnt) -> int {
+        if (cnt <= 0) return BCPP_OK;
+        if (host_out) {
+            std::memcpy(dst, srcp, cnt * sizeof(*srcp));
+            return BCPP_OK;
+        }
+        return to_dev(c, dst, srcp, cnt);
+    };
+    if (sk_nodes_out) CK_RC(put(sk_nodes_out, nodes.data(), K.N));
+    if (au) CK_RC(put(au, hu.data(), K.arcs));
+    if (av) CK_RC(put(av, hv.data(), K.arcs));
+    if (aw) CK_RC(put(aw, w.data(), K.arcs));
+    if (amu) CK_RC(put(amu, mu.data(), K.arcs));
+    return BCPP_OK;
+}
+
+int csr_build_dev(bcpp_ctx* c, int32_t n, int64_t m, const int32_t* eu, const int32_t* ev, const uint32_t* ew,
+                  int32_t directed, int64_t* rp, int32_t* col, uint32_t* w_out, int64_t* num_arcs_out) {
+    if (n < 0 || m < 0 || !rp || !num_arcs_out || (m > 0 && (!eu || !ev || !col))) return BCPP_EINVAL;
+    if (ew && !w_out && m > 0) return BCPP_EINVAL;
+    CK_RC(reset_flags(c));
+    const int64_t na = directed ? m : 2 * m;
+    DBuf<uint64_t> keys(c, na), kb(c, na);
+    DBuf<uint32_t> vals(c, na), vb(c, na);
+    DBuf<int64_t> hist(c, radix_hist_elems(na)), tmp(c, scan_tmp_elems(radix_hist_elems(na)));
+    CK_ALLOC(keys); CK_ALLOC(kb); CK_ALLOC(vals); CK_ALLOC(vb); CK_ALLOC(hist); CK_ALLOC(tmp);
+    csr_expand(n, m, eu, ev, ew, directed, keys.p, vals.p, c->flags, c->stream);
+    c->launches++;
+    CK_RC(sync_flags(c));
+    if (c->hflags[FLAG_INVALID]) return BCPP_EINVAL;
+    radix_sort_pairs(keys.p, vals.p, kb.p, vb.p, na, bits_for((uint64_t)n * (uint64_t)n), hist.p, tmp.p, c->stream,
+                     c->launches);
+    csr_finish(keys.p, vals.p, na, n, rp, col, ew ? w_out : nullptr, c->flags, c->stream);
+    c->launches += 2;
+    CK_CUDA(cudaGetLastError());
+    *num_arcs_out = na;
+    return finish_status(c, nullptr);
+}
+
+// --------------------------------------------------------------------------- host-buffer staging
+template <typename T>
+int stage_in(bcpp_ctx* c, DBuf<T>& buf, const T* host, int64_t count, const T** dev) {
+    if (!host) { *dev = nullptr; return BCPP_OK; }
+    CK_ALLOC(buf.alloc(c, count));
+    if (count > 0) CK_CUDA(cudaMemcpyAsync(buf.p, host, count * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    *dev = buf.p;
+    return BCPP_OK;
+}
+
+struct StagedGraph {
+    DBuf<int64_t> rp;
+    DBuf<int32_t> col;
+    DBuf<uint32_t> w;
+    bcpp_graph g{};
+};
+int stage_graph(bcpp_ctx* c, const bcpp_graph* hg, StagedGraph& sg) {
+    CK_RC(check_graph_struct(hg));
+    sg.g = *hg;
+    CK_RC(stage_in(c, sg.rp, hg->row_ptr, (int64_t)hg->n + 1, &sg.g.row_ptr));
+    CK_RC(stage_in(c, sg.col, hg->col, hg->num_arcs, &sg.g.col));
+    CK_RC(stage_in(c, sg.w, hg->w, hg->num_arcs, &sg.g.w));
+    return BCPP_OK;
+}
+
+}  // namespace
+
+// =========================================================================== C ABI
+extern "C" {
+
+void bcpp_default_opts(bcpp_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = BCPP_FP64;
+    o->halve_undirected = 1;
+    o->batch = 0;
+    o->ctas_per_sm = 0;
+    o->validate = 1;
+    o->host_buffers = 0;
+    o->order_sources = 1;
+}
+
+const char* bcpp_strerror(int s) {
+    switch (s) {
+        case BCPP_OK: return "ok";
+        case BCPP_EINVAL: return "invalid argument (graph, targets, partition or options)";
+        case BCPP_ENOMEM: return "out of device or host memory";
+        case BCPP_ECUDA: return "CUDA runtime error";
+        case BCPP_ETIMEOUT: return "a bounded device wait expired";
+        case BCPP_EOVERFLOW_SIGMA: return "a shortest-path count exceeded 2^64 (results written, not exact)";
+        case BCPP_ECAPACITY: return "a per-batch device list or an output buffer is too small";
+        default: return "unknown status";
+    }
+}
+
+int bcpp_create(bcpp_ctx** out, void* stream) {
+    if (!out) return BCPP_EINVAL;
+    *out = nullptr;
+    bcpp_ctx* c = new (std::nothrow) bcpp_ctx();
+    if (!c) return BCPP_ENOMEM;
+    c->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
+        cudaMalloc(&c->flags, FLAG_COUNT * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMallocHost(&c->hflags, FLAG_COUNT * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->flags) cudaFree(c->flags);
+        delete c;
+        return BCPP_ECUDA;
+    }
+    *out = c;
+    return BCPP_OK;
+}
+
+void bcpp_destroy(bcpp_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (auto& b : c->pool) cudaFree(b.p);
+    cudaFree(c->flags);
+    cudaFreeHost(c->hflags);
+    delete c;
+}
+
+int64_t bcpp_workspace_bytes(const bcpp_ctx* c) { return c ? c->held() : 0; }
+
+int bcpp_csr_build(bcpp_ctx* c, int32_t n, int64_t m, const int32_t* eu, const int32_t* ev, const uint32_t* ew,
+                   int32_t directed, int64_t* row_ptr_out, int32_t* col_out, uint32_t* w_out, int64_t* num_arcs_out) {
+    if (!c) return BCPP_EINVAL;
+    return csr_build_dev(c, n, m, eu, ev, ew, directed, row_ptr_out, col_out, w_out, num_arcs_out);
+}
+
+int bcpp_csr_validate(bcpp_ctx* c, const bcpp_graph* g) {
+    if (!c) return BCPP_EINVAL;
+    int rc = check_graph_struct(g);
+    if (rc) return rc;
+    if (reset_flags(c)) return BCPP_ECUDA;
+    uint64_t wmax = 1;
+    return validate_csr(c, g, &wmax);
+}
+
+int bcpp_brandes(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, const bcpp_opts* opts, double* bc_out,
+                 bcpp_stats* stats) {
+    if (!c || !g) return BCPP_EINVAL;
+    const bcpp_opts o = opts_or_default(opts);
+    const int64_t l0 = c->launches;
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    int rc;
+    if (o.host_buffers) {
+        StagedGraph sg;
+        DBuf<int32_t> dS;
+        DBuf<double> dbc;
+        const int32_t* pS = nullptr;
+        rc = stage_graph(c, g, sg);
+        if (!rc) rc = stage_in(c, dS, S, nS, &pS);
+        if (!rc && !dbc.alloc(c, g->n)) rc = BCPP_ENOMEM;
+        if (!rc) rc = brandes_dev(c, &sg.g, pS, nS, o, dbc.p, stats);
+        if ((rc == BCPP_OK || rc == BCPP_EOVERFLOW_SIGMA) && g->n > 0 &&
+            to_host(c, bc_out, dbc.p, g->n) != BCPP_OK)
+            rc = BCPP_ECUDA;
+    } else {
+        rc = brandes_dev(c, g, S, nS, o, bc_out, stats);
+    }
+    if (stats) stats->kernel_launches = c->launches - l0;
+    return rc;
+}
+
+int bcpp_brandes_pp(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, const int32_t* part, int32_t k,
+                    const bcpp_opts* opts, double* bc_out, bcpp_stats* stats) {
+    if (!c || !g) return BCPP_EINVAL;
+    const bcpp_opts o = opts_or_default(opts);
+    const int64_t l0 = c->launches;
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    int rc;
+    if (o.host_buffers) {
+        StagedGraph sg;
+        DBuf<int32_t> dS, dpart;
+        DBuf<double> dbc;
+        const int32_t *pS = nullptr, *pp = nullptr;
+        rc = stage_graph(c, g, sg);
+        if (!rc) rc = stage_in(c, dS, S, nS, &pS);
+        if (!rc) rc = stage_in(c, dpart, part, g->n, &pp);
+        if (!rc && !dbc.alloc(c, g->n)) rc = BCPP_ENOMEM;
+        if (!rc) rc = brandes_pp_dev(c, &sg.g, pS, nS, pp, k, o, dbc.p, stats);
+        if ((rc == BCPP_OK || rc == BCPP_EOVERFLOW_SIGMA) && g->n > 0 &&
+            to_host(c, bc_out, dbc.p, g->n) != BCPP_OK)
+            rc = BCPP_ECUDA;
+    } else {
+        rc = brandes_pp_dev(c, g, S, nS, part, k, o, bc_out, stats);
+    }
+    if (stats) stats->kernel_launches = c->launches - l0;
+    return rc;
+}
+
+int bcpp_brandes_batched(bcpp_ctx* c, int32_t num_graphs, const int64_t* graph_node_ptr, const bcpp_graph* arena,
+                         const bcpp_opts* opts, double* bc_out, bcpp_stats* stats) {
+    if (!c || !arena || !graph_node_ptr || num_graphs < 0) return BCPP_EINVAL;
+    const bcpp_opts o = opts_or_default(opts);
+    const int64_t l0 = c->launches;
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    int rc;
+    std::vector<int64_t> hptr((size_t)num_graphs + 1);
+    if (o.host_buffers) {
+        std::memcpy(hptr.data(), graph_node_ptr, hptr.size() * sizeof(int64_t));
+        StagedGraph sg;
+        DBuf<int64_t> dptr;
+        DBuf<double> dbc;
+        const int64_t* pptr = nullptr;
+        rc = stage_graph(c, arena, sg);
+        if (!rc) rc = stage_in(c, dptr, graph_node_ptr, (int64_t)num_graphs + 1, &pptr);
+        if (!rc && !dbc.alloc(c, arena->n)) rc = BCPP_ENOMEM;
+        if (!rc) rc = batched_dev(c, num_graphs, pptr, hptr.data(), &sg.g, o, dbc.p, stats);
+        if ((rc == BCPP_OK || rc == BCPP_EOVERFLOW_SIGMA) && arena->n > 0 &&
+            to_host(c, bc_out, dbc.p, arena->n) != BCPP_OK)
+            rc = BCPP_ECUDA;
+    } else {
+        rc = to_host(c, hptr.data(), graph_node_ptr, (int64_t)num_graphs + 1);
+        if (!rc) rc = batched_dev(c, num_graphs, graph_node_ptr, hptr.data(), arena, o, bc_out, stats);
+    }
+    if (stats) stats->kernel_launches = c->launches - l0;
+    return rc;
+}
+
+int bcpp_sssp(bcpp_ctx* c, const bcpp_graph* g, const int32_t* src, int32_t nsrc, int32_t* dist_out,
+              uint64_t* sigma_out, const bcpp_opts* opts) {
+    if (!c || !g) return BCPP_EINVAL;
+    const bcpp_opts o = opts_or_default(opts);
+    if (o.host_buffers) {
+        StagedGraph sg;
+        DBuf<int32_t> dsrc, dd;
+        DBuf<uint64_t> ds;
+        const int32_t* ps = nullptr;
+        int rc = stage_graph(c, g, sg);
+        if (!rc) rc = stage_in(c, dsrc, src, nsrc, &ps);
+        const int64_t cnt = (int64_t)nsrc * g->n;
+        if (!rc && (!dd.alloc(c, cnt) || !ds.alloc(c, cnt))) rc = BCPP_ENOMEM;
+        if (!rc) rc = sssp_dev(c, &sg.g, ps, nsrc, dd.p, ds.p, o);
+        if ((rc == BCPP_OK || rc == BCPP_EOVERFLOW_SIGMA) && cnt > 0) {
+            if (to_host(c, dist_out, dd.p, cnt) || to_host(c, sigma_out, ds.p, cnt)) rc = BCPP_ECUDA;
+        }
+        return rc;
+    }
+    return sssp_dev(c, g, src, nsrc, dist_out, sigma_out, o);
+}
+
+int bcpp_skeleton(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, const int32_t* part, int32_t k,
+                  int32_t* sk_nodes_out, int32_t* n_sk_out, int64_t cap_arcs, int32_t* au, int32_t* av, int32_t* aw,
+                  uint64_t* amu, int64_t* n_arcs_out, const bcpp_opts* opts) {
+    if (!c || !g) return BCPP_EINVAL;
+    const bcpp_opts o = opts_or_default(opts);
+    if (o.host_buffers) {
+        StagedGraph sg;
+        DBuf<int32_t> dS, dpart;
+        const int32_t *pS = nullptr, *pp = nullptr;
+        int rc = stage_graph(c, g, sg);
+        if (!rc) rc = stage_in(c, dS, S, nS, &pS);
+        if (!rc) rc = stage_in(c, dpart, part, g->n, &pp);
+        if (!rc)
+            rc = skeleton_dev(c, &sg.g, pS, nS, pp, k, sk_nodes_out, n_sk_out, cap_arcs, au, av, aw, amu, n_arcs_out, o,
+                              true);
+        return rc;
+    }
+    return skeleton_dev(c, g, S, nS, part, k, sk_nodes_out, n_sk_out, cap_arcs, au, av, aw, amu, n_arcs_out, o, false);
+}
+
+}  // extern "C"

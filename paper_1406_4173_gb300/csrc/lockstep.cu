@@ -1,0 +1,359 @@
+// Lockstep multi-source Brandes kernel (see lockstep.cuh for the layout and the modes).
+//
+// Forward (Sec. 3, Eq. 2; Sec. 4, Eq. 11; Dijkstra_SK Eq. 10): a node u settled at distance
+// D on some lanes pulls its path count from the in-neighbours v with d(v) + w(v,u) = D
+// (sigma(s,u) = sum sigma(s,v) * m(v,u)), then relaxes its out-arcs: an improved tentative
+// distance D + w marks the head in bucket (D + w) mod nb.  Weights are >= 1, so every parent
+// is settled in an earlier step and its count is final when it is read.
+// Backward (Eq. 7 / Eq. 12): steps are replayed in reverse; u on lane s gets
+// delta(s|u) = sigma(s,u) * sum over successors v (d(v) = d(u) + w) of m(u,v) * c(s,v) with
+// c(s,v) = (I_{v in S} + delta(s|v)) / sigma(s,v), stores c(s,u), and its dependency is
+// added (u != s) into the slot's partial betweenness.
+#include "lockstep.cuh"
+
+namespace bcpp {
+
+namespace {
+
+constexpr int UNROLL = 4;
+
+__device__ __forceinline__ void mark_bucket(const LsParams& P, uint32_t* bm, uint8_t* bflag, int64_t bm_words,
+                                            int v, int32_t nd, int* s_maxpush) {
+    const int bk = nd % P.nb;
+    const uint32_t bit = 1u << (v & 31);
+    uint32_t old = atomicOr(&bm[(int64_t)bk * bm_words + (v >> 5)], bit);
+    if (!(old & bit)) {
+        bflag[bk] = 1;
+        atomicMax(s_maxpush, nd);
+    }
+}
+
+// Visit the arcs [a0, a1) of one row: fetch 32 heads/weights/multiplicities per coalesced
+// load, broadcast them by shuffle, and load UNROLL distance rows before using them.
+template <class F>
+__device__ __forceinline__ void for_arcs(const int32_t* __restrict__ col, const int32_t* __restrict__ w,
+                                         const uint64_t* __restrict__ mu, int64_t a0, int64_t a1,
+                                         const int32_t* d, int lane, F&& f) {
+    for (int64_t c0 = a0; c0 < a1; c0 += 32) {
+        const int cnt = (int)min((int64_t)32, a1 - c0);
+        int32_t mv = 0, mw = 1;
+        uint64_t mm = 1;
+        if (lane < cnt) {
+            mv = __ldg(col + c0 + lane);
+            if (w) mw = __ldg(w + c0 + lane);
+            if (mu) mm = __ldg(mu + c0 + lane);
+        }
+        for (int j = 0; j < cnt; j += UNROLL) {
+            int32_t vv[UNROLL], ww[UNROLL], dv[UNROLL];
+            uint64_t mk[UNROLL];
+#pragma unroll
+            for (int k = 0; k < UNROLL; k++) {
+                vv[k] = __shfl_sync(FULL, mv, (j + k) & 31);
+                ww[k] = w ? __shfl_sync(FULL, mw, (j + k) & 31) : 1;
+                mk[k] = mu ? shfl_u64(mm, (j + k) & 31) : 1ull;
+            }
+#pragma unroll
+            for (int k = 0; k < UNROLL; k++)
+                dv[k] = (j + k < cnt) ? d[(int64_t)vv[k] * LS_LANES + lane] : DINF;
+#pragma unroll
+            for (int k = 0; k < UNROLL; k++)
+                if (j + k < cnt) f(vv[k], ww[k], mk[k], dv[k]);
+        }
+    }
+}
+
+template <typename DT, bool FUSED>
+__global__ void __launch_bounds__(LS_THREADS, 2)
+ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __restrict__ items, int nitems) {
+    __shared__ int s_item, s_pos, s_next, s_D, s_done, s_maxpush, s_nsteps, s_err, s_end;
+    const int lane = threadIdx.x & 31;
+    const int slot = blockIdx.x;
+
+    int32_t* d = W.d + (int64_t)slot * W.cap_n * LS_LANES;
+    uint64_t* sg = W.sg + (int64_t)slot * W.cap_n * LS_LANES;
+    DT* dl = reinterpret_cast<DT*>(W.dl) + (int64_t)slot * W.cap_n * LS_LANES;
+    int32_t* order = W.order + (int64_t)slot * W.cap_order;
+    int32_t* step_d = W.step_d + (int64_t)slot * W.cap_steps;
+    int32_t* step_beg = W.step_beg + (int64_t)slot * W.cap_steps;
+    uint32_t* bm = W.bm + (int64_t)slot * P.nb * W.bm_words;
+    uint8_t* bflag = W.bflag + (int64_t)slot * P.nb;
+    double* bcs = W.bc_sum ? W.bc_sum + (int64_t)slot * W.cap_bc : nullptr;
+    double* bcc = W.bc_cmp ? W.bc_cmp + (int64_t)slot * W.cap_bc : nullptr;
+
+    bool first = true;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            if (P.items_static) s_item = first ? slot : nitems;
+            else s_item = atomicAdd(P.item_counter, 1);
+        }
+        first = false;
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        const LsItem I = items[it];
+        const int64_t base = A.node_off[I.g];
+        const int32_t n = (int32_t)(A.node_off[I.g + 1] - base);
+        const int64_t* rp = A.rp + base;
+        const int64_t* irp = A.irp + base;
+        const int32_t nf = P.nfront ? P.nfront[I.g] : 0;
+        const bool unit = (A.w == nullptr);
+        const int32_t my_src = lane < I.nsrc ? P.srcs[I.src_off + lane] : -1;
+
+        // sources: d = 0, sigma = 1, bucket 0
+        if (threadIdx.x < 32) {
+            if (my_src >= 0) {
+                d[(int64_t)my_src * LS_LANES + lane] = 0;
+                sg[(int64_t)my_src * LS_LANES + lane] = 1;
+                atomicOr(&bm[my_src >> 5], 1u << (my_src & 31));
+            }
+        }
+        if (threadIdx.x == 0) {
+            bflag[0] = 1;
+            s_pos = 0; s_D = 0; s_maxpush = 0; s_nsteps = 0; s_err = 0;
+        }
+        __syncthreads();
+
+        // ------------------------------------------------------------------ forward
+        for (;;) {
+            if (threadIdx.x == 0) {
+                int D = s_D;
+                while (D <= s_maxpush && bflag[D % P.nb] == 0) D++;
+                s_D = D;
+                s_done = (D > s_maxpush) || s_err;
+                if (!s_done) {
+                    bflag[D % P.nb] = 0;
+                    if (s_nsteps >= W.cap_steps) {
+                        s_err = 1; s_done = 1;
+                    } else {
+                        step_d[s_nsteps] = D;
+                        step_beg[s_nsteps] = s_pos;
+                        s_next = s_pos;
+                    }
+                }
+            }
+            __syncthreads();
+            if (s_done) break;
+            const int32_t D = s_D;
+            // collect bucket D into the order list
+            {
+                uint32_t* bmD = bm + (int64_t)(D % P.nb) * W.bm_words;
+                const int nwords = (n + 31) >> 5;
+                const int nwr = (nwords + 31) & ~31;
+                for (int wi = threadIdx.x; wi < nwr; wi += LS_THREADS) {
+                    uint32_t x = wi < nwords ? bmD[wi] : 0u;
+                    if (x) bmD[wi] = 0u;
+                    const int c = __popc(x);
+                    const int incl = warp_incl_scan(c, lane);
+                    const int tot = __shfl_sync(FULL, incl, 31);
+                    int bpos = 0;
+                    if (lane == 31 && tot) bpos = atomicAdd(&s_pos, tot);
+                    bpos = __shfl_sync(FULL, bpos, 31);
+                    if (tot && bpos + tot > W.cap_order) {
+                        if (lane == 0) atomicExch(&s_err, 1);
+                        continue;
+                    }
+                    int p = bpos + incl - c;
+                    while (x) {
+                        const int b = __ffs(x) - 1;
+                        x &= x - 1;
+                        order[p++] = wi * 32 + b;
+                    }
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) s_end = min(s_pos, (int)W.cap_order);
+            __syncthreads();
+            if (s_err) break;
+            const int end = s_end;
+            // settle the nodes of step D
+            for (;;) {
+                int e = 0;
+                if (lane == 0) e = atomicAdd(&s_next, 1);
+                e = __shfl_sync(FULL, e, 0);
+                if (e >= end) break;
+                const int u = order[e];
+                const int32_t du = d[(int64_t)u * LS_LANES + lane];
+                const bool act = (du == D);
+                if (!__ballot_sync(FULL, act)) continue;
+                bool ovf = false;
+                uint64_t acc = 0;
+                const bool pull = act && D > 0;
+                auto relax = [&](int32_t v, int32_t wv, int32_t dv) {
+                    const int64_t nd64 = (int64_t)D + wv;
+                    const int32_t nd = nd64 < DINF ? (int32_t)nd64 : DINF;
+                    const bool imp = act && nd < dv;
+                    if (__ballot_sync(FULL, imp)) {
+                        bool nw = false;
+                        if (imp) {
+                            int32_t* pd = &d[(int64_t)v * LS_LANES + lane];
+                            if (unit) { *pd = nd; nw = true; }
+                            else nw = nd < atomicMin(pd, nd);
+                        }
+                        const unsigned nm = __ballot_sync(FULL, nw);
+                        if (nm && lane == __ffs(nm) - 1) mark_bucket(P, bm, bflag, W.bm_words, v, nd, &s_maxpush);
+                    }
+                };
+                if (FUSED) {
+                    for_arcs(A.col, A.w, A.mu, rp[u], rp[u + 1], d, lane,
+                             [&](int32_t v, int32_t wv, uint64_t m, int32_t dv) {
+                                 if (pull && dv < D && dv + wv == D && (v >= nf || dv == 0))
+                                     acc = madd_ck(acc, sg[(int64_t)v * LS_LANES + lane], m, ovf);
+                                 relax(v, wv, dv);
+                             });
+                } else {
+                    if (D > 0)
+                        for_arcs(A.icol, A.iw, A.imu, irp[u], irp[u + 1], d, lane,
+                                 [&](int32_t v, int32_t wv, uint64_t m, int32_t dv) {
+                                     if (pull && dv < D && dv + wv == D && (v >= nf || dv == 0))
+                                         acc = madd_ck(acc, sg[(int64_t)v * LS_LANES + lane], m, ovf);
+                                 });
+                    for_arcs(A.col, A.w, A.mu, rp[u], rp[u + 1], d, lane,
+                             [&](int32_t v, int32_t wv, uint64_t, int32_t dv) { relax(v, wv, dv); });
+                }
+                if (pull) sg[(int64_t)u * LS_LANES + lane] = acc;
+                if (__any_sync(FULL, ovf) && lane == 0) atomicOr(&P.flags[FLAG_SIGMA_OVF], 1u);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) { s_nsteps++; s_D = D + 1; }
+        }
+        __syncthreads();
+        const int nsteps = s_nsteps;
+        const int olen = min(s_pos, (int)W.cap_order);
+        if (s_err) {
+            // a list outgrew its bound: report it and leave the slot clean for the next batch
+            if (threadIdx.x == 0) atomicOr(&P.flags[FLAG_CAPACITY], 1u);
+            for (int64_t i = threadIdx.x; i < (int64_t)n * LS_LANES; i += LS_THREADS) d[i] = DINF;
+            for (int64_t i = threadIdx.x; i < (int64_t)P.nb * W.bm_words; i += LS_THREADS) bm[i] = 0u;
+            for (int i = threadIdx.x; i < P.nb; i += LS_THREADS) bflag[i] = 0;
+            if (P.mode == LS_SKEL && threadIdx.x == 0) {
+                W.hdr[slot * 4 + 0] = 0; W.hdr[slot * 4 + 1] = 0; W.hdr[slot * 4 + 2] = it;
+            }
+            __syncthreads();
+            continue;
+        }
+
+        if (P.mode == LS_BRANDES || P.mode == LS_SKEL) {
+            // -------------------------------------------------------------- backward
+            for (int st = nsteps - 1; st >= 0; st--) {
+                if (threadIdx.x == 0) s_next = step_beg[st];
+                __syncthreads();
+                const int32_t D = step_d[st];
+                const int end = (st + 1 < nsteps) ? step_beg[st + 1] : olen;
+                for (;;) {
+                    int e = 0;
+                    if (lane == 0) e = atomicAdd(&s_next, 1);
+                    e = __shfl_sync(FULL, e, 0);
+                    if (e >= end) break;
+                    const int u = order[e];
+                    const int32_t du = d[(int64_t)u * LS_LANES + lane];
+                    const bool act = (du == D);
+                    if (!__ballot_sync(FULL, act)) continue;
+                    DT acc = (DT)0;
+                    for_arcs(A.col, A.w, A.mu, rp[u], rp[u + 1], d, lane,
+                             [&](int32_t v, int32_t wv, uint64_t m, int32_t dv) {
+                                 if (act && dv != DINF && (int64_t)dv == (int64_t)D + wv)
+                                     acc += (DT)m * dl[(int64_t)v * LS_LANES + lane];
+                             });
+                    double contrib = 0.0;
+                    if (act) {
+                        const DT sd = (DT)sg[(int64_t)u * LS_LANES + lane];
+                        const DT delta = sd * acc;
+                        const DT is_t = P.in_s ? (DT)P.in_s[base + u] : (DT)1;
+                        dl[(int64_t)u * LS_LANES + lane] = (is_t + delta) / sd;
+                        if (u != my_src) contrib = (double)delta;
+                    }
+                    const double tot = warp_sum(contrib);
+                    if (lane == 0 && bcs && tot != 0.0) {
+                        const int64_t ix = P.bc_map ? (int64_t)P.bc_map[base + u] : base + u;
+                        double s = bcs[ix], c = bcc[ix];
+                        neumaier_add(s, c, tot);
+                        bcs[ix] = s;
+                        bcc[ix] = c;
+                    }
+                }
+                __syncthreads();
+            }
+        } else if (P.mode == LS_TABLE) {
+            // -------------------------------------------------------------- tables d_i[v][f], sigma_i[v][f]
+            const int64_t t0 = P.toff[I.g];
+            const int warp = threadIdx.x >> 5;
+            for (int v = warp; v < n; v += LS_THREADS / 32) {
+                if (lane < I.nsrc) {
+                    const int32_t dv = d[(int64_t)v * LS_LANES + lane];
+                    const int64_t o = t0 + (int64_t)v * nf + I.aux + lane;
+                    P.td[o] = dv;
+                    P.ts[o] = dv == DINF ? 0ull : sg[(int64_t)v * LS_LANES + lane];
+                }
+            }
+            __syncthreads();
+        } else if (P.mode == LS_SSSP) {
+            const int warp = threadIdx.x >> 5;
+            for (int v = warp; v < n; v += LS_THREADS / 32) {
+                if (lane < I.nsrc) {
+                    const int32_t dv = d[(int64_t)v * LS_LANES + lane];
+                    const int64_t o = (int64_t)(I.src_off + lane) * P.dbg_n + v;
+                    P.dbg_d[o] = dv;
+                    P.dbg_s[o] = dv == DINF ? 0ull : sg[(int64_t)v * LS_LANES + lane];
+                }
+            }
+            __syncthreads();
+        }
+
+        if (P.mode == LS_SKEL) {
+            if (threadIdx.x == 0) {
+                W.hdr[slot * 4 + 0] = olen;
+                W.hdr[slot * 4 + 1] = nsteps;
+                W.hdr[slot * 4 + 2] = it;
+            }
+        } else {
+            // restore "unreached" on every touched row
+            const int warp = threadIdx.x >> 5;
+            for (int e = warp; e < olen; e += LS_THREADS / 32)
+                d[(int64_t)order[e] * LS_LANES + lane] = DINF;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void ls_reset_kernel(const LsSlots W) {
+    const int slot = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t* d = W.d + (int64_t)slot * W.cap_n * LS_LANES;
+    const int32_t* order = W.order + (int64_t)slot * W.cap_order;
+    const int olen = W.hdr[slot * 4 + 0];
+    for (int e = warp; e < olen; e += blockDim.x / 32) d[(int64_t)order[e] * LS_LANES + lane] = DINF;
+    __syncthreads();
+    if (threadIdx.x == 0) W.hdr[slot * 4 + 0] = 0;
+}
+
+__global__ void fill_i32_kernel(int32_t* p, int32_t v, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+}  // namespace
+
+void ls_launch(bool fp32_delta, bool fused, const LsArena& A, const LsParams& P, const LsSlots& W,
+               const LsItem* items, int nitems, int slots, cudaStream_t st) {
+    if (nitems <= 0 || slots <= 0) return;
+    if (fp32_delta) {
+        if (fused) ls_kernel<float, true><<<slots, LS_THREADS, 0, st>>>(A, P, W, items, nitems);
+        else ls_kernel<float, false><<<slots, LS_THREADS, 0, st>>>(A, P, W, items, nitems);
+    } else {
+        if (fused) ls_kernel<double, true><<<slots, LS_THREADS, 0, st>>>(A, P, W, items, nitems);
+        else ls_kernel<double, false><<<slots, LS_THREADS, 0, st>>>(A, P, W, items, nitems);
+    }
+}
+
+void ls_reset_launch(const LsSlots& W, int slots, cudaStream_t st) {
+    if (slots > 0) ls_reset_kernel<<<slots, 512, 0, st>>>(W);
+}
+
+void fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t st) {
+    if (n <= 0) return;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 65536) blocks = 65536;
+    fill_i32_kernel<<<(unsigned)blocks, 256, 0, st>>>(p, v, n);
+}
+
+}  // namespace bcpp

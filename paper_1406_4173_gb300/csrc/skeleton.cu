@@ -1,0 +1,401 @@
+// Build_SK steps (Sec. 3 "The skeleton graph", Sec. 4 Alg. 1-2), the Centrality step
+// (Sec. 4, Eq. 13) and the combination of partial betweenness.
+#include "skeleton.cuh"
+
+namespace bcpp {
+
+namespace {
+
+inline unsigned grid_for(int64_t work, int threads, int max_blocks = 16384) {
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (unsigned)b;
+}
+
+#define GRID_STRIDE(i, n) for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); \
+                               i += (int64_t)gridDim.x * blockDim.x)
+#define WARP_STRIDE(j, n)                                                        \
+    const int lane = threadIdx.x & 31;                                           \
+    const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; \
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;               \
+    for (int64_t j = warp_id; j < (n); j += nwarps)
+
+__global__ void partp_copy_kernel(int32_t n, const int32_t* part, int32_t k, int32_t* partp, uint32_t* flags) {
+    GRID_STRIDE(v, n) {
+        const int32_t p = part[v];
+        if (p < 0 || p >= k) flag_invalid(flags, WHY_PART);
+        partp[v] = p;
+    }
+}
+
+__global__ void partp_targets_kernel(const int32_t* S, int32_t nS, int32_t k, int32_t* partp) {
+    GRID_STRIDE(j, nS) partp[S[j]] = k + (int32_t)j;
+}
+
+__global__ void frontier_kernel(int32_t n, const int64_t* rp, const int32_t* col, const int32_t* partp, uint8_t* fr) {
+    WARP_STRIDE(u, n) {
+        const int32_t pu = partp[u];
+        bool any = false;
+        for (int64_t p = rp[u] + lane; p < rp[u + 1]; p += 32) {
+            const int32_t v = col[p];
+            if (partp[v] != pu) { fr[v] = 1; any = true; }
+        }
+        if (__any_sync(FULL, any) && lane == 0) fr[u] = 1;
+    }
+}
+
+__global__ void group_keys_kernel(int32_t n, const int32_t* partp, const uint8_t* fr, uint64_t* keys, uint32_t* vals) {
+    GRID_STRIDE(v, n) {
+        keys[v] = 2ull * (uint64_t)partp[v] + (fr[v] ? 0ull : 1ull);
+        vals[v] = (uint32_t)v;
+    }
+}
+
+__device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* a, int64_t n, uint64_t x) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void segments_kernel(const uint64_t* keys, int32_t n, int32_t kp, int32_t* pstart, int32_t* nf) {
+    GRID_STRIDE(i, (int64_t)kp + 1) {
+        const int64_t a = lower_bound_u64(keys, n, 2ull * (uint64_t)i);
+        pstart[i] = (int32_t)a;
+        if (i < kp) nf[i] = (int32_t)(lower_bound_u64(keys, n, 2ull * (uint64_t)i + 1ull) - a);
+    }
+}
+
+__global__ void local_ids_kernel(int32_t n, const uint32_t* pnodes, const int32_t* partp, const int32_t* pstart,
+                                 const int32_t* nf, const int32_t* skbase, int32_t* loc, int32_t* skid,
+                                 int32_t* sknode) {
+    GRID_STRIDE(j, n) {
+        const int32_t v = (int32_t)pnodes[j];
+        const int32_t i = partp[v];
+        const int32_t li = (int32_t)j - pstart[i];
+        loc[v] = li;
+        if (li < nf[i]) {
+            const int32_t x = skbase[i] + li;
+            skid[v] = x;
+            sknode[x] = v;
+        } else {
+            skid[v] = -1;
+        }
+    }
+}
+
+__global__ void local_count_kernel(int32_t n, const uint32_t* pnodes, const int64_t* rp, const int32_t* col,
+                                   const int32_t* partp, int64_t* cnt) {
+    WARP_STRIDE(j, n) {
+        const int32_t v = (int32_t)pnodes[j];
+        const int32_t pv = partp[v];
+        int c = 0;
+        for (int64_t p = rp[v] + lane; p < rp[v + 1]; p += 32) c += (partp[col[p]] == pv);
+        c = warp_sum(c);
+        if (lane == 0) cnt[j] = c;
+    }
+}
+
+__global__ void local_fill_kernel(int32_t n, const uint32_t* pnodes, const int64_t* rp, const int32_t* col,
+                                  const uint32_t* w, const int32_t* partp, const int32_t* loc, const int64_t* lrp,
+                                  int32_t* lcol, int32_t* lw) {
+    WARP_STRIDE(j, n) {
+        const int32_t v = (int32_t)pnodes[j];
+        const int32_t pv = partp[v];
+        int64_t out = lrp[j];
+        for (int64_t p0 = rp[v]; p0 < rp[v + 1]; p0 += 32) {
+            const int64_t p = p0 + lane;
+            bool keep = false;
+            int32_t u = 0;
+            if (p < rp[v + 1]) { u = col[p]; keep = partp[u] == pv; }
+            const unsigned m = __ballot_sync(FULL, keep);
+            if (keep) {
+                const int64_t q = out + __popc(m & ((1u << lane) - 1u));
+                lcol[q] = loc[u];
+                if (lw) lw[q] = w ? (int32_t)w[p] : 1;
+            }
+            out += __popc(m);
+        }
+    }
+}
+
+// skeleton arcs of skeleton node x: R arcs (G row, other part) then clique arcs (exit table row)
+__global__ void sk_arcs_count_kernel(int32_t N, const int32_t* sknode, const int64_t* rp, const int32_t* col,
+                                     const int32_t* partp, const int32_t* loc, SkTables T, int64_t* cnt) {
+    WARP_STRIDE(x, N) {
+        const int32_t v = sknode[x];
+        const int32_t i = partp[v];
+        int c = 0;
+        for (int64_t p = rp[v] + lane; p < rp[v + 1]; p += 32) c += (partp[col[p]] != i);
+        const int32_t nfi = T.nf[i];
+        if (nfi >= 2) {
+            const int32_t fi = loc[v];
+            const int64_t row = T.toff[i] + (int64_t)fi * nfi;
+            for (int32_t q = lane; q < nfi; q += 32)
+                c += (q != fi && T.tdr[row + q] != DINF && T.tsr[row + q] != 0ull);
+        }
+        c = warp_sum(c);
+        if (lane == 0) cnt[x] = c;
+    }
+}
+
+__global__ void sk_arcs_fill_kernel(int32_t N, const int32_t* sknode, const int64_t* rp, const int32_t* col,
+                                    const uint32_t* w, const int32_t* partp, const int32_t* loc, const int32_t* skid,
+                                    SkTables T, const int64_t* skrp, int32_t* skcol, int32_t* skw, uint64_t* skmu,
+                                    unsigned long long* maxes) {
+    uint32_t wmax = 0;
+    unsigned long long mmax = 0;
+    WARP_STRIDE(x, N) {
+        const int32_t v = sknode[x];
+        const int32_t i = partp[v];
+        int64_t out = skrp[x];
+        for (int64_t p0 = rp[v]; p0 < rp[v + 1]; p0 += 32) {
+            const int64_t p = p0 + lane;
+            bool keep = false;
+            int32_t u = 0;
+            if (p < rp[v + 1]) { u = col[p]; keep = partp[u] != i; }
+            const unsigned m = __ballot_sync(FULL, keep);
+            if (keep) {
+                const int64_t q = out + __popc(m & ((1u << lane) - 1u));
+                const uint32_t wv = w ? w[p] : 1u;
+                skcol[q] = skid[u];
+                skw[q] = (int32_t)wv;
+                skmu[q] = 1ull;
+                wmax = max(wmax, wv);
+                mmax = max(mmax, 1ull);
+            }
+            out += __popc(m);
+        }
+        const int32_t nfi = T.nf[i];
+        if (nfi >= 2) {
+            const int32_t fi = loc[v];
+            const int64_t row = T.toff[i] + (int64_t)fi * nfi;
+            const int32_t xb = x - fi;   // skeleton id of the part's first frontier
+            for (int32_t q0 = 0; q0 < nfi; q0 += 32) {
+                const int32_t q = q0 + lane;
+                bool keep = false;
+                int32_t dq = 0;
+                uint64_t sq = 0;
+                if (q < nfi && q != fi) {
+                    dq = T.tdr[row + q];
+                    sq = T.tsr[row + q];
+                    keep = dq != DINF && sq != 0ull;
+                }
+                const unsigned m = __ballot_sync(FULL, keep);
+                if (keep) {
+                    const int64_t o = out + __popc(m & ((1u << lane) - 1u));
+                    skcol[o] = xb + q;
+                    skw[o] = dq;
+                    skmu[o] = sq;
+                    wmax = max(wmax, (uint32_t)dq);
+                    mmax = max(mmax, (unsigned long long)sq);
+                }
+                out += __popc(m);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        wmax = max(wmax, __shfl_xor_sync(FULL, wmax, o));
+        mmax = max(mmax, __shfl_xor_sync(FULL, mmax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&maxes[0], (unsigned long long)wmax);
+        atomicMax(&maxes[1], mmax);
+    }
+}
+
+__global__ void sk_transpose_kernel(int32_t N, const int64_t* rp, const int32_t* col, const int32_t* w,
+                                    const uint64_t* mu, int64_t* cursor, int32_t* tcol, int32_t* tw, uint64_t* tmu,
+                                    int pass) {
+    WARP_STRIDE(u, N) {
+        for (int64_t p = rp[u] + lane; p < rp[u + 1]; p += 32) {
+            const int32_t v = col[p];
+            if (pass == 0) {
+                atomicAdd((unsigned long long*)&cursor[v], 1ull);
+            } else {
+                const int64_t q = (int64_t)atomicAdd((unsigned long long*)&cursor[v], 1ull);
+                tcol[q] = (int32_t)u;
+                tw[q] = w[p];
+                tmu[q] = mu[p];
+            }
+        }
+    }
+}
+
+__global__ void gather_flags_kernel(int32_t N, const int32_t* sknode, const uint8_t* in_s, uint8_t* out) {
+    GRID_STRIDE(x, N) out[x] = in_s[sknode[x]];
+}
+
+// ordered compaction of targets that are skeleton nodes (single block, keeps S order)
+__global__ void target_ids_kernel(const int32_t* S, int32_t nS, const int32_t* skid, int32_t* out, int32_t* cnt) {
+    __shared__ int32_t base;
+    __shared__ int32_t wt[32];
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t c0 = 0; c0 < nS; c0 += blockDim.x) {
+        const int64_t j = c0 + threadIdx.x;
+        int32_t x = j < nS ? skid[S[j]] : -1;
+        const bool keep = x >= 0;
+        const unsigned m = __ballot_sync(FULL, keep);
+        if (lane == 0) wt[warp] = __popc(m);
+        __syncthreads();
+        int32_t pre = 0, tot = 0;
+        for (int w = 0; w < nw; w++) { if (w < warp) pre += wt[w]; tot += wt[w]; }
+        if (keep) out[base + pre + __popc(m & ((1u << lane) - 1u))] = x;
+        __syncthreads();
+        if (threadIdx.x == 0) base += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *cnt = base;
+}
+
+// One warp per (non-frontier node, slot): lanes are the slot's sources.  Forward: the
+// distance and count through the entry frontiers; backward: the dependency through the exit
+// frontiers that stay on a shortest path (Eq. 13).
+template <typename DT>
+__global__ void __launch_bounds__(256)
+centrality_kernel(const CentralityUnit* __restrict__ units, SkTables T, const uint32_t* __restrict__ pnodes,
+                  const int32_t* __restrict__ skbase, const int32_t* __restrict__ d_all,
+                  const uint64_t* __restrict__ sg_all, const DT* __restrict__ dl_all, int64_t cap_n,
+                  double* bc_sum, double* bc_cmp, int64_t cap_bc, uint32_t* flags) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const CentralityUnit U = units[blockIdx.x];
+    const int slot = blockIdx.y;
+    const int32_t i = U.part;
+    const int32_t nfi = T.nf[i];
+    const int64_t t0 = T.toff[i];
+    const int32_t ps = T.pstart[i];
+    const int64_t sb = skbase[i];
+    const int32_t* d = d_all + (int64_t)slot * cap_n * 32 + sb * 32;
+    const uint64_t* sg = sg_all + (int64_t)slot * cap_n * 32 + sb * 32;
+    const DT* dl = dl_all + (int64_t)slot * cap_n * 32 + sb * 32;
+    bool ovf = false;
+    for (int32_t vl = U.v0 + warp; vl < U.v1; vl += nw) {
+        const int32_t* te = T.td + t0 + (int64_t)vl * nfi;
+        const uint64_t* se = T.ts + t0 + (int64_t)vl * nfi;
+        const int32_t* tx = T.tdr + t0 + (int64_t)vl * nfi;
+        const uint64_t* sx = T.tsr + t0 + (int64_t)vl * nfi;
+        int64_t dv = DINF;
+        uint64_t sv = 0;
+        for (int32_t f = 0; f < nfi; f++) {
+            const int32_t dfv = te[f];
+            if (dfv == DINF) continue;
+            const int32_t dsf = d[(int64_t)f * 32 + lane];
+            if (dsf == DINF) continue;
+            const int64_t c = (int64_t)dsf + dfv;
+            if (c < dv) { dv = c; sv = 0; }
+            if (c == dv) sv = madd_ck(sv, sg[(int64_t)f * 32 + lane], se[f], ovf);
+        }
+        DT acc = (DT)0;
+        if (sv != 0) {
+            for (int32_t f = 0; f < nfi; f++) {
+                const int32_t dvf = tx[f];
+                if (dvf == DINF) continue;
+                const int32_t dsf = d[(int64_t)f * 32 + lane];
+                if (dsf == DINF || dv + dvf != (int64_t)dsf) continue;
+                acc += (DT)sx[f] * dl[(int64_t)f * 32 + lane];
+            }
+        }
+        const double delta = (double)((DT)sv * acc);
+        const double tot = warp_sum(delta);
+        if (lane == 0 && tot != 0.0) {
+            const int64_t ix = (int64_t)slot * cap_bc + pnodes[ps + vl];
+            double s = bc_sum[ix], c = bc_cmp[ix];
+            neumaier_add(s, c, tot);
+            bc_sum[ix] = s;
+            bc_cmp[ix] = c;
+        }
+    }
+    if (__any_sync(FULL, ovf) && lane == 0) atomicOr(&flags[FLAG_SIGMA_OVF], 1u);
+}
+
+__global__ void combine_kernel(const double* bc_sum, const double* bc_cmp, int nslots, int64_t cap_bc, int64_t n,
+                               double scale, double* out) {
+    GRID_STRIDE(v, n) {
+        double s = 0.0, c = 0.0;
+        for (int k = 0; k < nslots; k++) {
+            neumaier_add(s, c, bc_sum[(int64_t)k * cap_bc + v]);
+            neumaier_add(s, c, bc_cmp[(int64_t)k * cap_bc + v]);
+        }
+        out[v] = (s + c) * scale;
+    }
+}
+
+}  // namespace
+
+void sk_partition(int32_t n, const int32_t* part, int32_t k, const int32_t* S, int32_t nS, int32_t* partp,
+                  uint32_t* flags, cudaStream_t st) {
+    if (n > 0) partp_copy_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, part, k, partp, flags);
+    if (nS > 0) partp_targets_kernel<<<grid_for(nS, 256), 256, 0, st>>>(S, nS, k, partp);
+}
+void sk_frontiers(int32_t n, const int64_t* rp, const int32_t* col, const int32_t* partp, uint8_t* fr, cudaStream_t st) {
+    if (n > 0) frontier_kernel<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(n, rp, col, partp, fr);
+}
+void sk_group_keys(int32_t n, const int32_t* partp, const uint8_t* fr, uint64_t* keys, uint32_t* vals, cudaStream_t st) {
+    if (n > 0) group_keys_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, partp, fr, keys, vals);
+}
+void sk_segments(const uint64_t* keys, int32_t n, int32_t kp, int32_t* pstart, int32_t* nf, cudaStream_t st) {
+    segments_kernel<<<grid_for((int64_t)kp + 1, 256), 256, 0, st>>>(keys, n, kp, pstart, nf);
+}
+void sk_local_ids(int32_t n, const uint32_t* pnodes, const int32_t* partp, const int32_t* pstart, const int32_t* nf,
+                  const int32_t* skbase, int32_t* loc, int32_t* skid, int32_t* sknode, cudaStream_t st) {
+    if (n > 0) local_ids_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, pnodes, partp, pstart, nf, skbase, loc, skid, sknode);
+}
+void sk_local_count(int32_t n, const uint32_t* pnodes, const int64_t* rp, const int32_t* col, const int32_t* partp,
+                    int64_t* cnt, cudaStream_t st) {
+    if (n > 0) local_count_kernel<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(n, pnodes, rp, col, partp, cnt);
+}
+void sk_local_fill(int32_t n, const uint32_t* pnodes, const int64_t* rp, const int32_t* col, const uint32_t* w,
+                   const int32_t* partp, const int32_t* loc, const int64_t* lrp, int32_t* lcol, int32_t* lw,
+                   cudaStream_t st) {
+    if (n > 0)
+        local_fill_kernel<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(n, pnodes, rp, col, w, partp, loc, lrp, lcol, lw);
+}
+void sk_arcs_count(int32_t N, const int32_t* sknode, const int64_t* rp, const int32_t* col, const int32_t* partp,
+                   const int32_t* loc, SkTables T, int64_t* cnt, cudaStream_t st) {
+    if (N > 0) sk_arcs_count_kernel<<<grid_for((int64_t)N * 32, 256), 256, 0, st>>>(N, sknode, rp, col, partp, loc, T, cnt);
+}
+void sk_arcs_fill(int32_t N, const int32_t* sknode, const int64_t* rp, const int32_t* col, const uint32_t* w,
+                  const int32_t* partp, const int32_t* loc, const int32_t* skid, SkTables T, const int64_t* skrp,
+                  int32_t* skcol, int32_t* skw, uint64_t* skmu, unsigned long long* maxes, cudaStream_t st) {
+    if (N > 0)
+        sk_arcs_fill_kernel<<<grid_for((int64_t)N * 32, 256), 256, 0, st>>>(N, sknode, rp, col, w, partp, loc, skid, T,
+                                                                           skrp, skcol, skw, skmu, maxes);
+}
+void sk_transpose(int32_t N, const int64_t* rp, const int32_t* col, const int32_t* w, const uint64_t* mu,
+                  int64_t* cursor, int32_t* tcol, int32_t* tw, uint64_t* tmu, int pass, cudaStream_t st) {
+    if (N > 0)
+        sk_transpose_kernel<<<grid_for((int64_t)N * 32, 256), 256, 0, st>>>(N, rp, col, w, mu, cursor, tcol, tw, tmu, pass);
+}
+void sk_gather_flags(int32_t N, const int32_t* sknode, const uint8_t* in_s, uint8_t* out, cudaStream_t st) {
+    if (N > 0) gather_flags_kernel<<<grid_for(N, 256), 256, 0, st>>>(N, sknode, in_s, out);
+}
+void sk_target_ids(const int32_t* S, int32_t nS, const int32_t* skid, int32_t* out, int32_t* cnt, cudaStream_t st) {
+    target_ids_kernel<<<1, 1024, 0, st>>>(S, nS, skid, out, cnt);
+}
+
+void centrality_launch(bool fp32_delta, const CentralityUnit* units, int nunits, int nslots, SkTables T,
+                       const uint32_t* pnodes, const int32_t* skbase, const int32_t* d, const uint64_t* sg,
+                       const void* dl, int64_t cap_n, double* bc_sum, double* bc_cmp, int64_t cap_bc,
+                       uint32_t* flags, cudaStream_t st) {
+    if (nunits <= 0 || nslots <= 0) return;
+    dim3 grid(nunits, nslots);
+    if (fp32_delta)
+        centrality_kernel<float><<<grid, 256, 0, st>>>(units, T, pnodes, skbase, d, sg, (const float*)dl, cap_n,
+                                                        bc_sum, bc_cmp, cap_bc, flags);
+    else
+        centrality_kernel<double><<<grid, 256, 0, st>>>(units, T, pnodes, skbase, d, sg, (const double*)dl, cap_n,
+                                                         bc_sum, bc_cmp, cap_bc, flags);
+}
+
+void combine_launch(const double* bc_sum, const double* bc_cmp, int nslots, int64_t cap_bc, int64_t n, double scale,
+                    double* bc_out, cudaStream_t st) {
+    if (n > 0) combine_kernel<<<grid_for(n, 256), 256, 0, st>>>(bc_sum, bc_cmp, nslots, cap_bc, n, scale, bc_out);
+}
+
+}  // namespace bcpp

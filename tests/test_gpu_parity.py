@@ -1,0 +1,245 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle.
+
+Distances and uint64 path counts must match bit for bit; betweenness to a relative 1e-12 in
+FP64 mode and to FP32_TOL in FP32-delta mode (relative error max_v |x - ref| / max(|ref|, 1)).
+Sizes span several 32-source batches with a ragged last batch.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1406_4173_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+# FP32 dependencies: each delta(s|v) carries ~1e-7 relative rounding per DAG level; summed
+# over sources in FP64 the relative error stays well below this bound on these graphs.
+FP32_TOL = 2e-4
+INF32 = np.iinfo(np.int32).max
+
+
+@pytest.fixture(scope="module")
+def bc():
+    import torch
+    import paper_1406_4173_gb300 as m
+    from paper_1406_4173_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    return m
+
+
+def rel_err(x, ref):
+    x = np.asarray(x, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return float(np.max(np.abs(x - ref) / np.maximum(np.abs(ref), 1.0))) if x.size else 0.0
+
+
+def graphs():
+    out = [
+        ("planted-u1", gen.planted_partition(700, 7, 0.03, 0.002, seed=1)),
+        ("planted-uw", gen.planted_partition(600, 6, 0.03, 0.003, seed=2, wmax=9)),
+        ("chunglu-d1", gen.chung_lu_communities(800, [200] * 4, 2.3, 6.0, 0.85, seed=3, directed=True)),
+        ("chunglu-dw", gen.chung_lu_communities(800, [160] * 5, 2.3, 6.0, 0.85, seed=4, directed=True, wmax=16)),
+        ("er-sparse-u", gen.erdos_renyi(900, 1.5 / 900, seed=5)),           # many components
+        ("chunglu-u-hub", gen.chung_lu_communities(1500, [300] * 5, 2.1, 8.0, 0.9, seed=6)),
+    ]
+    return out
+
+
+GRAPHS = graphs()
+IDS = [g[0] for g in GRAPHS]
+
+
+# ----------------------------------------------------------------------------- d and sigma
+@pytest.mark.parametrize("name,g", GRAPHS, ids=IDS)
+def test_sssp_bit_exact(bc, name, g):
+    G = bc.graph_from_edgelist(g)
+    src = np.unique(np.concatenate([np.arange(0, g.n, max(1, g.n // 67)), [g.n - 1]])).astype(np.int32)
+    dist, sig = bc.sssp(G, src, allow_overflow=True)
+    dist = dist.cpu().numpy()
+    sig = sig.cpu().numpy().view(np.uint64)
+    for i, s in enumerate(src):
+        d_ref, s_ref, _ = oracle.sssp(g, int(s))
+        assert np.array_equal(dist[i], d_ref), (name, s)
+        assert np.array_equal(sig[i], s_ref), (name, s)
+
+
+def test_sigma_uint64_limit_and_overflow(bc):
+    g = gen.grid(34, 34)
+    dist, sig = bc.sssp(bc.graph_from_edgelist(g), np.array([0], np.int32))
+    assert int(sig.cpu().numpy().view(np.uint64)[0, -1]) == math.comb(66, 33)
+    g = gen.grid(35, 35)
+    with pytest.raises(bc.SigmaOverflow):
+        bc.sssp(bc.graph_from_edgelist(g), np.array([0], np.int32))
+
+
+# ----------------------------------------------------------------------------- plain Brandes
+@pytest.mark.parametrize("name,g", GRAPHS, ids=IDS)
+def test_brandes_all_targets(bc, name, g):
+    G = bc.graph_from_edgelist(g)
+    ref, _ = oracle.brandes(g)
+    got = bc.brandes(G).cpu().numpy()
+    assert rel_err(got, ref) < FP64_TOL
+    got32 = bc.brandes(G, precision="fp32").cpu().numpy()
+    assert rel_err(got32, ref) < FP32_TOL
+
+
+@pytest.mark.parametrize("name,g", GRAPHS, ids=IDS)
+def test_brandes_target_subset(bc, name, g):
+    G = bc.graph_from_edgelist(g)
+    S = gen.sample_targets(g.n, 75, seed=11)
+    ref, _ = oracle.brandes(g, S)
+    got = bc.brandes(G, S).cpu().numpy()
+    assert rel_err(got, ref) < FP64_TOL
+    # unhalved (ordered pairs)
+    ref_o, _ = oracle.brandes(g, S, halve=False)
+    got_o = bc.brandes(G, S, halve=False).cpu().numpy()
+    assert rel_err(got_o, ref_o) < FP64_TOL
+
+
+@pytest.mark.parametrize("n", [2, 3, 33, 65])
+def test_brandes_closed_forms(bc, n):
+    i = np.arange(n)
+    got = bc.brandes(bc.graph_from_edgelist(gen.path(n))).cpu().numpy()
+    assert rel_err(got, i * (n - 1 - i)) < FP64_TOL
+    if n >= 3:
+        got = bc.brandes(bc.graph_from_edgelist(gen.star(n))).cpu().numpy()
+        ref = np.zeros(n)
+        ref[0] = (n - 1) * (n - 2) / 2
+        assert rel_err(got, ref) < FP64_TOL
+        got = bc.brandes(bc.graph_from_edgelist(gen.cycle(n))).cpu().numpy()
+        k = n // 2
+        assert rel_err(got, np.full(n, k * (k - 1) / 2 if n % 2 else (k - 1) ** 2 / 2)) < FP64_TOL
+
+
+def test_brandes_degenerate_inputs(bc):
+    import torch
+    g = gen.erdos_renyi(50, 0.05, seed=9)
+    G = bc.graph_from_edgelist(g)
+    # |S| < 2: all zeros
+    assert torch.all(bc.brandes(G, np.array([3], np.int32)) == 0)
+    # a graph without arcs
+    e = gen.EdgeList(n=10, src=np.zeros(0, np.int32), dst=np.zeros(0, np.int32))
+    assert torch.all(bc.brandes(bc.graph_from_edgelist(e)) == 0)
+    # isolated targets
+    S = np.array([0, 1, 2, 49], np.int32)
+    ref, _ = oracle.brandes(g, S)
+    assert rel_err(bc.brandes(G, S).cpu().numpy(), ref) < FP64_TOL
+
+
+def test_brandes_rejects_bad_targets(bc):
+    G = bc.graph_from_edgelist(gen.path(10))
+    with pytest.raises(bc.BcppError):
+        bc.brandes(G, np.array([1, 1], np.int32))
+    with pytest.raises(bc.BcppError):
+        bc.brandes(G, np.array([1, 10], np.int32))
+
+
+# ----------------------------------------------------------------------------- CSR build / validation
+def test_csr_build_matches_definition(bc):
+    g = gen.chung_lu_communities(500, [100] * 5, 2.3, 6.0, 0.8, seed=12, wmax=7)
+    G = bc.graph_from_edgelist(g)
+    rp = G.row_ptr.cpu().numpy()
+    col = G.col.cpu().numpy()
+    w = G.w.cpu().numpy().view(np.uint32)
+    arcs = sorted([(int(a), int(b), int(c)) for a, b, c in zip(g.src, g.dst, g.w)] +
+                  [(int(b), int(a), int(c)) for a, b, c in zip(g.src, g.dst, g.w)])
+    got = [(u, int(col[p]), int(w[p])) for u in range(g.n) for p in range(rp[u], rp[u + 1])]
+    assert got == arcs
+    bc.csr_validate(G)
+
+
+@pytest.mark.parametrize("case", ["self_loop", "duplicate", "reverse_duplicate", "zero_weight", "range"])
+def test_csr_build_rejects(bc, case):
+    src, dst, w = np.array([0, 1, 2], np.int32), np.array([1, 2, 3], np.int32), None
+    if case == "self_loop":
+        dst[2] = 2
+    elif case == "duplicate":
+        src, dst = np.array([0, 0], np.int32), np.array([1, 1], np.int32)
+    elif case == "reverse_duplicate":
+        src, dst = np.array([0, 1], np.int32), np.array([1, 0], np.int32)
+    elif case == "zero_weight":
+        w = np.array([1, 0, 2], np.uint32)
+    elif case == "range":
+        dst[2] = 4
+    with pytest.raises(bc.BcppError):
+        bc.csr_build(4, src, dst, w, directed=False)
+
+
+# ----------------------------------------------------------------------------- Brandes++
+def partitions(g, seed):
+    rng = np.random.default_rng(seed)
+    return {
+        "planted": g.part,
+        "random": rng.integers(0, 5, g.n).astype(np.int32),
+        "single": np.zeros(g.n, np.int32),
+        "singletons": np.arange(g.n, dtype=np.int32),
+    }
+
+
+@pytest.mark.parametrize("name,g", GRAPHS[:4] + GRAPHS[5:], ids=IDS[:4] + IDS[5:])
+def test_brandes_pp_equals_oracle(bc, name, g):
+    G = bc.graph_from_edgelist(g)
+    part_all = partitions(g, 5)
+    for S in (gen.sample_targets(g.n, 70, seed=13), None):
+        ref, _ = oracle.brandes(g, S)
+        for pname, part in part_all.items():
+            got = bc.brandes_pp(G, S, part).cpu().numpy()
+            assert rel_err(got, ref) < FP64_TOL, (pname, S is None)
+    S = gen.sample_targets(g.n, 70, seed=14)
+    ref, _ = oracle.brandes(g, S)
+    got32 = bc.brandes_pp(G, S, g.part, precision="fp32").cpu().numpy()
+    assert rel_err(got32, ref) < FP32_TOL
+
+
+@pytest.mark.parametrize("name,g", GRAPHS[:4], ids=IDS[:4])
+def test_skeleton_matches_oracle(bc, name, g):
+    G = bc.graph_from_edgelist(g)
+    S = gen.sample_targets(g.n, 40, seed=15)
+    nodes, (au, av, aw, amu) = bc.skeleton(G, S, g.part)
+    onodes, (ou, ov, ow, omu), _ = oracle.skeleton(g, S, g.part)
+    assert np.array_equal(nodes, onodes)
+    got = sorted(zip(au.tolist(), av.tolist(), aw.tolist(), amu.tolist()))
+    ref = sorted(zip(ou.tolist(), ov.tolist(), ow.tolist(), omu.tolist()))
+    assert got == ref
+
+
+def test_brandes_pp_stats(bc):
+    g = gen.planted_partition(600, 6, 0.04, 0.002, seed=16)
+    S = gen.sample_targets(g.n, 50, seed=16)
+    G = bc.graph_from_edgelist(g)
+    _, st = bc.brandes_pp(G, S, g.part, stats=True)
+    _, _, ost = oracle.brandes_pp(g, S, g.part)
+    assert st["skel_nodes"] == ost["N"] and st["skel_edges"] == ost["M"]
+    assert st["k"] == ost["k"] and st["lcs"] == ost["LCS"]
+
+
+# ----------------------------------------------------------------------------- batched graphs
+def test_batched_graphs(bc):
+    gs = [gen.erdos_renyi(int(n), 6.0 / (n - 1), seed=100 + i) for i, n in
+          enumerate([64, 100, 37, 512, 2, 1, 300, 90, 129, 33, 700])]
+    arena = bc.build_arena(gs)
+    got = bc.brandes_batched(arena).cpu().numpy()
+    got32 = bc.brandes_batched(arena, precision="fp32").cpu().numpy()
+    off = arena.node_ptr_host
+    for i, g in enumerate(gs):
+        ref, _ = oracle.brandes(g)
+        assert rel_err(got[off[i]:off[i + 1]], ref) < FP64_TOL, i
+        assert rel_err(got32[off[i]:off[i + 1]], ref) < FP32_TOL, i
+
+
+# ----------------------------------------------------------------------------- host buffers
+def test_host_buffer_calls_match_device(bc):
+    g = gen.planted_partition(500, 5, 0.04, 0.003, seed=17, wmax=5)
+    S = gen.sample_targets(g.n, 60, seed=17)
+    G = bc.graph_from_edgelist(g)
+    H = bc.HostCSR.from_device(G)
+    dev = bc.brandes(G, S).cpu().numpy()
+    host = bc.brandes_host(H, S).numpy()
+    assert np.array_equal(dev, host)
+    dev_pp = bc.brandes_pp(G, S, g.part).cpu().numpy()
+    host_pp = bc.brandes_pp_host(H, S, g.part).numpy()
+    assert rel_err(host_pp, dev_pp) < FP64_TOL
