@@ -72,7 +72,11 @@ typedef struct {
     int32_t validate;          /* reserved: the CSR, S and the partition are always checked */
     int32_t host_buffers;      /* 1: array arguments are host pointers (copied in and out) */
     int32_t order_sources;     /* 1 (default): batch targets of the same part together (Brandes++) */
-    int32_t reserved;
+    int32_t shard_index;       /* with shard_count > 1: use only this shard's targets as sources */
+    int32_t shard_count;       /* 0 or 1: every target is a source.  Otherwise the source batches are
+                                * split into shard_count contiguous shards; the result is this shard's
+                                * partial sum (targets stay all of S), so the shards' results add up to
+                                * the unsharded result (multi-GPU source sharding). */
 } bcpp_opts;
 
 typedef struct {

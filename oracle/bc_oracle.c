@@ -151,9 +151,15 @@ static hitem heap_pop(heap_t *h) {
  * the settled nodes in non-decreasing distance; returns their count, or -1 on ENOMEM.
  * Unit weights use a FIFO queue (breadth-first search), otherwise a binary heap. */
 static int64_t sssp(const graph_t *g, int32_t s, const uint8_t *keep, const uint8_t *frontier,
-                    int32_t *dist, uint64_t *sigma, int32_t *order, uint32_t *ovf) {
+                    int32_t *dist, uint64_t *sigma, int32_t *order, uint32_t *ovf,
+                    const int32_t *part_nodes, int32_t n_part) {
     int32_t n = g->n;
-    for (int32_t v = 0; v < n; v++) { dist[v] = INF32; sigma[v] = 0; }
+    /* with keep, only the part's own nodes can be reached, so only they are reset */
+    if (part_nodes) {
+        for (int32_t j = 0; j < n_part; j++) { dist[part_nodes[j]] = INF32; sigma[part_nodes[j]] = 0; }
+    } else {
+        for (int32_t v = 0; v < n; v++) { dist[v] = INF32; sigma[v] = 0; }
+    }
     dist[s] = 0; sigma[s] = 1;
     int64_t cnt = 0;
     if (!g->wt) {
@@ -173,7 +179,7 @@ static int64_t sssp(const graph_t *g, int32_t s, const uint8_t *keep, const uint
         return cnt;
     }
     heap_t h = {0};
-    uint8_t *done = calloc((size_t)n, 1);
+    uint8_t *done = calloc((size_t)(n ? n : 1), 1);
     if (!done || heap_push(&h, 0, s)) { free(done); free(h.a); return -1; }
     while (h.len) {
         hitem it = heap_pop(&h);
@@ -266,7 +272,7 @@ int orc_sssp(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, const u
     if (graph_build(&g, n, m, eu, ev, (const int32_t *)ew, NULL, !directed)) return ORC_ENOMEM;
     int32_t *order = malloc((size_t)n * sizeof(int32_t));
     uint32_t ovf = 0;
-    int64_t c = order ? sssp(&g, src, NULL, NULL, dist, sigma, order, &ovf) : -1;
+    int64_t c = order ? sssp(&g, src, NULL, NULL, dist, sigma, order, &ovf, NULL, 0) : -1;
     free(order); graph_free(&g);
     if (overflow) *overflow = ovf;
     return c < 0 ? ORC_ENOMEM : ORC_OK;
@@ -298,7 +304,7 @@ int orc_brandes(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, cons
     if (ns_all >= 2) {
         for (int32_t i = 0; i < ns; i++) {
             int32_t s = nS ? S[i] : i;
-            int64_t cnt = sssp(&g, s, NULL, NULL, dist, sigma, order, &ovf);
+            int64_t cnt = sssp(&g, s, NULL, NULL, dist, sigma, order, &ovf, NULL, 0);
             if (cnt < 0) { rc = ORC_ENOMEM; goto out; }
             accumulate(&g, order, cnt, dist, sigma, in_s, delta);
             for (int64_t j = 0; j < cnt; j++) {
@@ -427,7 +433,9 @@ static int build_sk(skel_t *K, int32_t n, int64_t m, const int32_t *eu, const in
             uint64_t *TS = dir ? K->tsr : K->ts;
             for (int32_t fi = 0; fi < K->nf[i]; fi++) {
                 int32_t f = K->pnodes[a + fi];
-                if (sssp(gg, f, keep, K->frontier, dist, sig, order, ovf) < 0) { rc = ORC_ENOMEM; goto done; }
+                if (sssp(gg, f, keep, K->frontier, dist, sig, order, ovf, K->pnodes + a, sz) < 0) {
+                    rc = ORC_ENOMEM; goto done;
+                }
                 for (int32_t j = 0; j < sz; j++) {
                     int32_t v = K->pnodes[a + j];
                     T[K->toff[i] + (int64_t)fi * sz + j] = dist[v];
@@ -521,7 +529,7 @@ int orc_brandes_pp(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, c
             int32_t s = S[j], ss = K.skid[s];
             if (ss < 0) continue;               /* isolated target: no paths */
             /* Brandes_SK: SSSP with multiplicities (Eq. 11), dependencies (Eq. 12) */
-            int64_t cnt = sssp(&K.sk, ss, NULL, NULL, dist, sig, order, &ovf);
+            int64_t cnt = sssp(&K.sk, ss, NULL, NULL, dist, sig, order, &ovf, NULL, 0);
             if (cnt < 0) { rc = ORC_ENOMEM; goto out; }
             accumulate(&K.sk, order, cnt, dist, sig, sk_in_s, delta);
             for (int64_t x = 0; x < cnt; x++) {

@@ -38,7 +38,7 @@ class c_graph(ctypes.Structure):
 class c_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("halve_undirected", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("validate", ctypes.c_int32), ("host_buffers", ctypes.c_int32),
-                ("order_sources", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("order_sources", ctypes.c_int32), ("shard_index", ctypes.c_int32), ("shard_count", ctypes.c_int32)]
 
 
 class c_stats(ctypes.Structure):
@@ -173,7 +173,7 @@ class Graph:
                        None if self.w is None else self.w.data_ptr(), int(self.directed))
 
 
-def _opts(precision="fp64", halve=True, ctas_per_sm=0, host=False, order_sources=True) -> c_opts:
+def _opts(precision="fp64", halve=True, ctas_per_sm=0, host=False, order_sources=True, shard=None) -> c_opts:
     o = c_opts()
     load_library().bcpp_default_opts(ctypes.byref(o))
     o.precision = {"fp64": BCPP_FP64, "fp32": BCPP_FP32_DELTA, "fp32_delta": BCPP_FP32_DELTA}[precision]
@@ -181,6 +181,8 @@ def _opts(precision="fp64", halve=True, ctas_per_sm=0, host=False, order_sources
     o.ctas_per_sm = int(ctas_per_sm)
     o.host_buffers = 1 if host else 0
     o.order_sources = 1 if order_sources else 0
+    if shard is not None:
+        o.shard_index, o.shard_count = int(shard[0]), int(shard[1])
     return o
 
 
@@ -230,9 +232,10 @@ def csr_validate(G: Graph, ctx: Context | None = None) -> None:
 
 # ----------------------------------------------------------------------------- betweenness
 def brandes(G: Graph, S=None, precision: str = "fp64", halve: bool = True, ctx: Context | None = None,
-            ctas_per_sm: int = 0, out=None, stats: bool = False, allow_overflow: bool = False):
+            ctas_per_sm: int = 0, out=None, stats: bool = False, allow_overflow: bool = False, shard=None):
     """Plain Brandes, target set S (None = all nodes).  Returns a float64 device tensor [n]
-    (and the stats dict when stats=True)."""
+    (and the stats dict when stats=True).  shard=(index, count) computes one shard's partial
+    sum over the sources (the shards add up to the full result)."""
     torch = _torch()
     ctx = ctx or default_context()
     dev = G.row_ptr.device
@@ -241,7 +244,7 @@ def brandes(G: Graph, S=None, precision: str = "fp64", halve: bool = True, ctx: 
     bc = out if out is not None else torch.empty(G.n, dtype=torch.float64, device=dev)
     st = c_stats()
     cg = G.c()
-    o = _opts(precision, halve, ctas_per_sm)
+    o = _opts(precision, halve, ctas_per_sm, shard=shard)
     rc = load_library().bcpp_brandes(ctx.handle, ctypes.byref(cg), None if nS == 0 else St.data_ptr(), nS,
                                      ctypes.byref(o), bc.data_ptr(), ctypes.byref(st))
     _check(rc, allow_overflow)
@@ -250,7 +253,7 @@ def brandes(G: Graph, S=None, precision: str = "fp64", halve: bool = True, ctx: 
 
 def brandes_pp(G: Graph, S, part, k: int | None = None, precision: str = "fp64", halve: bool = True,
                ctx: Context | None = None, ctas_per_sm: int = 0, order_sources: bool = True, out=None,
-               stats: bool = False, allow_overflow: bool = False):
+               stats: bool = False, allow_overflow: bool = False, shard=None):
     """Brandes++ (Build_SK, Brandes_SK, Centrality) for target set S (None = all nodes) and
     node partition `part` with values in [0, k)."""
     torch = _torch()
@@ -264,7 +267,7 @@ def brandes_pp(G: Graph, S, part, k: int | None = None, precision: str = "fp64",
     bc = out if out is not None else torch.empty(G.n, dtype=torch.float64, device=dev)
     st = c_stats()
     cg = G.c()
-    o = _opts(precision, halve, ctas_per_sm, order_sources=order_sources)
+    o = _opts(precision, halve, ctas_per_sm, order_sources=order_sources, shard=shard)
     rc = load_library().bcpp_brandes_pp(ctx.handle, ctypes.byref(cg), None if nS == 0 else St.data_ptr(), nS,
                                         pt.data_ptr(), int(k), ctypes.byref(o), bc.data_ptr(), ctypes.byref(st))
     _check(rc, allow_overflow)

@@ -177,6 +177,17 @@ __global__ void i64_from_i32_kernel(const int32_t* in, int64_t* out, int64_t n) 
         out[i] = in[i];
 }
 
+// batches [b0, b1) of this shard (all batches when unsharded)
+void shard_range(const bcpp_opts& o, int nitems, int& b0, int& b1) {
+    b0 = 0;
+    b1 = nitems;
+    if (o.shard_count > 1) {
+        const int64_t r = std::max(0, std::min(o.shard_index, o.shard_count - 1));
+        b0 = (int)((int64_t)nitems * r / o.shard_count);
+        b1 = (int)((int64_t)nitems * (r + 1) / o.shard_count);
+    }
+}
+
 int bits_for(uint64_t maxval) {
     int b = 0;
     while (b < 64 && (maxval >> b) != 0) b++;
@@ -384,10 +395,18 @@ int brandes_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, 
     InCsr T;
     if (g->directed) CK_RC(build_in_csr(c, g, T));
     // items: batches of 32 targets in the given order
-    const int nitems = (int)((ns + LS_LANES - 1) / LS_LANES);
-    std::vector<LsItem> hitems(nitems);
+    int b0, b1;
+    shard_range(o, (int)((ns + LS_LANES - 1) / LS_LANES), b0, b1);
+    const int nitems = b1 - b0;
+    std::vector<LsItem> hitems(std::max(nitems, 0));
     for (int i = 0; i < nitems; i++)
-        hitems[i] = LsItem{0, i * LS_LANES, (int32_t)std::min<int64_t>(LS_LANES, ns - (int64_t)i * LS_LANES), 0};
+        hitems[i] = LsItem{0, (b0 + i) * LS_LANES,
+                           (int32_t)std::min<int64_t>(LS_LANES, ns - (int64_t)(b0 + i) * LS_LANES), 0};
+    if (nitems <= 0) {
+        CK_CUDA(cudaMemsetAsync(bc_out, 0, (size_t)n * sizeof(double), c->stream));
+        CK_CUDA(cudaStreamSynchronize(c->stream));
+        return BCPP_OK;
+    }
     DBuf<LsItem> items(c, nitems);
     DBuf<int64_t> node_off(c, 2);
     CK_ALLOC(items); CK_ALLOC(node_off);
@@ -419,11 +438,11 @@ int brandes_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, 
     tb.start();
     ls_launch(fp32, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream);
     c->launches++;
+    tb.stop();
     CK_CUDA(cudaGetLastError());
     const bool halve = !g->directed && o.halve_undirected != 0;
     combine_launch(ws.W.bc_sum, ws.W.bc_cmp, slots, n, n, halve ? 0.5 : 1.0, bc_out, c->stream);
     c->launches++;
-    tb.stop();
     int rc = finish_status(c, st);
     tt.stop();
     if (st) {
@@ -725,7 +744,9 @@ int brandes_pp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t n
     const bool unit = K.wmax_sk == 1;
     const bool mult = K.mmax_sk > 1;
     const int nb = (int)K.wmax_sk + 1;
-    const int nitems = (nt + LS_LANES - 1) / LS_LANES;
+    int b0, b1;
+    shard_range(o, (nt + LS_LANES - 1) / LS_LANES, b0, b1);
+    const int nitems = std::max(0, b1 - b0);
     const int slots = nitems > 0 ? choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(std::max(N, 1), nb, fp32),
                                                 (int64_t)n * 16)
                                  : 1;
@@ -781,7 +802,7 @@ int brandes_pp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t n
         CK_RC(to_dev(c, units.p, hunits.data(), (int64_t)hunits.size()));
         std::vector<LsItem> hitems(nitems);
         for (int i = 0; i < nitems; i++)
-            hitems[i] = LsItem{0, i * LS_LANES, std::min(LS_LANES, nt - i * LS_LANES), 0};
+            hitems[i] = LsItem{0, (b0 + i) * LS_LANES, std::min(LS_LANES, nt - (b0 + i) * LS_LANES), 0};
         DBuf<LsItem> items(c, nitems);
         CK_ALLOC(items);
         CK_RC(to_dev(c, items.p, hitems.data(), nitems));
@@ -1091,6 +1112,8 @@ void bcpp_default_opts(bcpp_opts* o) {
     o->validate = 1;
     o->host_buffers = 0;
     o->order_sources = 1;
+    o->shard_index = 0;
+    o->shard_count = 0;
 }
 
 const char* bcpp_strerror(int s) {
