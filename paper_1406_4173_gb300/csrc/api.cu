@@ -807,7 +807,23 @@ int brandes_pp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t n
         CK_ALLOC(items);
         CK_RC(to_dev(c, items.p, hitems.data(), nitems));
         const SkTables T = K.tables();
-        for (int c0 = 0; c0 < nitems; c0 += slots) {
+        if (hunits.empty()) {
+            // no non-frontier nodes: Brandes_SK alone, batches scheduled dynamically
+            LsParams P{};
+            P.mode = LS_BRANDES;
+            P.nb = nb;
+            P.srcs = tsk.p;
+            P.in_s = sk_in_s.p;
+            P.bc_map = K.sknode.p;
+            P.item_counter = ws.counter.p;
+            P.flags = c->flags;
+            tbr.start();
+            ls_launch(fp32, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream);
+            c->launches++;
+            tbr.stop();
+            CK_CUDA(cudaGetLastError());
+        }
+        for (int c0 = 0; c0 < nitems && !hunits.empty(); c0 += slots) {
             const int cn = std::min(slots, nitems - c0);
             LsParams P{};
             P.mode = LS_SKEL;

@@ -15,33 +15,33 @@ namespace bcpp {
 
 namespace {
 
-constexpr int UNROLL = 4;
 
+// Mark head v in the bucket of distance nd (fire-and-forget: a stale mark only costs a
+// visit that finds no lane at that distance).
 __device__ __forceinline__ void mark_bucket(const LsParams& P, uint32_t* bm, uint8_t* bflag, int64_t bm_words,
                                             int v, int32_t nd, int* s_maxpush) {
     const int bk = nd % P.nb;
-    const uint32_t bit = 1u << (v & 31);
-    uint32_t old = atomicOr(&bm[(int64_t)bk * bm_words + (v >> 5)], bit);
-    if (!(old & bit)) {
-        bflag[bk] = 1;
-        atomicMax(s_maxpush, nd);
-    }
+    atomicOr(&bm[(int64_t)bk * bm_words + (v >> 5)], 1u << (v & 31));
+    bflag[bk] = 1;
+    atomicMax(s_maxpush, nd);
 }
 
-// Visit the arcs [a0, a1) of one row: fetch 32 heads/weights/multiplicities per coalesced
-// load, broadcast them by shuffle, and load UNROLL distance rows before using them.
-template <class F>
-__device__ __forceinline__ void for_arcs(const int32_t* __restrict__ col, const int32_t* __restrict__ w,
-                                         const uint64_t* __restrict__ mu, int64_t a0, int64_t a1,
-                                         const int32_t* d, int lane, F&& f) {
+// Visit the arcs [a0, a1) of one row in groups of UNROLL: 32 heads (and weights and
+// multiplicities) come in one coalesced load and are broadcast by shuffle; the distance
+// rows of a whole group are loaded before the group is handed to f, which can then issue its
+// own dependent loads for the whole group at once.
+template <int UNROLL, bool WEIGHTED, bool MULT, class F>
+__device__ __forceinline__ void for_arc_groups(const int32_t* __restrict__ col, const int32_t* __restrict__ w,
+                                               const uint64_t* __restrict__ mu, int64_t a0, int64_t a1,
+                                               const int32_t* d, int lane, F&& f) {
     for (int64_t c0 = a0; c0 < a1; c0 += 32) {
         const int cnt = (int)min((int64_t)32, a1 - c0);
         int32_t mv = 0, mw = 1;
         uint64_t mm = 1;
         if (lane < cnt) {
             mv = __ldg(col + c0 + lane);
-            if (w) mw = __ldg(w + c0 + lane);
-            if (mu) mm = __ldg(mu + c0 + lane);
+            if (WEIGHTED) mw = __ldg(w + c0 + lane);
+            if (MULT) mm = __ldg(mu + c0 + lane);
         }
         for (int j = 0; j < cnt; j += UNROLL) {
             int32_t vv[UNROLL], ww[UNROLL], dv[UNROLL];
@@ -49,25 +49,25 @@ __device__ __forceinline__ void for_arcs(const int32_t* __restrict__ col, const 
 #pragma unroll
             for (int k = 0; k < UNROLL; k++) {
                 vv[k] = __shfl_sync(FULL, mv, (j + k) & 31);
-                ww[k] = w ? __shfl_sync(FULL, mw, (j + k) & 31) : 1;
-                mk[k] = mu ? shfl_u64(mm, (j + k) & 31) : 1ull;
+                ww[k] = WEIGHTED ? __shfl_sync(FULL, mw, (j + k) & 31) : 1;
+                mk[k] = MULT ? shfl_u64(mm, (j + k) & 31) : 1ull;
             }
 #pragma unroll
             for (int k = 0; k < UNROLL; k++)
                 dv[k] = (j + k < cnt) ? d[(int64_t)vv[k] * LS_LANES + lane] : DINF;
-#pragma unroll
-            for (int k = 0; k < UNROLL; k++)
-                if (j + k < cnt) f(vv[k], ww[k], mk[k], dv[k]);
+            f(vv, ww, mk, dv, cnt - j);
         }
     }
 }
 
-template <typename DT, bool FUSED>
+template <typename DT, bool FUSED, bool WEIGHTED, bool MULT>
 __global__ void __launch_bounds__(LS_THREADS, 2)
 ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __restrict__ items, int nitems) {
     __shared__ int s_item, s_pos, s_next, s_D, s_done, s_maxpush, s_nsteps, s_err, s_end;
     const int lane = threadIdx.x & 31;
     const int slot = blockIdx.x;
+    // arcs handled per group (bounded by the 64 registers of two resident 512-thread CTAs)
+    constexpr int UNROLL = (WEIGHTED && FUSED) ? (MULT ? 4 : 6) : (MULT ? 6 : 8);
 
     int32_t* d = W.d + (int64_t)slot * W.cap_n * LS_LANES;
     uint64_t* sg = W.sg + (int64_t)slot * W.cap_n * LS_LANES;
@@ -96,7 +96,6 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
         const int64_t* rp = A.rp + base;
         const int64_t* irp = A.irp + base;
         const int32_t nf = P.nfront ? P.nfront[I.g] : 0;
-        const bool unit = (A.w == nullptr);
         const int32_t my_src = lane < I.nsrc ? P.srcs[I.src_off + lane] : -1;
 
         // sources: d = 0, sigma = 1, bucket 0
@@ -178,37 +177,54 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                 bool ovf = false;
                 uint64_t acc = 0;
                 const bool pull = act && D > 0;
-                auto relax = [&](int32_t v, int32_t wv, int32_t dv) {
-                    const int64_t nd64 = (int64_t)D + wv;
-                    const int32_t nd = nd64 < DINF ? (int32_t)nd64 : DINF;
-                    const bool imp = act && nd < dv;
-                    if (__ballot_sync(FULL, imp)) {
-                        bool nw = false;
-                        if (imp) {
-                            int32_t* pd = &d[(int64_t)v * LS_LANES + lane];
-                            if (unit) { *pd = nd; nw = true; }
-                            else nw = nd < atomicMin(pd, nd);
+                // sigma(s,u) = sum over parents v (d(v) + w(v,u) = D) of sigma(s,v) * m(v,u)
+                auto pull_group = [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk, const int32_t* dv,
+                                      int left) {
+                    uint64_t sp[UNROLL];
+#pragma unroll
+                    for (int k = 0; k < UNROLL; k++) {
+                        const bool par = k < left && pull && dv[k] < D && dv[k] + ww[k] == D &&
+                                         (vv[k] >= nf || dv[k] == 0);
+                        sp[k] = par ? sg[(int64_t)vv[k] * LS_LANES + lane] : 0ull;
+                    }
+#pragma unroll
+                    for (int k = 0; k < UNROLL; k++)
+                        if (sp[k]) acc = madd_ck(acc, sp[k], MULT ? mk[k] : 1ull, ovf);
+                };
+                // relax the out-arcs: lower tentative distances, mark improved heads in their bucket
+                auto relax_group = [&](const int32_t* vv, const int32_t* ww, const int32_t* dv, int left) {
+#pragma unroll
+                    for (int k = 0; k < UNROLL; k++) {
+                        if (k >= left) break;
+                        const int64_t nd64 = (int64_t)D + ww[k];
+                        const int32_t nd = nd64 < DINF ? (int32_t)nd64 : DINF;
+                        const bool imp = act && nd < dv[k];
+                        const unsigned im = __ballot_sync(FULL, imp);
+                        if (im) {
+                            int32_t* pd = &d[(int64_t)vv[k] * LS_LANES + lane];
+                            if (imp) {
+                                if (WEIGHTED) atomicMin(pd, nd);
+                                else *pd = nd;
+                            }
+                            if (lane == __ffs(im) - 1) mark_bucket(P, bm, bflag, W.bm_words, vv[k], nd, &s_maxpush);
                         }
-                        const unsigned nm = __ballot_sync(FULL, nw);
-                        if (nm && lane == __ffs(nm) - 1) mark_bucket(P, bm, bflag, W.bm_words, v, nd, &s_maxpush);
                     }
                 };
                 if (FUSED) {
-                    for_arcs(A.col, A.w, A.mu, rp[u], rp[u + 1], d, lane,
-                             [&](int32_t v, int32_t wv, uint64_t m, int32_t dv) {
-                                 if (pull && dv < D && dv + wv == D && (v >= nf || dv == 0))
-                                     acc = madd_ck(acc, sg[(int64_t)v * LS_LANES + lane], m, ovf);
-                                 relax(v, wv, dv);
-                             });
+                    for_arc_groups<UNROLL, WEIGHTED, MULT>(A.col, A.w, A.mu, rp[u], rp[u + 1], d, lane,
+                        [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk, const int32_t* dv, int left) {
+                            pull_group(vv, ww, mk, dv, left);
+                            relax_group(vv, ww, dv, left);
+                        });
                 } else {
                     if (D > 0)
-                        for_arcs(A.icol, A.iw, A.imu, irp[u], irp[u + 1], d, lane,
-                                 [&](int32_t v, int32_t wv, uint64_t m, int32_t dv) {
-                                     if (pull && dv < D && dv + wv == D && (v >= nf || dv == 0))
-                                         acc = madd_ck(acc, sg[(int64_t)v * LS_LANES + lane], m, ovf);
-                                 });
-                    for_arcs(A.col, A.w, A.mu, rp[u], rp[u + 1], d, lane,
-                             [&](int32_t v, int32_t wv, uint64_t, int32_t dv) { relax(v, wv, dv); });
+                        for_arc_groups<UNROLL, WEIGHTED, MULT>(A.icol, A.iw, A.imu, irp[u], irp[u + 1], d, lane,
+                            [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk, const int32_t* dv,
+                                int left) { pull_group(vv, ww, mk, dv, left); });
+                    for_arc_groups<UNROLL, WEIGHTED, false>(A.col, A.w, nullptr, rp[u], rp[u + 1], d, lane,
+                        [&](const int32_t* vv, const int32_t* ww, const uint64_t*, const int32_t* dv, int left) {
+                            relax_group(vv, ww, dv, left);
+                        });
                 }
                 if (pull) sg[(int64_t)u * LS_LANES + lane] = acc;
                 if (__any_sync(FULL, ovf) && lane == 0) atomicOr(&P.flags[FLAG_SIGMA_OVF], 1u);
@@ -249,11 +265,18 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                     const bool act = (du == D);
                     if (!__ballot_sync(FULL, act)) continue;
                     DT acc = (DT)0;
-                    for_arcs(A.col, A.w, A.mu, rp[u], rp[u + 1], d, lane,
-                             [&](int32_t v, int32_t wv, uint64_t m, int32_t dv) {
-                                 if (act && dv != DINF && (int64_t)dv == (int64_t)D + wv)
-                                     acc += (DT)m * dl[(int64_t)v * LS_LANES + lane];
-                             });
+                    for_arc_groups<UNROLL, WEIGHTED, MULT>(A.col, A.w, A.mu, rp[u], rp[u + 1], d, lane,
+                        [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk, const int32_t* dv, int left) {
+                            DT cv[UNROLL];
+#pragma unroll
+                            for (int k = 0; k < UNROLL; k++) {
+                                const bool succ = k < left && act && dv[k] != DINF &&
+                                                  (int64_t)dv[k] == (int64_t)D + ww[k];
+                                cv[k] = succ ? dl[(int64_t)vv[k] * LS_LANES + lane] : (DT)0;
+                            }
+#pragma unroll
+                            for (int k = 0; k < UNROLL; k++) acc += MULT ? (DT)mk[k] * cv[k] : cv[k];
+                        });
                     double contrib = 0.0;
                     if (act) {
                         const DT sd = (DT)sg[(int64_t)u * LS_LANES + lane];
@@ -333,16 +356,33 @@ __global__ void fill_i32_kernel(int32_t* p, int32_t v, int64_t n) {
 
 }  // namespace
 
+template <typename DT>
+static void ls_launch_t(bool fused, bool weighted, bool mult, const LsArena& A, const LsParams& P, const LsSlots& W,
+                        const LsItem* items, int nitems, int slots, cudaStream_t st) {
+#define LS_GO(F, WT, M) ls_kernel<DT, F, WT, M><<<slots, LS_THREADS, 0, st>>>(A, P, W, items, nitems)
+    if (fused) {
+        if (!weighted) LS_GO(true, false, false);
+        else if (!mult) LS_GO(true, true, false);
+        else LS_GO(true, true, true);
+    } else {
+        if (!weighted) LS_GO(false, false, false);
+        else if (!mult) LS_GO(false, true, false);
+        else LS_GO(false, true, true);
+    }
+#undef LS_GO
+}
+
 void ls_launch(bool fp32_delta, bool fused, const LsArena& A, const LsParams& P, const LsSlots& W,
                const LsItem* items, int nitems, int slots, cudaStream_t st) {
     if (nitems <= 0 || slots <= 0) return;
-    if (fp32_delta) {
-        if (fused) ls_kernel<float, true><<<slots, LS_THREADS, 0, st>>>(A, P, W, items, nitems);
-        else ls_kernel<float, false><<<slots, LS_THREADS, 0, st>>>(A, P, W, items, nitems);
-    } else {
-        if (fused) ls_kernel<double, true><<<slots, LS_THREADS, 0, st>>>(A, P, W, items, nitems);
-        else ls_kernel<double, false><<<slots, LS_THREADS, 0, st>>>(A, P, W, items, nitems);
-    }
+    // arcs with multiplicities run the weighted kernel (a unit weight array is not needed:
+    // multiplicities > 1 only occur on skeleton arcs whose weights are > 1 as well)
+    LsArena B = A;
+    const bool mult = A.mu != nullptr;
+    const bool weighted = A.w != nullptr;
+    if (mult && !weighted) return;
+    if (fp32_delta) ls_launch_t<float>(fused, weighted, mult, B, P, W, items, nitems, slots, st);
+    else ls_launch_t<double>(fused, weighted, mult, B, P, W, items, nitems, slots, st);
 }
 
 void ls_reset_launch(const LsSlots& W, int slots, cudaStream_t st) {

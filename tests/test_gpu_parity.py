@@ -243,3 +243,19 @@ def test_host_buffer_calls_match_device(bc):
     dev_pp = bc.brandes_pp(G, S, g.part).cpu().numpy()
     host_pp = bc.brandes_pp_host(H, S, g.part).numpy()
     assert rel_err(host_pp, dev_pp) < FP64_TOL
+
+
+# ----------------------------------------------------------------------------- source shards
+@pytest.mark.parametrize("world", [2, 3])
+def test_source_shards_add_up(bc, world):
+    import torch
+    g = gen.planted_partition(700, 7, 0.03, 0.002, seed=23, wmax=4)
+    S = gen.sample_targets(g.n, 200, seed=23)
+    G = bc.graph_from_edgelist(g)
+    full = bc.brandes(G, S, halve=False).cpu().numpy()
+    parts = sum(bc.brandes(G, S, halve=False, shard=(r, world)).cpu().numpy() for r in range(world))
+    assert rel_err(parts, full) < FP64_TOL
+    full_pp = bc.brandes_pp(G, S, g.part, halve=False).cpu().numpy()
+    parts_pp = sum(bc.brandes_pp(G, S, g.part, halve=False, shard=(r, world)).cpu().numpy() for r in range(world))
+    assert rel_err(parts_pp, full_pp) < FP64_TOL
+    assert rel_err(full_pp, full) < FP64_TOL
