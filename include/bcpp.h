@@ -168,6 +168,34 @@ int bcpp_skeleton(bcpp_ctx *ctx, const bcpp_graph *g, const int32_t *S, int32_t 
                   int64_t cap_arcs, int32_t *au, int32_t *av, int32_t *aw, uint64_t *amu,
                   int64_t *n_arcs_out, const bcpp_opts *opts);
 
+/* Limits of bcpp_brandes_noalloc (sizes of its static scratch array). */
+#define BCPP_NOALLOC_MAX_NODES 4096
+#define BCPP_NOALLOC_MAX_WEIGHT 15
+
+/* Plain Brandes for small undirected graphs that allocates no memory at all.  The paper has
+ * no counterpart: this is a deployment variant of bcpp_brandes for callers that cannot call
+ * cudaMalloc -- a host whose own allocator owns all device memory (an allocation behind its
+ * back breaks its accounting or fails against its reservation), or a latency-critical path
+ * where an allocation, which can synchronize the device, is not acceptable.  No context is
+ * needed: the call takes only inputs, the output and a stream.
+ *
+ * Computes exactly what bcpp_brandes computes with BCPP_FP64 (same kernels): bc_out[n] (device)
+ * receives C^S(v) for the targets S[nS] (device; nS == 0 means S = V), halved when `halve`
+ * is non-zero.  The graph (device CSR) must be undirected with n <= BCPP_NOALLOC_MAX_NODES
+ * and unit weights or integer weights <= BCPP_NOALLOC_MAX_WEIGHT; anything else returns
+ * BCPP_EINVAL before any work is queued.  Other errors as for bcpp_brandes.
+ *
+ * Scratch lives in one file-scope static device array of about 27 MB, which every GPU that
+ * loads the library holds until the process exits.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress) once for the current device; make that
+ * first call before any stream capture.  All calls share the array and it keeps the last
+ * call's contents (each call clears what must start at zero), so calls whose GPU work
+ * overlaps -- on different streams or from different host threads -- race on it: serialize
+ * them.  The call synchronizes `cuda_stream` (NULL = legacy default stream) before it
+ * returns. */
+int bcpp_brandes_noalloc(const bcpp_graph *g, const int32_t *S, int32_t nS, int32_t halve,
+                         double *bc_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -54,7 +54,7 @@ class c_stats(ctypes.Structure):
 
 EXPORTS = ["bcpp_default_opts", "bcpp_strerror", "bcpp_create", "bcpp_destroy", "bcpp_workspace_bytes",
            "bcpp_csr_build", "bcpp_csr_validate", "bcpp_brandes", "bcpp_brandes_pp", "bcpp_brandes_batched",
-           "bcpp_sssp", "bcpp_skeleton"]
+           "bcpp_sssp", "bcpp_skeleton", "bcpp_brandes_noalloc"]
 
 _lib = None
 _lock = threading.Lock()
@@ -87,6 +87,7 @@ def load_library(path: str | None = None):
             "bcpp_sssp": (ctypes.c_int, [P, G, P, i32, P, P, O]),
             "bcpp_skeleton": (ctypes.c_int, [P, G, P, i32, P, i32, P, ctypes.POINTER(i32), i64, P, P, P, P,
                                              ctypes.POINTER(i64), O]),
+            "bcpp_brandes_noalloc": (ctypes.c_int, [G, P, i32, i32, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -426,3 +427,20 @@ def brandes_pp_host(H: HostCSR, S, part, k=None, precision="fp64", halve=True, c
                                         pt.data_ptr(), int(k), ctypes.byref(o), bc.data_ptr(), ctypes.byref(st))
     _check(rc, allow_overflow)
     return (bc, st.as_dict()) if stats else bc
+
+
+def brandes_noalloc(G: Graph, S=None, halve: bool = True, out=None, stream=None, allow_overflow: bool = False):
+    """Plain Brandes through bcpp_brandes_noalloc: no library allocation (scratch is a static
+    device array), for undirected graphs of at most 4,096 nodes and weights <= 15.  For
+    callers that cannot allocate device memory; `out` may be a caller-owned float64 tensor."""
+    torch = _torch()
+    dev = G.row_ptr.device
+    St = _dev_i32(S, dev)
+    nS = 0 if St is None else int(St.numel())
+    bc = out if out is not None else torch.empty(G.n, dtype=torch.float64, device=dev)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    cg = G.c()
+    rc = load_library().bcpp_brandes_noalloc(ctypes.byref(cg), None if nS == 0 else St.data_ptr(), nS,
+                                             1 if halve else 0, bc.data_ptr(), ctypes.c_void_p(st.cuda_stream))
+    _check(rc, allow_overflow)
+    return bc
