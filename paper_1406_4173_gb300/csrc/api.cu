@@ -29,6 +29,7 @@ struct bcpp_ctx {
     uint32_t* flags = nullptr;       // device [FLAG_COUNT]
     uint32_t* hflags = nullptr;      // pinned host copy
     int64_t launches = 0;
+    int order_factor = 8;            // settled-entry capacity per node of a batch (retry: 32)
     cudaEvent_t ev[8] = {};
 
     void* acquire(size_t bytes) {
@@ -232,7 +233,8 @@ struct SlotWs {
     DBuf<int32_t> d;
     DBuf<uint64_t> sg;
     DBuf<char> dl;
-    DBuf<int32_t> order, step_d, step_beg, hdr;
+    DBuf<LsEnt> order;
+    DBuf<int32_t> step_d, step_beg, hdr;
     DBuf<uint32_t> bm;
     DBuf<uint8_t> bflag;
     DBuf<double> bcs, bcc;
@@ -240,10 +242,10 @@ struct SlotWs {
     LsSlots W{};
 };
 
-int64_t slot_bytes(int64_t cap_n, int nb, bool fp32) {
-    int64_t cap_order = 32 * cap_n + 1024;
-    int64_t bm_words = (cap_n + 31) / 32;
-    return cap_n * 32 * (4 + 8 + (fp32 ? 4 : 8)) + cap_order * 4 + 2 * (cap_n + 4098) * 4 +
+int64_t slot_bytes(int64_t cap_n, int nb, bool fp32, int order_factor = 8) {
+    const int64_t cap_order = order_factor * cap_n + 1024;
+    const int64_t bm_words = (cap_n + 31) / 32;
+    return cap_n * 32 * (4 + 8 + (fp32 ? 4 : 8)) + cap_order * (int64_t)sizeof(LsEnt) + 2 * (cap_n + 4098) * 4 +
            (int64_t)nb * bm_words * 4 + nb;
 }
 
@@ -263,7 +265,8 @@ int choose_slots(bcpp_ctx* c, int nitems, int ctas_per_sm, int64_t per_slot, int
 }
 
 int alloc_slots(bcpp_ctx* c, SlotWs& S, int slots, int64_t cap_n, int nb, bool fp32, int64_t cap_bc) {
-    const int64_t cap_order = 32 * cap_n + 1024;
+    if (cap_n >= (1 << 26)) return BCPP_EINVAL;   // 32-bit row offsets inside a slot
+    const int64_t cap_order = (int64_t)c->order_factor * cap_n + 1024;
     const int32_t cap_steps = (int32_t)std::min<int64_t>(cap_order, 4 * (cap_n + 2) + 4096);
     const int64_t bm_words = (cap_n + 31) / 32;
     CK_ALLOC(S.d.alloc(c, (int64_t)slots * cap_n * 32));
@@ -414,7 +417,7 @@ int brandes_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, 
     const int64_t hoff[2] = {0, n};
     CK_RC(to_dev(c, node_off.p, hoff, 2));
     const int nb = g->w ? (int)wmax + 1 : 2;
-    const int slots = choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(n, nb, fp32), (int64_t)n * 16);
+    const int slots = choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(n, nb, fp32, c->order_factor), (int64_t)n * 16);
     SlotWs ws;
     CK_RC(alloc_slots(c, ws, slots, n, nb, fp32, n));
     LsArena A{};
@@ -606,7 +609,7 @@ int build_sk(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS_eff,
         iota(srcs.p, maxnf, c->stream);
         c->launches++;
         const int nb = g->w ? (int)wmax + 1 : 2;
-        const int slots = choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(maxpart_tab, nb, false), 0);
+        const int slots = choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(maxpart_tab, nb, false, c->order_factor), 0);
         for (int dir = 0; dir < (g->directed ? 2 : 1); dir++) {
             SlotWs ws;
             CK_RC(alloc_slots(c, ws, slots, maxpart_tab, nb, false, 0));
@@ -747,7 +750,7 @@ int brandes_pp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t n
     int b0, b1;
     shard_range(o, (nt + LS_LANES - 1) / LS_LANES, b0, b1);
     const int nitems = std::max(0, b1 - b0);
-    const int slots = nitems > 0 ? choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(std::max(N, 1), nb, fp32),
+    const int slots = nitems > 0 ? choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(std::max(N, 1), nb, fp32, c->order_factor),
                                                 (int64_t)n * 16)
                                  : 1;
     CK_RC(alloc_slots(c, ws, slots, std::max(N, 1), nb, fp32, n));
@@ -919,7 +922,7 @@ int batched_dev(bcpp_ctx* c, int32_t ngraphs, const int64_t* node_ptr_dev, const
     iota(srcs.p, maxn, c->stream);
     c->launches++;
     const int nb = g->w ? (int)wmax + 1 : 2;
-    const int slots = choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(maxn, nb, fp32), (int64_t)n * 16);
+    const int slots = choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(maxn, nb, fp32, c->order_factor), (int64_t)n * 16);
     SlotWs ws;
     CK_RC(alloc_slots(c, ws, slots, maxn, nb, fp32, n));
     LsArena A{};
@@ -979,7 +982,7 @@ int sssp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* src, int32_t nsrc,
     // a batch holds each source at most once: split repeated sources across batches is not
     // needed because LS_SSSP lanes are independent rows (a repeat only repeats the row)
     const int nb = g->w ? (int)wmax + 1 : 2;
-    const int slots = choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(n, nb, false), 0);
+    const int slots = choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(n, nb, false, c->order_factor), 0);
     SlotWs ws;
     CK_RC(alloc_slots(c, ws, slots, n, nb, false, 0));
     LsArena A{};
@@ -1115,6 +1118,20 @@ int stage_graph(bcpp_ctx* c, const bcpp_graph* hg, StagedGraph& sg) {
 
 }  // namespace
 
+// A call whose per-batch settle lists outgrew the default capacity is run once more with the
+// worst-case capacity (32 entries per node: one per lane).
+template <class F>
+int with_capacity_retry(bcpp_ctx* c, F&& f) {
+    c->order_factor = 8;
+    int rc = f();
+    if (rc == BCPP_ECAPACITY) {
+        c->order_factor = 32;
+        rc = f();
+        c->order_factor = 8;
+    }
+    return rc;
+}
+
 // =========================================================================== C ABI
 extern "C" {
 
@@ -1205,12 +1222,12 @@ int bcpp_brandes(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS,
         rc = stage_graph(c, g, sg);
         if (!rc) rc = stage_in(c, dS, S, nS, &pS);
         if (!rc && !dbc.alloc(c, g->n)) rc = BCPP_ENOMEM;
-        if (!rc) rc = brandes_dev(c, &sg.g, pS, nS, o, dbc.p, stats);
+        if (!rc) rc = with_capacity_retry(c, [&] { return brandes_dev(c, &sg.g, pS, nS, o, dbc.p, stats); });
         if ((rc == BCPP_OK || rc == BCPP_EOVERFLOW_SIGMA) && g->n > 0 &&
             to_host(c, bc_out, dbc.p, g->n) != BCPP_OK)
             rc = BCPP_ECUDA;
     } else {
-        rc = brandes_dev(c, g, S, nS, o, bc_out, stats);
+        rc = with_capacity_retry(c, [&] { return brandes_dev(c, g, S, nS, o, bc_out, stats); });
     }
     if (stats) stats->kernel_launches = c->launches - l0;
     return rc;
@@ -1232,12 +1249,12 @@ int bcpp_brandes_pp(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t 
         if (!rc) rc = stage_in(c, dS, S, nS, &pS);
         if (!rc) rc = stage_in(c, dpart, part, g->n, &pp);
         if (!rc && !dbc.alloc(c, g->n)) rc = BCPP_ENOMEM;
-        if (!rc) rc = brandes_pp_dev(c, &sg.g, pS, nS, pp, k, o, dbc.p, stats);
+        if (!rc) rc = with_capacity_retry(c, [&] { return brandes_pp_dev(c, &sg.g, pS, nS, pp, k, o, dbc.p, stats); });
         if ((rc == BCPP_OK || rc == BCPP_EOVERFLOW_SIGMA) && g->n > 0 &&
             to_host(c, bc_out, dbc.p, g->n) != BCPP_OK)
             rc = BCPP_ECUDA;
     } else {
-        rc = brandes_pp_dev(c, g, S, nS, part, k, o, bc_out, stats);
+        rc = with_capacity_retry(c, [&] { return brandes_pp_dev(c, g, S, nS, part, k, o, bc_out, stats); });
     }
     if (stats) stats->kernel_launches = c->launches - l0;
     return rc;
@@ -1260,13 +1277,15 @@ int bcpp_brandes_batched(bcpp_ctx* c, int32_t num_graphs, const int64_t* graph_n
         rc = stage_graph(c, arena, sg);
         if (!rc) rc = stage_in(c, dptr, graph_node_ptr, (int64_t)num_graphs + 1, &pptr);
         if (!rc && !dbc.alloc(c, arena->n)) rc = BCPP_ENOMEM;
-        if (!rc) rc = batched_dev(c, num_graphs, pptr, hptr.data(), &sg.g, o, dbc.p, stats);
+        if (!rc)
+            rc = with_capacity_retry(c, [&] { return batched_dev(c, num_graphs, pptr, hptr.data(), &sg.g, o, dbc.p, stats); });
         if ((rc == BCPP_OK || rc == BCPP_EOVERFLOW_SIGMA) && arena->n > 0 &&
             to_host(c, bc_out, dbc.p, arena->n) != BCPP_OK)
             rc = BCPP_ECUDA;
     } else {
         rc = to_host(c, hptr.data(), graph_node_ptr, (int64_t)num_graphs + 1);
-        if (!rc) rc = batched_dev(c, num_graphs, graph_node_ptr, hptr.data(), arena, o, bc_out, stats);
+        if (!rc)
+            rc = with_capacity_retry(c, [&] { return batched_dev(c, num_graphs, graph_node_ptr, hptr.data(), arena, o, bc_out, stats); });
     }
     if (stats) stats->kernel_launches = c->launches - l0;
     return rc;
@@ -1285,13 +1304,13 @@ int bcpp_sssp(bcpp_ctx* c, const bcpp_graph* g, const int32_t* src, int32_t nsrc
         if (!rc) rc = stage_in(c, dsrc, src, nsrc, &ps);
         const int64_t cnt = (int64_t)nsrc * g->n;
         if (!rc && (!dd.alloc(c, cnt) || !ds.alloc(c, cnt))) rc = BCPP_ENOMEM;
-        if (!rc) rc = sssp_dev(c, &sg.g, ps, nsrc, dd.p, ds.p, o);
+        if (!rc) rc = with_capacity_retry(c, [&] { return sssp_dev(c, &sg.g, ps, nsrc, dd.p, ds.p, o); });
         if ((rc == BCPP_OK || rc == BCPP_EOVERFLOW_SIGMA) && cnt > 0) {
             if (to_host(c, dist_out, dd.p, cnt) || to_host(c, sigma_out, ds.p, cnt)) rc = BCPP_ECUDA;
         }
         return rc;
     }
-    return sssp_dev(c, g, src, nsrc, dist_out, sigma_out, o);
+    return with_capacity_retry(c, [&] { return sssp_dev(c, g, src, nsrc, dist_out, sigma_out, o); });
 }
 
 int bcpp_skeleton(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, const int32_t* part, int32_t k,
@@ -1307,11 +1326,16 @@ int bcpp_skeleton(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS
         if (!rc) rc = stage_in(c, dS, S, nS, &pS);
         if (!rc) rc = stage_in(c, dpart, part, g->n, &pp);
         if (!rc)
-            rc = skeleton_dev(c, &sg.g, pS, nS, pp, k, sk_nodes_out, n_sk_out, cap_arcs, au, av, aw, amu, n_arcs_out, o,
-                              true);
+            rc = with_capacity_retry(c, [&] {
+                return skeleton_dev(c, &sg.g, pS, nS, pp, k, sk_nodes_out, n_sk_out, cap_arcs, au, av, aw, amu,
+                                    n_arcs_out, o, true);
+            });
         return rc;
     }
-    return skeleton_dev(c, g, S, nS, part, k, sk_nodes_out, n_sk_out, cap_arcs, au, av, aw, amu, n_arcs_out, o, false);
+    return with_capacity_retry(c, [&] {
+        return skeleton_dev(c, g, S, nS, part, k, sk_nodes_out, n_sk_out, cap_arcs, au, av, aw, amu, n_arcs_out, o,
+                            false);
+    });
 }
 
 }  // extern "C"

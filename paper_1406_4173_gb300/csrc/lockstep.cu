@@ -9,12 +9,18 @@
 // delta(s|u) = sigma(s,u) * sum over successors v (d(v) = d(u) + w) of m(u,v) * c(s,v) with
 // c(s,v) = (I_{v in S} + delta(s|v)) / sigma(s,v), stores c(s,u), and its dependency is
 // added (u != s) into the slot's partial betweenness.
+//
+// Latency structure: a warp works on one settled entry at a time, and every dependent memory
+// round trip costs it a full HBM latency, so the kernel keeps the chain per entry short: the
+// entry already carries the node's arc range (filled by a parallel pass over the step's list),
+// the next entry is fetched while the current one is processed, a group of arcs issues all its
+// distance-row loads and then all its sigma (or c) loads together, bucket marks and
+// partial-sum updates are fire-and-forget atomics.
 #include "lockstep.cuh"
 
 namespace bcpp {
 
 namespace {
-
 
 // Mark head v in the bucket of distance nd (fire-and-forget: a stale mark only costs a
 // visit that finds no lane at that distance).
@@ -26,22 +32,22 @@ __device__ __forceinline__ void mark_bucket(const LsParams& P, uint32_t* bm, uin
     atomicMax(s_maxpush, nd);
 }
 
-// Visit the arcs [a0, a1) of one row in groups of UNROLL: 32 heads (and weights and
-// multiplicities) come in one coalesced load and are broadcast by shuffle; the distance
-// rows of a whole group are loaded before the group is handed to f, which can then issue its
-// own dependent loads for the whole group at once.
+// Visit the arcs [a0, a0 + deg) of one row in groups of UNROLL: 32 heads (and weights and
+// multiplicities) come in one coalesced load and are broadcast by shuffle; the distance rows
+// of a whole group (drow = this lane's column of the slot's distance array) are loaded before
+// the group is handed to f, which then issues its own dependent loads for the whole group.
 template <int UNROLL, bool WEIGHTED, bool MULT, class F>
 __device__ __forceinline__ void for_arc_groups(const int32_t* __restrict__ col, const int32_t* __restrict__ w,
-                                               const uint64_t* __restrict__ mu, int64_t a0, int64_t a1,
-                                               const int32_t* d, int lane, F&& f) {
-    for (int64_t c0 = a0; c0 < a1; c0 += 32) {
-        const int cnt = (int)min((int64_t)32, a1 - c0);
+                                               const uint64_t* __restrict__ mu, int64_t a0, int32_t deg,
+                                               const int32_t* drow, int lane, F&& f) {
+    for (int32_t c0 = 0; c0 < deg; c0 += 32) {
+        const int cnt = min(32, deg - c0);
         int32_t mv = 0, mw = 1;
         uint64_t mm = 1;
         if (lane < cnt) {
-            mv = __ldg(col + c0 + lane);
-            if (WEIGHTED) mw = __ldg(w + c0 + lane);
-            if (MULT) mm = __ldg(mu + c0 + lane);
+            mv = __ldg(col + a0 + c0 + lane);
+            if (WEIGHTED) mw = __ldg(w + a0 + c0 + lane);
+            if (MULT) mm = __ldg(mu + a0 + c0 + lane);
         }
         for (int j = 0; j < cnt; j += UNROLL) {
             int32_t vv[UNROLL], ww[UNROLL], dv[UNROLL];
@@ -54,10 +60,24 @@ __device__ __forceinline__ void for_arc_groups(const int32_t* __restrict__ col, 
             }
 #pragma unroll
             for (int k = 0; k < UNROLL; k++)
-                dv[k] = (j + k < cnt) ? d[(int64_t)vv[k] * LS_LANES + lane] : DINF;
+                dv[k] = (j + k < cnt) ? drow[(uint32_t)vv[k] << 5] : DINF;
             f(vv, ww, mk, dv, cnt - j);
         }
     }
+}
+
+// Fetch the next entry index of the current step for this warp (dynamic scheduling).
+__device__ __forceinline__ int fetch_entry(int* s_next, int lane) {
+    int e = 0;
+    if (lane == 0) e = atomicAdd(s_next, 1);
+    return __shfl_sync(FULL, e, 0);
+}
+
+__device__ __forceinline__ LsEnt load_entry(const LsEnt* order, int e, int end) {
+    if (e < end) return order[e];
+    LsEnt z;
+    z.u = -1; z.deg = 0; z.a0 = 0;
+    return z;
 }
 
 template <typename DT, bool FUSED, bool WEIGHTED, bool MULT>
@@ -72,13 +92,15 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
     int32_t* d = W.d + (int64_t)slot * W.cap_n * LS_LANES;
     uint64_t* sg = W.sg + (int64_t)slot * W.cap_n * LS_LANES;
     DT* dl = reinterpret_cast<DT*>(W.dl) + (int64_t)slot * W.cap_n * LS_LANES;
-    int32_t* order = W.order + (int64_t)slot * W.cap_order;
+    int32_t* drow = d + lane;              // this lane's column: node v at drow[v << 5]
+    uint64_t* srow = sg + lane;
+    DT* crow = dl + lane;
+    LsEnt* order = W.order + (int64_t)slot * W.cap_order;
     int32_t* step_d = W.step_d + (int64_t)slot * W.cap_steps;
     int32_t* step_beg = W.step_beg + (int64_t)slot * W.cap_steps;
     uint32_t* bm = W.bm + (int64_t)slot * P.nb * W.bm_words;
     uint8_t* bflag = W.bflag + (int64_t)slot * P.nb;
     double* bcs = W.bc_sum ? W.bc_sum + (int64_t)slot * W.cap_bc : nullptr;
-    double* bcc = W.bc_cmp ? W.bc_cmp + (int64_t)slot * W.cap_bc : nullptr;
 
     bool first = true;
     for (;;) {
@@ -101,8 +123,8 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
         // sources: d = 0, sigma = 1, bucket 0
         if (threadIdx.x < 32) {
             if (my_src >= 0) {
-                d[(int64_t)my_src * LS_LANES + lane] = 0;
-                sg[(int64_t)my_src * LS_LANES + lane] = 1;
+                drow[(uint32_t)my_src << 5] = 0;
+                srow[(uint32_t)my_src << 5] = 1;
                 atomicOr(&bm[my_src >> 5], 1u << (my_src & 31));
             }
         }
@@ -133,6 +155,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
             __syncthreads();
             if (s_done) break;
             const int32_t D = s_D;
+            const int beg = s_next;
             // collect bucket D into the order list
             {
                 uint32_t* bmD = bm + (int64_t)(D % P.nb) * W.bm_words;
@@ -155,7 +178,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                     while (x) {
                         const int b = __ffs(x) - 1;
                         x &= x - 1;
-                        order[p++] = wi * 32 + b;
+                        order[p++].u = wi * 32 + b;
                     }
                 }
             }
@@ -164,70 +187,85 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
             __syncthreads();
             if (s_err) break;
             const int end = s_end;
+            // attach every entry's out-arc range (independent loads, all threads)
+            for (int e = beg + threadIdx.x; e < end; e += LS_THREADS) {
+                const int32_t u = order[e].u;
+                const int64_t a0 = __ldg(rp + u);
+                order[e].a0 = a0;
+                order[e].deg = (int32_t)(__ldg(rp + u + 1) - a0);
+            }
+            __syncthreads();
             // settle the nodes of step D
-            for (;;) {
-                int e = 0;
-                if (lane == 0) e = atomicAdd(&s_next, 1);
-                e = __shfl_sync(FULL, e, 0);
-                if (e >= end) break;
-                const int u = order[e];
-                const int32_t du = d[(int64_t)u * LS_LANES + lane];
+            int e = fetch_entry(&s_next, lane);
+            LsEnt cur = load_entry(order, e, end);
+            while (e < end) {
+                const int e2 = fetch_entry(&s_next, lane);
+                const LsEnt nxt = load_entry(order, e2, end);
+                const int u = cur.u;
+                const int32_t du = drow[(uint32_t)u << 5];
                 const bool act = (du == D);
-                if (!__ballot_sync(FULL, act)) continue;
-                bool ovf = false;
-                uint64_t acc = 0;
-                const bool pull = act && D > 0;
-                // sigma(s,u) = sum over parents v (d(v) + w(v,u) = D) of sigma(s,v) * m(v,u)
-                auto pull_group = [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk, const int32_t* dv,
-                                      int left) {
-                    uint64_t sp[UNROLL];
+                if (__ballot_sync(FULL, act)) {
+                    bool ovf = false;
+                    uint64_t acc = 0;
+                    const bool pull = act && D > 0;
+                    // sigma(s,u) = sum over parents v (d(v) + w(v,u) = D) of sigma(s,v) * m(v,u)
+                    auto pull_group = [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk,
+                                          const int32_t* dv, int left) {
+                        uint64_t sp[UNROLL];
 #pragma unroll
-                    for (int k = 0; k < UNROLL; k++) {
-                        const bool par = k < left && pull && dv[k] < D && dv[k] + ww[k] == D &&
-                                         (vv[k] >= nf || dv[k] == 0);
-                        sp[k] = par ? sg[(int64_t)vv[k] * LS_LANES + lane] : 0ull;
-                    }
-#pragma unroll
-                    for (int k = 0; k < UNROLL; k++)
-                        if (sp[k]) acc = madd_ck(acc, sp[k], MULT ? mk[k] : 1ull, ovf);
-                };
-                // relax the out-arcs: lower tentative distances, mark improved heads in their bucket
-                auto relax_group = [&](const int32_t* vv, const int32_t* ww, const int32_t* dv, int left) {
-#pragma unroll
-                    for (int k = 0; k < UNROLL; k++) {
-                        if (k >= left) break;
-                        const int64_t nd64 = (int64_t)D + ww[k];
-                        const int32_t nd = nd64 < DINF ? (int32_t)nd64 : DINF;
-                        const bool imp = act && nd < dv[k];
-                        const unsigned im = __ballot_sync(FULL, imp);
-                        if (im) {
-                            int32_t* pd = &d[(int64_t)vv[k] * LS_LANES + lane];
-                            if (imp) {
-                                if (WEIGHTED) atomicMin(pd, nd);
-                                else *pd = nd;
-                            }
-                            if (lane == __ffs(im) - 1) mark_bucket(P, bm, bflag, W.bm_words, vv[k], nd, &s_maxpush);
+                        for (int k = 0; k < UNROLL; k++) {
+                            const bool par = k < left && pull && dv[k] < D && dv[k] + ww[k] == D &&
+                                             (vv[k] >= nf || dv[k] == 0);
+                            sp[k] = par ? srow[(uint32_t)vv[k] << 5] : 0ull;
                         }
-                    }
-                };
-                if (FUSED) {
-                    for_arc_groups<UNROLL, WEIGHTED, MULT>(A.col, A.w, A.mu, rp[u], rp[u + 1], d, lane,
-                        [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk, const int32_t* dv, int left) {
-                            pull_group(vv, ww, mk, dv, left);
-                            relax_group(vv, ww, dv, left);
-                        });
-                } else {
-                    if (D > 0)
-                        for_arc_groups<UNROLL, WEIGHTED, MULT>(A.icol, A.iw, A.imu, irp[u], irp[u + 1], d, lane,
+#pragma unroll
+                        for (int k = 0; k < UNROLL; k++)
+                            if (sp[k]) acc = madd_ck(acc, sp[k], MULT ? mk[k] : 1ull, ovf);
+                    };
+                    // relax the out-arcs: lower tentative distances, mark improved heads
+                    auto relax_group = [&](const int32_t* vv, const int32_t* ww, const int32_t* dv, int left) {
+#pragma unroll
+                        for (int k = 0; k < UNROLL; k++) {
+                            if (k >= left) break;
+                            const int64_t nd64 = (int64_t)D + ww[k];
+                            const int32_t nd = nd64 < DINF ? (int32_t)nd64 : DINF;
+                            const bool imp = act && nd < dv[k];
+                            const unsigned im = __ballot_sync(FULL, imp);
+                            if (im) {
+                                int32_t* pd = &drow[(uint32_t)vv[k] << 5];
+                                if (imp) {
+                                    if (WEIGHTED) atomicMin(pd, nd);
+                                    else *pd = nd;
+                                }
+                                if (lane == __ffs(im) - 1)
+                                    mark_bucket(P, bm, bflag, W.bm_words, vv[k], nd, &s_maxpush);
+                            }
+                        }
+                    };
+                    if (FUSED) {
+                        for_arc_groups<UNROLL, WEIGHTED, MULT>(A.col, A.w, A.mu, cur.a0, cur.deg, drow, lane,
                             [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk, const int32_t* dv,
-                                int left) { pull_group(vv, ww, mk, dv, left); });
-                    for_arc_groups<UNROLL, WEIGHTED, false>(A.col, A.w, nullptr, rp[u], rp[u + 1], d, lane,
-                        [&](const int32_t* vv, const int32_t* ww, const uint64_t*, const int32_t* dv, int left) {
-                            relax_group(vv, ww, dv, left);
-                        });
+                                int left) {
+                                pull_group(vv, ww, mk, dv, left);
+                                relax_group(vv, ww, dv, left);
+                            });
+                    } else {
+                        if (D > 0) {
+                            const int64_t i0 = __ldg(irp + u);
+                            const int32_t ideg = (int32_t)(__ldg(irp + u + 1) - i0);
+                            for_arc_groups<UNROLL, WEIGHTED, MULT>(A.icol, A.iw, A.imu, i0, ideg, drow, lane,
+                                [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk, const int32_t* dv,
+                                    int left) { pull_group(vv, ww, mk, dv, left); });
+                        }
+                        for_arc_groups<UNROLL, WEIGHTED, false>(A.col, A.w, nullptr, cur.a0, cur.deg, drow, lane,
+                            [&](const int32_t* vv, const int32_t* ww, const uint64_t*, const int32_t* dv,
+                                int left) { relax_group(vv, ww, dv, left); });
+                    }
+                    if (pull) srow[(uint32_t)u << 5] = acc;
+                    if (__any_sync(FULL, ovf) && lane == 0) atomicOr(&P.flags[FLAG_SIGMA_OVF], 1u);
                 }
-                if (pull) sg[(int64_t)u * LS_LANES + lane] = acc;
-                if (__any_sync(FULL, ovf) && lane == 0) atomicOr(&P.flags[FLAG_SIGMA_OVF], 1u);
+                e = e2;
+                cur = nxt;
             }
             __syncthreads();
             if (threadIdx.x == 0) { s_nsteps++; s_D = D + 1; }
@@ -255,44 +293,47 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                 __syncthreads();
                 const int32_t D = step_d[st];
                 const int end = (st + 1 < nsteps) ? step_beg[st + 1] : olen;
-                for (;;) {
-                    int e = 0;
-                    if (lane == 0) e = atomicAdd(&s_next, 1);
-                    e = __shfl_sync(FULL, e, 0);
-                    if (e >= end) break;
-                    const int u = order[e];
-                    const int32_t du = d[(int64_t)u * LS_LANES + lane];
+                int e = fetch_entry(&s_next, lane);
+                LsEnt cur = load_entry(order, e, end);
+                while (e < end) {
+                    const int e2 = fetch_entry(&s_next, lane);
+                    const LsEnt nxt = load_entry(order, e2, end);
+                    const int u = cur.u;
+                    const int32_t du = drow[(uint32_t)u << 5];
                     const bool act = (du == D);
-                    if (!__ballot_sync(FULL, act)) continue;
-                    DT acc = (DT)0;
-                    for_arc_groups<UNROLL, WEIGHTED, MULT>(A.col, A.w, A.mu, rp[u], rp[u + 1], d, lane,
-                        [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk, const int32_t* dv, int left) {
-                            DT cv[UNROLL];
+                    if (__ballot_sync(FULL, act)) {
+                        DT acc = (DT)0;
+                        for_arc_groups<UNROLL, WEIGHTED, MULT>(A.col, A.w, A.mu, cur.a0, cur.deg, drow, lane,
+                            [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk, const int32_t* dv,
+                                int left) {
+                                DT cv[UNROLL];
 #pragma unroll
-                            for (int k = 0; k < UNROLL; k++) {
-                                const bool succ = k < left && act && dv[k] != DINF &&
-                                                  (int64_t)dv[k] == (int64_t)D + ww[k];
-                                cv[k] = succ ? dl[(int64_t)vv[k] * LS_LANES + lane] : (DT)0;
-                            }
+                                for (int k = 0; k < UNROLL; k++) {
+                                    const bool succ = k < left && act && dv[k] != DINF &&
+                                                      (int64_t)dv[k] == (int64_t)D + ww[k];
+                                    cv[k] = succ ? crow[(uint32_t)vv[k] << 5] : (DT)0;
+                                }
 #pragma unroll
-                            for (int k = 0; k < UNROLL; k++) acc += MULT ? (DT)mk[k] * cv[k] : cv[k];
-                        });
-                    double contrib = 0.0;
-                    if (act) {
-                        const DT sd = (DT)sg[(int64_t)u * LS_LANES + lane];
-                        const DT delta = sd * acc;
-                        const DT is_t = P.in_s ? (DT)P.in_s[base + u] : (DT)1;
-                        dl[(int64_t)u * LS_LANES + lane] = (is_t + delta) / sd;
-                        if (u != my_src) contrib = (double)delta;
+                                for (int k = 0; k < UNROLL; k++) acc += MULT ? (DT)mk[k] * cv[k] : cv[k];
+                            });
+                        double contrib = 0.0;
+                        if (act) {
+                            const DT sd = (DT)srow[(uint32_t)u << 5];
+                            const DT delta = sd * acc;
+                            const DT is_t = P.in_s ? (DT)P.in_s[base + u] : (DT)1;
+                            crow[(uint32_t)u << 5] = (is_t + delta) / sd;
+                            if (u != my_src) contrib = (double)delta;
+                        }
+                        const double tot = warp_sum(contrib);
+                        if (lane == 0 && bcs && tot != 0.0) {
+                            // the slot owns its partial sums: no other CTA adds here, and the
+                            // add needs no reply, so the warp does not wait for it
+                            const int64_t ix = P.bc_map ? (int64_t)P.bc_map[base + u] : base + u;
+                            atomicAdd(&bcs[ix], tot);
+                        }
                     }
-                    const double tot = warp_sum(contrib);
-                    if (lane == 0 && bcs && tot != 0.0) {
-                        const int64_t ix = P.bc_map ? (int64_t)P.bc_map[base + u] : base + u;
-                        double s = bcs[ix], c = bcc[ix];
-                        neumaier_add(s, c, tot);
-                        bcs[ix] = s;
-                        bcc[ix] = c;
-                    }
+                    e = e2;
+                    cur = nxt;
                 }
                 __syncthreads();
             }
@@ -302,10 +343,10 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
             const int warp = threadIdx.x >> 5;
             for (int v = warp; v < n; v += LS_THREADS / 32) {
                 if (lane < I.nsrc) {
-                    const int32_t dv = d[(int64_t)v * LS_LANES + lane];
+                    const int32_t dv = drow[(uint32_t)v << 5];
                     const int64_t o = t0 + (int64_t)v * nf + I.aux + lane;
                     P.td[o] = dv;
-                    P.ts[o] = dv == DINF ? 0ull : sg[(int64_t)v * LS_LANES + lane];
+                    P.ts[o] = dv == DINF ? 0ull : srow[(uint32_t)v << 5];
                 }
             }
             __syncthreads();
@@ -313,10 +354,10 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
             const int warp = threadIdx.x >> 5;
             for (int v = warp; v < n; v += LS_THREADS / 32) {
                 if (lane < I.nsrc) {
-                    const int32_t dv = d[(int64_t)v * LS_LANES + lane];
+                    const int32_t dv = drow[(uint32_t)v << 5];
                     const int64_t o = (int64_t)(I.src_off + lane) * P.dbg_n + v;
                     P.dbg_d[o] = dv;
-                    P.dbg_s[o] = dv == DINF ? 0ull : sg[(int64_t)v * LS_LANES + lane];
+                    P.dbg_s[o] = dv == DINF ? 0ull : srow[(uint32_t)v << 5];
                 }
             }
             __syncthreads();
@@ -331,8 +372,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
         } else {
             // restore "unreached" on every touched row
             const int warp = threadIdx.x >> 5;
-            for (int e = warp; e < olen; e += LS_THREADS / 32)
-                d[(int64_t)order[e] * LS_LANES + lane] = DINF;
+            for (int e = warp; e < olen; e += LS_THREADS / 32) drow[(uint32_t)order[e].u << 5] = DINF;
         }
         __syncthreads();
     }
@@ -342,9 +382,9 @@ __global__ void ls_reset_kernel(const LsSlots W) {
     const int slot = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t* d = W.d + (int64_t)slot * W.cap_n * LS_LANES;
-    const int32_t* order = W.order + (int64_t)slot * W.cap_order;
+    const LsEnt* order = W.order + (int64_t)slot * W.cap_order;
     const int olen = W.hdr[slot * 4 + 0];
-    for (int e = warp; e < olen; e += blockDim.x / 32) d[(int64_t)order[e] * LS_LANES + lane] = DINF;
+    for (int e = warp; e < olen; e += blockDim.x / 32) d[(int64_t)order[e].u * LS_LANES + lane] = DINF;
     __syncthreads();
     if (threadIdx.x == 0) W.hdr[slot * 4 + 0] = 0;
 }
@@ -354,11 +394,9 @@ __global__ void fill_i32_kernel(int32_t* p, int32_t v, int64_t n) {
         p[i] = v;
 }
 
-}  // namespace
-
 template <typename DT>
-static void ls_launch_t(bool fused, bool weighted, bool mult, const LsArena& A, const LsParams& P, const LsSlots& W,
-                        const LsItem* items, int nitems, int slots, cudaStream_t st) {
+void ls_launch_t(bool fused, bool weighted, bool mult, const LsArena& A, const LsParams& P, const LsSlots& W,
+                 const LsItem* items, int nitems, int slots, cudaStream_t st) {
 #define LS_GO(F, WT, M) ls_kernel<DT, F, WT, M><<<slots, LS_THREADS, 0, st>>>(A, P, W, items, nitems)
     if (fused) {
         if (!weighted) LS_GO(true, false, false);
@@ -372,17 +410,18 @@ static void ls_launch_t(bool fused, bool weighted, bool mult, const LsArena& A, 
 #undef LS_GO
 }
 
+}  // namespace
+
 void ls_launch(bool fp32_delta, bool fused, const LsArena& A, const LsParams& P, const LsSlots& W,
                const LsItem* items, int nitems, int slots, cudaStream_t st) {
     if (nitems <= 0 || slots <= 0) return;
-    // arcs with multiplicities run the weighted kernel (a unit weight array is not needed:
-    // multiplicities > 1 only occur on skeleton arcs whose weights are > 1 as well)
-    LsArena B = A;
+    // multiplicities > 1 only occur on skeleton arcs, whose weights then exceed 1 as well,
+    // so a multiplicity array always comes with a weight array
     const bool mult = A.mu != nullptr;
     const bool weighted = A.w != nullptr;
     if (mult && !weighted) return;
-    if (fp32_delta) ls_launch_t<float>(fused, weighted, mult, B, P, W, items, nitems, slots, st);
-    else ls_launch_t<double>(fused, weighted, mult, B, P, W, items, nitems, slots, st);
+    if (fp32_delta) ls_launch_t<float>(fused, weighted, mult, A, P, W, items, nitems, slots, st);
+    else ls_launch_t<double>(fused, weighted, mult, A, P, W, items, nitems, slots, st);
 }
 
 void ls_reset_launch(const LsSlots& W, int slots, cudaStream_t st) {

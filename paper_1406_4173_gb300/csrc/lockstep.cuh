@@ -65,12 +65,19 @@ struct LsParams {
     uint32_t* flags;
 };
 
+// One settled (node, step) entry: the node and its out-arc range, read with one 16-byte load.
+struct __align__(16) LsEnt {
+    int32_t u;
+    int32_t deg;
+    int64_t a0;
+};
+
 struct LsSlots {
     int32_t* d;                  // [slot][cap_n][32]
     uint64_t* sg;                // [slot][cap_n][32]
     void* dl;                    // [slot][cap_n][32] of DT: (I_{v in S} + delta) / sigma
     int64_t cap_n;
-    int32_t* order;              // [slot][cap_order] settled (node, step) entries
+    LsEnt* order;                // [slot][cap_order] settled (node, step) entries, in step order
     int64_t cap_order;
     int32_t* step_d;             // [slot][cap_steps] distance of each non-empty step
     int32_t* step_beg;           // [slot][cap_steps] first entry of each step
@@ -78,8 +85,8 @@ struct LsSlots {
     uint32_t* bm;                // [slot][nb][bm_words] bucket bitmaps
     int64_t bm_words;
     uint8_t* bflag;              // [slot][nb] bucket non-empty flags
-    double* bc_sum;              // [slot][cap_bc] partial betweenness (Neumaier sum)
-    double* bc_cmp;              // [slot][cap_bc] compensation
+    double* bc_sum;              // [slot][cap_bc] partial betweenness (sum)
+    double* bc_cmp;              // [slot][cap_bc] compensation (Neumaier, where a kernel keeps one)
     int64_t cap_bc;
     int32_t* hdr;                // [slot][4]: order length, steps, item, -
 };

@@ -8,7 +8,7 @@
 // their inputs and output.
 //
 // The array is part of the library image: every GPU that loads the library holds it (about
-// 27 MB) until the process exits.  All calls share it and it keeps the last call's contents;
+// 40 MB) until the process exits.  All calls share it and it keeps the last call's contents;
 // each call clears what must start at zero.  Calls whose work overlaps on the GPU (other
 // streams, other host threads) race on the array; serialize them.
 #include <mutex>
@@ -36,7 +36,7 @@ struct NaScratch {
     int32_t d[NA_SLOTS][NA_NODES][LS_LANES];
     uint64_t sg[NA_SLOTS][NA_NODES][LS_LANES];
     double dl[NA_SLOTS][NA_NODES][LS_LANES];
-    int32_t order[NA_SLOTS][NA_CAP_ORDER];
+    LsEnt order[NA_SLOTS][NA_CAP_ORDER];
     int32_t step_d[NA_SLOTS][NA_CAP_STEPS];
     int32_t step_beg[NA_SLOTS][NA_CAP_STEPS];
     uint32_t bm[NA_SLOTS][NA_NB][NA_BM_WORDS];
