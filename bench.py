@@ -153,23 +153,31 @@ def dist_env():
 
 
 # ----------------------------------------------------------------------------- cpu baseline (oracle)
-def oracle_sample_rate(g, part, seconds):
-    """Oracle plain Brandes + Brandes++ from a bounded sample of sources (targets = V)."""
+def oracle_sample(g, S_order, part, seconds, with_pp=True):
+    """Oracle plain Brandes (+ Brandes++) from the first `ns` sources of S_order (targets = all
+    of S_order), ns a multiple of 32 sized to the time budget.  Returns (ns, t_plain, t_pp,
+    unhalved plain partial betweenness of those sources)."""
     import oracle
     oracle.build()
-    S = np.arange(g.n, dtype=np.int32)
-    # calibrate on 8 sources, then size the sample to the budget
+    S = np.ascontiguousarray(S_order, np.int32)
     t0 = time.perf_counter()
-    oracle.brandes(g, None, nsrc=8)
-    oracle.brandes_pp(g, S, part, nsrc=8)
+    oracle.brandes(g, S, nsrc=8)
     per = (time.perf_counter() - t0) / 8
-    ns = int(max(8, min(g.n, seconds / max(per, 1e-6))))
+    if with_pp:
+        t0 = time.perf_counter()
+        oracle.brandes_pp(g, S, part, nsrc=8)
+        per += (time.perf_counter() - t0) / 8
+    nb = (len(S) + 31) // 32
+    want = int(max(1, min(nb, seconds / max(per, 1e-6) / 32)))
+    count = max(1, nb // want)
+    ns = min(len(S), 32 * (nb // count))
     t0 = time.perf_counter()
-    oracle.brandes(g, None, nsrc=ns)
+    part_bc, _ = oracle.brandes(g, S, nsrc=ns, halve=False)
     t1 = time.perf_counter()
-    oracle.brandes_pp(g, S, part, nsrc=ns)
+    if with_pp:
+        oracle.brandes_pp(g, S, part, nsrc=ns)
     t2 = time.perf_counter()
-    return ns, t1 - t0, t2 - t1
+    return ns, count, t1 - t0, t2 - t1, part_bc
 
 
 def run_reference(args):
@@ -177,37 +185,59 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_1406_4173_gb300 import gen
-    g, S = gen.workload(args.workload)
     import oracle
     oracle.build()
-    Sall = np.arange(g.n, dtype=np.int32) if S is None else S
-    # size each step to ~4 s of oracle work
-    t0 = time.perf_counter()
-    oracle.brandes(g, Sall, nsrc=4)
-    oracle.brandes_pp(g, Sall, g.part, nsrc=4)
-    per = (time.perf_counter() - t0) / 4
-    ns = int(max(4, min(len(Sall), 4.0 / max(per, 1e-6))))
+    g, S = gen.workload(args.workload)
+    if isinstance(g, list):
+        graphs = g
+        per = []
 
-    def step():
-        oracle.brandes(g, Sall, nsrc=ns)
-        oracle.brandes_pp(g, Sall, g.part, nsrc=ns)
+        def step():
+            t0 = time.perf_counter()
+            u = 0.0
+            for gi in graphs[:64]:
+                oracle.brandes(gi)
+                u += gi.n * gi.m
+            per.append(u)
+            return time.perf_counter() - t0
 
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    dt = time.perf_counter() - t0
-    units = 2.0 * ns * g.m * args.steps
-    val = units / dt
+        for _ in range(args.warmup):
+            step()
+        per.clear()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+        dt = time.perf_counter() - t0
+        val = sum(per) / dt
+        sample = "first 64 graphs per step, full betweenness each"
+        cfg = {"workload": args.workload, "graphs_per_step": 64}
+    else:
+        Sall = np.arange(g.n, dtype=np.int32) if S is None else np.asarray(S, np.int32)
+        t0 = time.perf_counter()
+        oracle.brandes(g, Sall, nsrc=4)
+        oracle.brandes_pp(g, Sall, g.part, nsrc=4)
+        per_src = (time.perf_counter() - t0) / 4
+        ns = int(max(4, min(len(Sall), 4.0 / max(per_src, 1e-6))))
+
+        def step():
+            oracle.brandes(g, Sall, nsrc=ns)
+            oracle.brandes_pp(g, Sall, g.part, nsrc=ns)
+
+        for _ in range(args.warmup):
+            step()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+        dt = time.perf_counter() - t0
+        val = 2.0 * ns * g.m * args.steps / dt
+        sample = f"first {ns} of {len(Sall)} sources per step (targets = S), plain + Brandes++"
+        cfg = {"workload": args.workload, "n": g.n, "m": g.m, "S": len(Sall), "sample_sources_per_step": ns}
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "n": g.n, "m": g.m, "S": len(Sall),
-                   "sample_sources_per_step": ns},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{ns} of {len(Sall)} sources per step (targets = S), plain + Brandes++"},
+        "config": cfg,
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -215,6 +245,26 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- ours
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(ws, x, dev):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1.0))) if a.size else 0.0
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -228,70 +278,88 @@ def run_ours(args):
     from paper_1406_4173_gb300 import _build, gen
     _build.build()
     dev = torch.device("cuda", torch.cuda.current_device())
-
+    ctx = bc.default_context()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     g, S = gen.workload(args.workload)
     if isinstance(g, list):
-        raise SystemExit("bench: use a single-graph workload")
+        line = _run_batched(args, bc, g, ctx, flush, dev, ws, rank)
+    else:
+        line = _run_single(args, bc, gen, g, S, ctx, flush, dev, ws, rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def _timed(args, ws, dev, step):
+    """W warm-up steps, then K steps between barriers and device syncs; clock samples."""
+    import torch
+    for _ in range(args.warmup):
+        step()
+    clk = Clocks(torch.cuda.current_device())
+    _barrier(ws)
+    torch.cuda.synchronize()
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    logs = []
+    e0.record()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        logs.append(step())
+    e1.record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    _barrier(ws)
+    clocks = clk.stop()
+    dt = _max_over_ranks(ws, e0.elapsed_time(e1) / 1e3, dev)
+    return dt, wall, logs, clocks
+
+
+def _run_single(args, bc, gen, g, S, ctx, flush, dev, ws, rank):
+    import torch
     n, m = g.n, g.m
-    nS = n if S is None else len(S)
+    S_order = np.arange(n, dtype=np.int32) if S is None else np.asarray(S, np.int32)
+    nS = len(S_order)
     Sarg = None if S is None or len(S) == n else S
+    prec = args.precision
     part = torch.as_tensor(g.part, device=dev)
     G = bc.graph_from_edgelist(g)
     A = G.num_arcs
     bc_plain = torch.empty(n, dtype=torch.float64, device=dev)
     bc_pp = torch.empty(n, dtype=torch.float64, device=dev)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    ctx = bc.default_context()
-
-    stats_log = []
 
     def step():
         flush.fill_(1)
-        _, s1 = bc.brandes(G, Sarg, precision=args.precision, out=bc_plain, stats=True, ctx=ctx)
-        _, s2 = bc.brandes_pp(G, Sarg, part, precision=args.precision, out=bc_pp, stats=True, ctx=ctx)
-        stats_log.append((s1, s2))
+        _, s1 = bc.brandes(G, Sarg, precision=prec, out=bc_plain, stats=True, ctx=ctx)
+        _, s2 = bc.brandes_pp(G, Sarg, part, precision=prec, out=bc_pp, stats=True, ctx=ctx)
+        return s1, s2
 
-    for _ in range(args.warmup):
-        step()
-    stats_log.clear()
-
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    clk = Clocks(torch.cuda.current_device())
-    barrier()
-    torch.cuda.synchronize()
-    clk.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    e1.record()
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    barrier()
-    clocks = clk.stop()
-    dt = e0.elapsed_time(e1) / 1e3
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([dt], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
+    dt, wall, logs, clocks = _timed(args, ws, dev, step)
     units_per_step = 2.0 * nS * m
     value = units_per_step * args.steps * ws / dt
-
-    plain_ms = [s1["ms_total"] for s1, _ in stats_log]
-    pp_ms = [s2["ms_total"] for _, s2 in stats_log]
-    ls_ms = [s1["ms_brandes_sk"] for s1, _ in stats_log]
-    launches = int(sum(s1["kernel_launches"] + s2["kernel_launches"] for s1, s2 in stats_log)) + args.steps
-    s_pp = stats_log[-1][1]
-
-    # exactness at full size: Brandes++ must equal plain Brandes (both FP64 on the GPU)
+    plain_ms = statistics.mean(s1["ms_total"] for s1, _ in logs)
+    pp_ms = statistics.mean(s2["ms_total"] for _, s2 in logs)
+    ls_ms = statistics.mean(s1["ms_brandes_sk"] for s1, _ in logs)
+    launches = int(sum(s1["kernel_launches"] + s2["kernel_launches"] for s1, s2 in logs)) + args.steps
+    s_pp = logs[-1][1]
     a, b = bc_plain.cpu().numpy(), bc_pp.cpu().numpy()
-    pp_vs_plain = float(np.max(np.abs(a - b) / np.maximum(np.abs(a), 1.0)))
+    pp_vs_plain = _rel(b, a)
+
+    # the other precision, measured once (untimed in the headline)
+    other = "fp32" if prec == "fp64" else "fp64"
+    flush.fill_(1)
+    x1, o1 = bc.brandes(G, Sarg, precision=other, stats=True, ctx=ctx)
+    flush.fill_(1)
+    x2, o2 = bc.brandes_pp(G, Sarg, part, precision=other, stats=True, ctx=ctx)
+    ref64 = a if prec == "fp64" else x1.cpu().numpy()
+    got32 = x1.cpu().numpy() if prec == "fp64" else a
+    fp32 = {"plain_ms": o1["ms_total"] if prec == "fp64" else plain_ms,
+            "pp_ms": o2["ms_total"] if prec == "fp64" else pp_ms,
+            "plain_fp64_ms": plain_ms if prec == "fp64" else o1["ms_total"],
+            "max_rel_err_fp32_vs_fp64": _rel(got32, ref64)}
+    fp32["speedup_fp32_over_fp64_plain"] = fp32["plain_fp64_ms"] / fp32["plain_ms"]
 
     # roofline of the dominant kernel (lockstep forward+backward of plain Brandes)
     sample = np.linspace(0, n - 1, 32).astype(np.int32)
@@ -299,24 +367,23 @@ def run_ours(args):
     dist_s = dist_s.cpu().numpy().astype(np.int64)
     rp = G.row_ptr.cpu().numpy()
     col = G.col.cpu().numpy()
+    wts = None if G.w is None else G.w.cpu().numpy().astype(np.int64)
     tails = np.repeat(np.arange(n), np.diff(rp))
     tight = []
     for i in range(len(sample)):
-        d = dist_s[i]
-        ok = (d[tails] < np.iinfo(np.int32).max) & (d[col] == d[tails] + 1)
+        dd = dist_s[i]
+        ok = (dd[tails] < np.iinfo(np.int32).max) & (dd[col] == dd[tails] + (1 if wts is None else wts))
         tight.append(int(ok.sum()))
     D_avg = float(np.mean(tight))
-    delta_bytes = 4 if args.precision == "fp32" else 8
+    delta_bytes = 4 if prec == "fp32" else 8
     bytes_launch = model_bytes_per_source(n, A, D_avg, 32, delta_bytes) * nS
-    ls_avg_s = statistics.mean(ls_ms) / 1e3
     peak, peak_kind = measured_peak_hbm()
-    achieved = bytes_launch / ls_avg_s / 1e9
-    traffic = profiled_traffic(args.workload)
+    achieved = bytes_launch / (ls_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "ls_kernel (plain Brandes, forward + backward)",
-                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                "traffic": profiled_traffic(args.workload), "kernel": "ls_kernel (plain Brandes, forward + backward)",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s", "algorithmic_bytes_per_launch": bytes_launch,
-                "avg_launch_ms": ls_avg_s * 1e3, "tight_arcs_per_source": D_avg}
+                "avg_launch_ms": ls_ms, "tight_arcs_per_source": D_avg}
 
     # end to end: host buffers through the C ABI (copies inside the timed region)
     e2e = None
@@ -325,57 +392,116 @@ def run_ours(args):
         part_h = np.ascontiguousarray(g.part, np.int32)
         out1 = torch.empty(n, dtype=torch.float64).pin_memory()
         out2 = torch.empty(n, dtype=torch.float64).pin_memory()
-        bc.brandes_host(H, Sarg, precision=args.precision, ctx=ctx, out=out1)
+        bc.brandes_host(H, Sarg, precision=prec, ctx=ctx, out=out1)
         torch.cuda.synchronize()
-        barrier()
+        _barrier(ws)
         t0 = time.perf_counter()
         for _ in range(args.steps):
             flush.fill_(1)
-            bc.brandes_host(H, Sarg, precision=args.precision, ctx=ctx, out=out1)
-            bc.brandes_pp_host(H, Sarg, part_h, precision=args.precision, ctx=ctx, out=out2)
+            bc.brandes_host(H, Sarg, precision=prec, ctx=ctx, out=out1)
+            bc.brandes_pp_host(H, Sarg, part_h, precision=prec, ctx=ctx, out=out2)
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
+        te = _max_over_ranks(ws, time.perf_counter() - t0, dev)
         in_bytes = (H.row_ptr.numel() * 8 + H.col.numel() * 4 + (0 if H.w is None else H.w.numel() * 4)
                     + (0 if Sarg is None else 4 * len(Sarg)))
         e2e = {"value": units_per_step * args.steps * ws / te, "unit": UNIT,
                "h2d_bytes_per_step": int(2 * in_bytes + 4 * n), "d2h_bytes_per_step": int(2 * 8 * n)}
 
-    cpu = None
+    # CPU oracle on a bounded sample of sources; the same sources' partial sums on the GPU
+    cpu, err_oracle = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        ns_c, tp, tpp = oracle_sample_rate(g, g.part, args.cpu_seconds)
+        ns_c, count, tp, tpp, ref_part = oracle_sample(g, S_order, g.part, args.cpu_seconds)
         cpu = {"value": 2.0 * ns_c * m / (tp + tpp), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{ns_c} of {nS} sources (targets = S), oracle plain Brandes + Brandes++, "
+               "sample": f"first {ns_c} of {nS} sources (targets = S), oracle plain Brandes + Brandes++, "
                          f"{tp:.1f} s + {tpp:.1f} s"}
+        got = bc.brandes(G, Sarg, precision=prec, halve=False, shard=(0, count), ctx=ctx).cpu().numpy()
+        err_oracle = {"sources": ns_c, "max_rel_err_plain": _rel(got, ref_part)}
 
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32-delta+f64",
-            "data": "synthetic",
-            "config": {"workload": args.workload, "n": n, "m": m, "arcs": A, "S": nS,
-                       "step": "plain Brandes + Brandes++ (Alg. 1), S = V, planted partition",
-                       "l2": "flushed before every step (512 MiB write)",
-                       "precision": args.precision, "multi_gpu": "independent replicas (weak scaling)"},
-            "plain": {"teps": nS * m / (statistics.mean(plain_ms) / 1e3), "ms": statistics.mean(plain_ms)},
-            "brandes_pp": {"teps": nS * m / (statistics.mean(pp_ms) / 1e3), "ms": statistics.mean(pp_ms),
-                           "ms_build_sk": s_pp["ms_build_sk"], "ms_brandes_sk": s_pp["ms_brandes_sk"],
-                           "ms_centrality": s_pp["ms_centrality"], "N": s_pp["skel_nodes"],
-                           "M": s_pp["skel_edges"], "k": s_pp["k"], "LCS": s_pp["lcs"]},
-            "speedup_pp_over_plain": statistics.mean(plain_ms) / statistics.mean(pp_ms),
-            "max_rel_err_pp_vs_plain": pp_vs_plain,
-            "wall_s": wall,
-            "gpu_launches": launches,
-            "roofline": roofline,
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            "clocks": clocks,
-        }
-        print(json.dumps(line), flush=True)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
-    return 0
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32-delta+f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "m": m, "arcs": A, "S": nS, "directed": g.directed,
+                   "weighted": g.w is not None,
+                   "step": "plain Brandes + Brandes++ (Alg. 1) with the planted partition",
+                   "l2": "flushed before every step (512 MiB write)", "precision": prec,
+                   "multi_gpu": "independent replicas (weak scaling)"},
+        "plain": {"teps": nS * m / (plain_ms / 1e3), "ms": plain_ms},
+        "brandes_pp": {"teps": nS * m / (pp_ms / 1e3), "ms": pp_ms, "ms_build_sk": s_pp["ms_build_sk"],
+                       "ms_brandes_sk": s_pp["ms_brandes_sk"], "ms_centrality": s_pp["ms_centrality"],
+                       "N": s_pp["skel_nodes"], "M": s_pp["skel_edges"], "k": s_pp["k"], "LCS": s_pp["lcs"],
+                       "table_entries": s_pp["table_entries"]},
+        "speedup_pp_over_plain": plain_ms / pp_ms,
+        "max_rel_err_pp_vs_plain": pp_vs_plain,
+        "rel_err_vs_oracle": err_oracle,
+        "fp32_delta": fp32,
+        "wall_s": wall,
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+    }
+
+
+def _run_batched(args, bc, graphs, ctx, flush, dev, ws, rank):
+    import torch
+    prec = args.precision
+    arena = bc.build_arena(graphs)
+    units_per_step = float(sum(g.n * g.m for g in graphs))
+    out = torch.empty(arena.graph.n, dtype=torch.float64, device=dev)
+
+    def step():
+        flush.fill_(1)
+        _, st = bc.brandes_batched(arena, precision=prec, out=out, stats=True, ctx=ctx)
+        return st
+
+    dt, wall, logs, clocks = _timed(args, ws, dev, step)
+    value = units_per_step * args.steps * ws / dt
+    ms = statistics.mean(st["ms_total"] for st in logs)
+    launches = int(sum(st["kernel_launches"] for st in logs)) + args.steps
+    other = "fp32" if prec == "fp64" else "fp64"
+    flush.fill_(1)
+    x, so = bc.brandes_batched(arena, precision=other, stats=True, ctx=ctx)
+    a, b = out.cpu().numpy(), x.cpu().numpy()
+    ref64, got32 = (a, b) if prec == "fp64" else (b, a)
+    fp32 = {"ms": so["ms_total"] if prec == "fp64" else ms, "fp64_ms": ms if prec == "fp64" else so["ms_total"],
+            "max_rel_err_fp32_vs_fp64": _rel(got32, ref64)}
+    cpu, err_oracle = None, None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        errs, done, u = [], 0, 0.0
+        off = arena.node_ptr_host
+        for i, gi in enumerate(graphs):
+            ref, _ = oracle.brandes(gi)
+            errs.append(_rel(a[off[i]:off[i + 1]], ref))
+            done += 1
+            u += gi.n * gi.m
+            if time.perf_counter() - t0 > args.cpu_seconds:
+                break
+        tc = time.perf_counter() - t0
+        cpu = {"value": u / tc, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {done} of {len(graphs)} graphs, full betweenness each"}
+        err_oracle = {"graphs": done, "max_rel_err": max(errs)}
+    ns = np.array([g.n for g in graphs])
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == "fp64" else "f32-delta+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "graphs": len(graphs), "nodes": int(ns.sum()),
+                   "n_median": float(np.median(ns)), "n_max": int(ns.max()),
+                   "step": "full betweenness of every graph in one launch (plain Brandes)",
+                   "units": "sum over graphs of n_g * m_g", "l2": "flushed before every step (512 MiB write)",
+                   "precision": prec},
+        "plain": {"teps": value / ws, "ms": ms},
+        "rel_err_vs_oracle": err_oracle,
+        "fp32_delta": fp32,
+        "wall_s": wall, "gpu_launches": launches, "roofline": None, "cpu_baseline": cpu, "e2e": None,
+        "clocks": clocks,
+    }
 
 
 def main():
