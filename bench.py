@@ -155,8 +155,9 @@ def dist_env():
 # ----------------------------------------------------------------------------- cpu baseline (oracle)
 def oracle_sample(g, S_order, part, seconds, with_pp=True):
     """Oracle plain Brandes (+ Brandes++) from the first `ns` sources of S_order (targets = all
-    of S_order), ns a multiple of 32 sized to the time budget.  Returns (ns, t_plain, t_pp,
-    unhalved plain partial betweenness of those sources)."""
+    of S_order), ns = |S| // count sized to the time budget, so that GPU shard 0 of `count`
+    covers the same sources.  Returns (ns, count, t_plain, t_pp, unhalved plain partial
+    betweenness of those sources)."""
     import oracle
     oracle.build()
     S = np.ascontiguousarray(S_order, np.int32)
@@ -167,10 +168,9 @@ def oracle_sample(g, S_order, part, seconds, with_pp=True):
         t0 = time.perf_counter()
         oracle.brandes_pp(g, S, part, nsrc=8)
         per += (time.perf_counter() - t0) / 8
-    nb = (len(S) + 31) // 32
-    want = int(max(1, min(nb, seconds / max(per, 1e-6) / 32)))
-    count = max(1, nb // want)
-    ns = min(len(S), 32 * (nb // count))
+    want = int(max(1, min(len(S), seconds / max(per, 1e-6))))
+    count = max(1, len(S) // want)
+    ns = len(S) // count                  # shard 0 of `count` covers positions [0, ns)
     t0 = time.perf_counter()
     part_bc, _ = oracle.brandes(g, S, nsrc=ns, halve=False)
     t1 = time.perf_counter()

@@ -67,16 +67,22 @@ typedef struct {
 typedef struct {
     int32_t precision;         /* BCPP_FP64 (default) or BCPP_FP32_DELTA */
     int32_t halve_undirected;  /* 1 (default): halve undirected results; 0: ordered-pair sums */
-    int32_t batch;             /* source lanes per batch: 0 = default (32, the only value today) */
+    int32_t batch;             /* sources per batch: 0 = auto (64 when 64-source batches still fill every
+                                * resident CTA, else 32), 32 or 64.  64 applies to plain Brandes passes
+                                * (bcpp_brandes, bcpp_brandes_batched, Brandes++ without non-frontier
+                                * nodes); Dijkstra_SK, Brandes_SK with Centrality and bcpp_sssp use 32. */
     int32_t ctas_per_sm;       /* resident source batches per SM: 0 = auto */
     int32_t validate;          /* reserved: the CSR, S and the partition are always checked */
     int32_t host_buffers;      /* 1: array arguments are host pointers (copied in and out) */
     int32_t order_sources;     /* 1 (default): batch targets of the same part together (Brandes++) */
     int32_t shard_index;       /* with shard_count > 1: use only this shard's targets as sources */
-    int32_t shard_count;       /* 0 or 1: every target is a source.  Otherwise the source batches are
-                                * split into shard_count contiguous shards; the result is this shard's
-                                * partial sum (targets stay all of S), so the shards' results add up to
-                                * the unsharded result (multi-GPU source sharding). */
+    int32_t shard_count;       /* 0 or 1: every target is a source.  Otherwise the targets, in the order
+                                * used for batching, are split into shard_count contiguous shards
+                                * (shard r: positions [|S| r / R, |S| (r+1) / R)); only shard_index's
+                                * targets are sources and the result is that shard's partial sum
+                                * (targets stay all of S), so the shards' results add up to the
+                                * unsharded result (multi-GPU source sharding).  Plain Brandes batches
+                                * S in the given order; Brandes++ in the order of order_sources. */
 } bcpp_opts;
 
 typedef struct {

@@ -174,7 +174,8 @@ class Graph:
                        None if self.w is None else self.w.data_ptr(), int(self.directed))
 
 
-def _opts(precision="fp64", halve=True, ctas_per_sm=0, host=False, order_sources=True, shard=None) -> c_opts:
+def _opts(precision="fp64", halve=True, ctas_per_sm=0, host=False, order_sources=True, shard=None,
+          batch=0) -> c_opts:
     o = c_opts()
     load_library().bcpp_default_opts(ctypes.byref(o))
     o.precision = {"fp64": BCPP_FP64, "fp32": BCPP_FP32_DELTA, "fp32_delta": BCPP_FP32_DELTA}[precision]
@@ -184,6 +185,7 @@ def _opts(precision="fp64", halve=True, ctas_per_sm=0, host=False, order_sources
     o.order_sources = 1 if order_sources else 0
     if shard is not None:
         o.shard_index, o.shard_count = int(shard[0]), int(shard[1])
+    o.batch = int(batch)
     return o
 
 
@@ -233,7 +235,8 @@ def csr_validate(G: Graph, ctx: Context | None = None) -> None:
 
 # ----------------------------------------------------------------------------- betweenness
 def brandes(G: Graph, S=None, precision: str = "fp64", halve: bool = True, ctx: Context | None = None,
-            ctas_per_sm: int = 0, out=None, stats: bool = False, allow_overflow: bool = False, shard=None):
+            ctas_per_sm: int = 0, out=None, stats: bool = False, allow_overflow: bool = False, shard=None,
+            batch: int = 0):
     """Plain Brandes, target set S (None = all nodes).  Returns a float64 device tensor [n]
     (and the stats dict when stats=True).  shard=(index, count) computes one shard's partial
     sum over the sources (the shards add up to the full result)."""
@@ -245,7 +248,7 @@ def brandes(G: Graph, S=None, precision: str = "fp64", halve: bool = True, ctx: 
     bc = out if out is not None else torch.empty(G.n, dtype=torch.float64, device=dev)
     st = c_stats()
     cg = G.c()
-    o = _opts(precision, halve, ctas_per_sm, shard=shard)
+    o = _opts(precision, halve, ctas_per_sm, shard=shard, batch=batch)
     rc = load_library().bcpp_brandes(ctx.handle, ctypes.byref(cg), None if nS == 0 else St.data_ptr(), nS,
                                      ctypes.byref(o), bc.data_ptr(), ctypes.byref(st))
     _check(rc, allow_overflow)
@@ -254,7 +257,7 @@ def brandes(G: Graph, S=None, precision: str = "fp64", halve: bool = True, ctx: 
 
 def brandes_pp(G: Graph, S, part, k: int | None = None, precision: str = "fp64", halve: bool = True,
                ctx: Context | None = None, ctas_per_sm: int = 0, order_sources: bool = True, out=None,
-               stats: bool = False, allow_overflow: bool = False, shard=None):
+               stats: bool = False, allow_overflow: bool = False, shard=None, batch: int = 0):
     """Brandes++ (Build_SK, Brandes_SK, Centrality) for target set S (None = all nodes) and
     node partition `part` with values in [0, k)."""
     torch = _torch()
@@ -268,7 +271,7 @@ def brandes_pp(G: Graph, S, part, k: int | None = None, precision: str = "fp64",
     bc = out if out is not None else torch.empty(G.n, dtype=torch.float64, device=dev)
     st = c_stats()
     cg = G.c()
-    o = _opts(precision, halve, ctas_per_sm, order_sources=order_sources, shard=shard)
+    o = _opts(precision, halve, ctas_per_sm, order_sources=order_sources, shard=shard, batch=batch)
     rc = load_library().bcpp_brandes_pp(ctx.handle, ctypes.byref(cg), None if nS == 0 else St.data_ptr(), nS,
                                         pt.data_ptr(), int(k), ctypes.byref(o), bc.data_ptr(), ctypes.byref(st))
     _check(rc, allow_overflow)
@@ -298,7 +301,8 @@ def build_arena(graphs, ctx: Context | None = None) -> Arena:
 
 
 def brandes_batched(arena: Arena, precision: str = "fp64", halve: bool = True, ctx: Context | None = None,
-                    ctas_per_sm: int = 0, out=None, stats: bool = False, allow_overflow: bool = False):
+                    ctas_per_sm: int = 0, out=None, stats: bool = False, allow_overflow: bool = False,
+                    batch: int = 0):
     """Full betweenness of every graph of the arena in one launch."""
     torch = _torch()
     ctx = ctx or default_context()
@@ -306,7 +310,7 @@ def brandes_batched(arena: Arena, precision: str = "fp64", halve: bool = True, c
     bc = out if out is not None else torch.empty(G.n, dtype=torch.float64, device=G.row_ptr.device)
     st = c_stats()
     cg = G.c()
-    o = _opts(precision, halve, ctas_per_sm)
+    o = _opts(precision, halve, ctas_per_sm, batch=batch)
     rc = load_library().bcpp_brandes_batched(ctx.handle, len(arena.node_ptr_host) - 1, arena.node_ptr.data_ptr(),
                                              ctypes.byref(cg), ctypes.byref(o), bc.data_ptr(), ctypes.byref(st))
     _check(rc, allow_overflow)

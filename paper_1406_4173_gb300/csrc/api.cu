@@ -29,7 +29,7 @@ struct bcpp_ctx {
     uint32_t* flags = nullptr;       // device [FLAG_COUNT]
     uint32_t* hflags = nullptr;      // pinned host copy
     int64_t launches = 0;
-    int order_factor = 8;            // settled-entry capacity per node of a batch (retry: 32)
+    int order_factor = 8;            // settled-entry capacity per node of a batch (retry: worst case)
     cudaEvent_t ev[8] = {};
 
     void* acquire(size_t bytes) {
@@ -178,15 +178,32 @@ __global__ void i64_from_i32_kernel(const int32_t* in, int64_t* out, int64_t n) 
         out[i] = in[i];
 }
 
-// batches [b0, b1) of this shard (all batches when unsharded)
-void shard_range(const bcpp_opts& o, int nitems, int& b0, int& b1) {
-    b0 = 0;
-    b1 = nitems;
+// sources [s0, s1) of this shard: shard r of R takes sources [ns*r/R, ns*(r+1)/R)
+void shard_sources(const bcpp_opts& o, int64_t ns, int64_t& s0, int64_t& s1) {
+    s0 = 0;
+    s1 = ns;
     if (o.shard_count > 1) {
         const int64_t r = std::max(0, std::min(o.shard_index, o.shard_count - 1));
-        b0 = (int)((int64_t)nitems * r / o.shard_count);
-        b1 = (int)((int64_t)nitems * (r + 1) / o.shard_count);
+        s0 = ns * r / o.shard_count;
+        s1 = ns * (r + 1) / o.shard_count;
     }
+}
+
+// batches of `lanes` consecutive sources of [s0, s1) of graph g
+std::vector<LsItem> make_items(int32_t g, int64_t s0, int64_t s1, int lanes) {
+    std::vector<LsItem> v;
+    for (int64_t b = s0; b < s1; b += lanes)
+        v.push_back(LsItem{g, (int32_t)b, (int32_t)std::min<int64_t>(lanes, s1 - b), 0});
+    return v;
+}
+
+// sources per lane: opts.batch 32 or 64 forces it; 0 picks 64-source batches (two per lane)
+// when they still fill every resident CTA
+int choose_spl(const bcpp_ctx* c, int64_t nsources_total, const bcpp_opts& o) {
+    if (o.batch == 32) return 1;
+    if (o.batch == 64) return 2;
+    const int cps = o.ctas_per_sm > 0 ? o.ctas_per_sm : 2;
+    return (nsources_total + 63) / 64 >= (int64_t)cps * c->num_sms ? 2 : 1;
 }
 
 int bits_for(uint64_t maxval) {
@@ -242,11 +259,15 @@ struct SlotWs {
     LsSlots W{};
 };
 
-int64_t slot_bytes(int64_t cap_n, int nb, bool fp32, int order_factor = 8) {
-    const int64_t cap_order = order_factor * cap_n + 1024;
+int64_t order_capacity(int64_t cap_n, int order_factor, int spl) {
+    return (int64_t)std::min(order_factor, 32 * spl) * cap_n + 1024;
+}
+
+int64_t slot_bytes(int64_t cap_n, int nb, bool fp32, int order_factor = 8, int spl = 1) {
+    const int64_t cap_order = order_capacity(cap_n, order_factor, spl);
     const int64_t bm_words = (cap_n + 31) / 32;
-    return cap_n * 32 * (4 + 8 + (fp32 ? 4 : 8)) + cap_order * (int64_t)sizeof(LsEnt) + 2 * (cap_n + 4098) * 4 +
-           (int64_t)nb * bm_words * 4 + nb;
+    return cap_n * 32 * spl * (4 + 8 + (fp32 ? 4 : 8)) + cap_order * (int64_t)sizeof(LsEnt) +
+           2 * (cap_n + 4098) * 4 + (int64_t)nb * bm_words * 4 + nb;
 }
 
 // Choose how many slots (resident batches) to run, within the memory budget.
@@ -264,14 +285,15 @@ int choose_slots(bcpp_ctx* c, int nitems, int ctas_per_sm, int64_t per_slot, int
     return std::max(1, slots);
 }
 
-int alloc_slots(bcpp_ctx* c, SlotWs& S, int slots, int64_t cap_n, int nb, bool fp32, int64_t cap_bc) {
-    if (cap_n >= (1 << 26)) return BCPP_EINVAL;   // 32-bit row offsets inside a slot
-    const int64_t cap_order = (int64_t)c->order_factor * cap_n + 1024;
+int alloc_slots(bcpp_ctx* c, SlotWs& S, int slots, int64_t cap_n, int nb, bool fp32, int64_t cap_bc, int spl = 1) {
+    if (cap_n >= (1 << 25)) return BCPP_EINVAL;   // 32-bit row offsets inside a slot
+    const int64_t cap_order = order_capacity(cap_n, c->order_factor, spl);
+    const int64_t rows = cap_n * spl;              // rows of 32 values
     const int32_t cap_steps = (int32_t)std::min<int64_t>(cap_order, 4 * (cap_n + 2) + 4096);
     const int64_t bm_words = (cap_n + 31) / 32;
-    CK_ALLOC(S.d.alloc(c, (int64_t)slots * cap_n * 32));
-    CK_ALLOC(S.sg.alloc(c, (int64_t)slots * cap_n * 32));
-    CK_ALLOC(S.dl.alloc(c, (int64_t)slots * cap_n * 32 * (fp32 ? 4 : 8)));
+    CK_ALLOC(S.d.alloc(c, (int64_t)slots * rows * 32));
+    CK_ALLOC(S.sg.alloc(c, (int64_t)slots * rows * 32));
+    CK_ALLOC(S.dl.alloc(c, (int64_t)slots * rows * 32 * (fp32 ? 4 : 8)));
     CK_ALLOC(S.order.alloc(c, (int64_t)slots * cap_order));
     CK_ALLOC(S.step_d.alloc(c, (int64_t)slots * cap_steps));
     CK_ALLOC(S.step_beg.alloc(c, (int64_t)slots * cap_steps));
@@ -285,7 +307,7 @@ int alloc_slots(bcpp_ctx* c, SlotWs& S, int slots, int64_t cap_n, int nb, bool f
         CK_CUDA(cudaMemsetAsync(S.bcs.p, 0, (size_t)slots * cap_bc * sizeof(double), c->stream));
         CK_CUDA(cudaMemsetAsync(S.bcc.p, 0, (size_t)slots * cap_bc * sizeof(double), c->stream));
     }
-    fill_i32(S.d.p, DINF, (int64_t)slots * cap_n * 32, c->stream);
+    fill_i32(S.d.p, DINF, (int64_t)slots * rows * 32, c->stream);
     c->launches++;
     CK_CUDA(cudaMemsetAsync(S.bm.p, 0, (size_t)slots * nb * bm_words * sizeof(uint32_t), c->stream));
     CK_CUDA(cudaMemsetAsync(S.bflag.p, 0, (size_t)slots * nb, c->stream));
@@ -398,13 +420,11 @@ int brandes_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, 
     InCsr T;
     if (g->directed) CK_RC(build_in_csr(c, g, T));
     // items: batches of 32 targets in the given order
-    int b0, b1;
-    shard_range(o, (int)((ns + LS_LANES - 1) / LS_LANES), b0, b1);
-    const int nitems = b1 - b0;
-    std::vector<LsItem> hitems(std::max(nitems, 0));
-    for (int i = 0; i < nitems; i++)
-        hitems[i] = LsItem{0, (b0 + i) * LS_LANES,
-                           (int32_t)std::min<int64_t>(LS_LANES, ns - (int64_t)(b0 + i) * LS_LANES), 0};
+    int64_t s0, s1;
+    shard_sources(o, ns, s0, s1);
+    const int spl = choose_spl(c, s1 - s0, o);
+    std::vector<LsItem> hitems = make_items(0, s0, s1, 32 * spl);
+    const int nitems = (int)hitems.size();
     if (nitems <= 0) {
         CK_CUDA(cudaMemsetAsync(bc_out, 0, (size_t)n * sizeof(double), c->stream));
         CK_CUDA(cudaStreamSynchronize(c->stream));
@@ -417,9 +437,10 @@ int brandes_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, 
     const int64_t hoff[2] = {0, n};
     CK_RC(to_dev(c, node_off.p, hoff, 2));
     const int nb = g->w ? (int)wmax + 1 : 2;
-    const int slots = choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(n, nb, fp32, c->order_factor), (int64_t)n * 16);
+    const int slots =
+        choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(n, nb, fp32, c->order_factor, spl), (int64_t)n * 16);
     SlotWs ws;
-    CK_RC(alloc_slots(c, ws, slots, n, nb, fp32, n));
+    CK_RC(alloc_slots(c, ws, slots, n, nb, fp32, n, spl));
     LsArena A{};
     A.rp = g->row_ptr; A.col = g->col; A.w = (const int32_t*)g->w; A.mu = nullptr;
     if (g->directed) {
@@ -439,7 +460,7 @@ int brandes_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, 
     P.flags = c->flags;
     Timer tb(c);
     tb.start();
-    ls_launch(fp32, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream);
+    ls_launch(fp32, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream, spl);
     c->launches++;
     tb.stop();
     CK_CUDA(cudaGetLastError());
@@ -747,13 +768,24 @@ int brandes_pp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t n
     const bool unit = K.wmax_sk == 1;
     const bool mult = K.mmax_sk > 1;
     const int nb = (int)K.wmax_sk + 1;
-    int b0, b1;
-    shard_range(o, (nt + LS_LANES - 1) / LS_LANES, b0, b1);
-    const int nitems = std::max(0, b1 - b0);
-    const int slots = nitems > 0 ? choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(std::max(N, 1), nb, fp32, c->order_factor),
+    int64_t s0, s1;
+    shard_sources(o, nt, s0, s1);
+    // Centrality work units: chunks of 64 non-frontier nodes of parts with frontiers
+    std::vector<CentralityUnit> hunits;
+    for (int32_t i = 0; i < K.kp; i++) {
+        const int32_t sz = K.h_pstart[i + 1] - K.h_pstart[i];
+        if (K.h_nf[i] < 1 || sz <= K.h_nf[i]) continue;
+        for (int32_t v0 = K.h_nf[i]; v0 < sz; v0 += 64) hunits.push_back({i, v0, std::min(sz, v0 + 64), 0});
+    }
+    // without non-frontier nodes Brandes_SK runs alone and may use 64-source batches
+    const int spl = hunits.empty() ? choose_spl(c, s1 - s0, o) : 1;
+    std::vector<LsItem> hitems = make_items(0, s0, s1, 32 * spl);
+    const int nitems = (int)hitems.size();
+    const int slots = nitems > 0 ? choose_slots(c, nitems, o.ctas_per_sm,
+                                                slot_bytes(std::max(N, 1), nb, fp32, c->order_factor, spl),
                                                 (int64_t)n * 16)
                                  : 1;
-    CK_RC(alloc_slots(c, ws, slots, std::max(N, 1), nb, fp32, n));
+    CK_RC(alloc_slots(c, ws, slots, std::max(N, 1), nb, fp32, n, spl));
     slots_used = slots;
     if (nitems > 0) {
         DBuf<uint8_t> sk_in_s(c, N);
@@ -793,19 +825,9 @@ int brandes_pp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t n
             A.irp = A.rp; A.icol = A.col; A.iw = A.w; A.imu = A.mu;
         }
         A.node_off = node_off.p;
-        // Centrality work units: chunks of 64 non-frontier nodes of parts with frontiers
-        std::vector<CentralityUnit> hunits;
-        for (int32_t i = 0; i < K.kp; i++) {
-            const int32_t sz = K.h_pstart[i + 1] - K.h_pstart[i];
-            if (K.h_nf[i] < 1 || sz <= K.h_nf[i]) continue;
-            for (int32_t v0 = K.h_nf[i]; v0 < sz; v0 += 64) hunits.push_back({i, v0, std::min(sz, v0 + 64), 0});
-        }
         DBuf<CentralityUnit> units(c, (int64_t)hunits.size());
         CK_ALLOC(units);
         CK_RC(to_dev(c, units.p, hunits.data(), (int64_t)hunits.size()));
-        std::vector<LsItem> hitems(nitems);
-        for (int i = 0; i < nitems; i++)
-            hitems[i] = LsItem{0, (b0 + i) * LS_LANES, std::min(LS_LANES, nt - (b0 + i) * LS_LANES), 0};
         DBuf<LsItem> items(c, nitems);
         CK_ALLOC(items);
         CK_RC(to_dev(c, items.p, hitems.data(), nitems));
@@ -821,7 +843,7 @@ int brandes_pp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t n
             P.item_counter = ws.counter.p;
             P.flags = c->flags;
             tbr.start();
-            ls_launch(fp32, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream);
+            ls_launch(fp32, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream, spl);
             c->launches++;
             tbr.stop();
             CK_CUDA(cudaGetLastError());
@@ -904,11 +926,15 @@ int batched_dev(bcpp_ctx* c, int32_t ngraphs, const int64_t* node_ptr_dev, const
     std::iota(gorder.begin(), gorder.end(), 0);
     std::stable_sort(gorder.begin(), gorder.end(),
                      [&](int32_t a, int32_t b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
+    int64_t total_sources = 0;
+    for (int32_t gi = 0; gi < ngraphs; gi++) total_sources += off[gi + 1] - off[gi] >= 2 ? off[gi + 1] - off[gi] : 0;
+    const int spl = choose_spl(c, total_sources, o);
     std::vector<LsItem> hitems;
     for (int32_t gi : gorder) {
         const int32_t ng = (int32_t)(off[gi + 1] - off[gi]);
         if (ng < 2) continue;
-        for (int32_t s0 = 0; s0 < ng; s0 += LS_LANES) hitems.push_back(LsItem{gi, s0, std::min(LS_LANES, ng - s0), 0});
+        const std::vector<LsItem> its = make_items(gi, 0, ng, 32 * spl);
+        hitems.insert(hitems.end(), its.begin(), its.end());
     }
     const int nitems = (int)hitems.size();
     if (nitems == 0) {
@@ -922,9 +948,10 @@ int batched_dev(bcpp_ctx* c, int32_t ngraphs, const int64_t* node_ptr_dev, const
     iota(srcs.p, maxn, c->stream);
     c->launches++;
     const int nb = g->w ? (int)wmax + 1 : 2;
-    const int slots = choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(maxn, nb, fp32, c->order_factor), (int64_t)n * 16);
+    const int slots =
+        choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(maxn, nb, fp32, c->order_factor, spl), (int64_t)n * 16);
     SlotWs ws;
-    CK_RC(alloc_slots(c, ws, slots, maxn, nb, fp32, n));
+    CK_RC(alloc_slots(c, ws, slots, maxn, nb, fp32, n, spl));
     LsArena A{};
     A.rp = g->row_ptr; A.col = lcol.p; A.w = (const int32_t*)g->w;
     A.irp = g->row_ptr; A.icol = lcol.p; A.iw = (const int32_t*)g->w;
@@ -936,7 +963,7 @@ int batched_dev(bcpp_ctx* c, int32_t ngraphs, const int64_t* node_ptr_dev, const
     P.item_counter = ws.counter.p;
     P.flags = c->flags;
     tb.start();
-    ls_launch(fp32, true, A, P, ws.W, items.p, nitems, slots, c->stream);
+    ls_launch(fp32, true, A, P, ws.W, items.p, nitems, slots, c->stream, spl);
     c->launches++;
     CK_CUDA(cudaGetLastError());
     combine_launch(ws.W.bc_sum, ws.W.bc_cmp, slots, n, n, o.halve_undirected ? 0.5 : 1.0, bc_out, c->stream);
@@ -1119,13 +1146,13 @@ int stage_graph(bcpp_ctx* c, const bcpp_graph* hg, StagedGraph& sg) {
 }  // namespace
 
 // A call whose per-batch settle lists outgrew the default capacity is run once more with the
-// worst-case capacity (32 entries per node: one per lane).
+// worst-case capacity (one entry per node and source of a batch).
 template <class F>
 int with_capacity_retry(bcpp_ctx* c, F&& f) {
     c->order_factor = 8;
     int rc = f();
     if (rc == BCPP_ECAPACITY) {
-        c->order_factor = 32;
+        c->order_factor = 64;
         rc = f();
         c->order_factor = 8;
     }

@@ -10,6 +10,9 @@
 // c(s,v) = (I_{v in S} + delta(s|v)) / sigma(s,v), stores c(s,u), and its dependency is
 // added (u != s) into the slot's partial betweenness.
 //
+// Each lane carries SPL sources (1 or 2); a node's row holds the batch's 32 * SPL sources
+// contiguously, so a lane reads its SPL values with one vector load.
+//
 // Latency structure: a warp works on one settled entry at a time, and every dependent memory
 // round trip costs it a full HBM latency, so the kernel keeps the chain per entry short: the
 // entry already carries the node's arc range (filled by a parallel pass over the step's list),
@@ -32,14 +35,53 @@ __device__ __forceinline__ void mark_bucket(const LsParams& P, uint32_t* bm, uin
     atomicMax(s_maxpush, nd);
 }
 
+// vector access to this lane's SPL consecutive values of one node row
+template <int SPL>
+__device__ __forceinline__ void ld_row(const int32_t* p, int32_t (&x)[SPL]) {
+    if constexpr (SPL == 1) {
+        x[0] = *p;
+    } else {
+        const int2 t = *reinterpret_cast<const int2*>(p);
+        x[0] = t.x; x[1] = t.y;
+    }
+}
+template <int SPL>
+__device__ __forceinline__ void ld_row(const uint64_t* p, uint64_t (&x)[SPL]) {
+    if constexpr (SPL == 1) {
+        x[0] = *p;
+    } else {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2*>(p);
+        x[0] = t.x; x[1] = t.y;
+    }
+}
+template <int SPL>
+__device__ __forceinline__ void ld_row(const double* p, double (&x)[SPL]) {
+    if constexpr (SPL == 1) {
+        x[0] = *p;
+    } else {
+        const double2 t = *reinterpret_cast<const double2*>(p);
+        x[0] = t.x; x[1] = t.y;
+    }
+}
+template <int SPL>
+__device__ __forceinline__ void ld_row(const float* p, float (&x)[SPL]) {
+    if constexpr (SPL == 1) {
+        x[0] = *p;
+    } else {
+        const float2 t = *reinterpret_cast<const float2*>(p);
+        x[0] = t.x; x[1] = t.y;
+    }
+}
+
 // Visit the arcs [a0, a0 + deg) of one row in groups of UNROLL: 32 heads (and weights and
 // multiplicities) come in one coalesced load and are broadcast by shuffle; the distance rows
-// of a whole group (drow = this lane's column of the slot's distance array) are loaded before
+// of a whole group (dl0 = this lane's slice of the slot's distance array) are loaded before
 // the group is handed to f, which then issues its own dependent loads for the whole group.
-template <int UNROLL, bool WEIGHTED, bool MULT, class F>
+template <int UNROLL, int SPL, bool WEIGHTED, bool MULT, class F>
 __device__ __forceinline__ void for_arc_groups(const int32_t* __restrict__ col, const int32_t* __restrict__ w,
                                                const uint64_t* __restrict__ mu, int64_t a0, int32_t deg,
-                                               const int32_t* drow, int lane, F&& f) {
+                                               const int32_t* dl0, int lane, F&& f) {
+    constexpr int SH = SPL == 1 ? 5 : 6;
     for (int32_t c0 = 0; c0 < deg; c0 += 32) {
         const int cnt = min(32, deg - c0);
         int32_t mv = 0, mw = 1;
@@ -50,7 +92,7 @@ __device__ __forceinline__ void for_arc_groups(const int32_t* __restrict__ col, 
             if (MULT) mm = __ldg(mu + a0 + c0 + lane);
         }
         for (int j = 0; j < cnt; j += UNROLL) {
-            int32_t vv[UNROLL], ww[UNROLL], dv[UNROLL];
+            int32_t vv[UNROLL], ww[UNROLL], dv[UNROLL][SPL];
             uint64_t mk[UNROLL];
 #pragma unroll
             for (int k = 0; k < UNROLL; k++) {
@@ -59,8 +101,14 @@ __device__ __forceinline__ void for_arc_groups(const int32_t* __restrict__ col, 
                 mk[k] = MULT ? shfl_u64(mm, (j + k) & 31) : 1ull;
             }
 #pragma unroll
-            for (int k = 0; k < UNROLL; k++)
-                dv[k] = (j + k < cnt) ? drow[(uint32_t)vv[k] << 5] : DINF;
+            for (int k = 0; k < UNROLL; k++) {
+                if (j + k < cnt) {
+                    ld_row<SPL>(dl0 + ((uint32_t)vv[k] << SH), dv[k]);
+                } else {
+#pragma unroll
+                    for (int s = 0; s < SPL; s++) dv[k][s] = DINF;
+                }
+            }
             f(vv, ww, mk, dv, cnt - j);
         }
     }
@@ -80,21 +128,24 @@ __device__ __forceinline__ LsEnt load_entry(const LsEnt* order, int e, int end) 
     return z;
 }
 
-template <typename DT, bool FUSED, bool WEIGHTED, bool MULT>
+template <typename DT, int SPL, bool FUSED, bool WEIGHTED, bool MULT>
 __global__ void __launch_bounds__(LS_THREADS, 2)
 ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __restrict__ items, int nitems) {
     __shared__ int s_item, s_pos, s_next, s_D, s_done, s_maxpush, s_nsteps, s_err, s_end;
     const int lane = threadIdx.x & 31;
     const int slot = blockIdx.x;
+    constexpr int ROW = 32 * SPL;                 // sources per node row
+    constexpr int SH = SPL == 1 ? 5 : 6;          // log2(ROW)
     // arcs handled per group (bounded by the 64 registers of two resident 512-thread CTAs)
-    constexpr int UNROLL = (WEIGHTED && FUSED) ? (MULT ? 4 : 6) : (MULT ? 6 : 8);
+    constexpr int UNROLL = SPL == 1 ? ((WEIGHTED && FUSED) ? (MULT ? 4 : 6) : (MULT ? 6 : 8))
+                                    : ((WEIGHTED && FUSED) ? (MULT ? 2 : 3) : (MULT ? 3 : 4));
 
-    int32_t* d = W.d + (int64_t)slot * W.cap_n * LS_LANES;
-    uint64_t* sg = W.sg + (int64_t)slot * W.cap_n * LS_LANES;
-    DT* dl = reinterpret_cast<DT*>(W.dl) + (int64_t)slot * W.cap_n * LS_LANES;
-    int32_t* drow = d + lane;              // this lane's column: node v at drow[v << 5]
-    uint64_t* srow = sg + lane;
-    DT* crow = dl + lane;
+    int32_t* d = W.d + (int64_t)slot * W.cap_n * ROW;
+    uint64_t* sg = W.sg + (int64_t)slot * W.cap_n * ROW;
+    DT* dlt = reinterpret_cast<DT*>(W.dl) + (int64_t)slot * W.cap_n * ROW;
+    int32_t* dl0 = d + lane * SPL;                // this lane's slice: node v at dl0[v << SH]
+    uint64_t* sl0 = sg + lane * SPL;
+    DT* cl0 = dlt + lane * SPL;
     LsEnt* order = W.order + (int64_t)slot * W.cap_order;
     int32_t* step_d = W.step_d + (int64_t)slot * W.cap_steps;
     int32_t* step_beg = W.step_beg + (int64_t)slot * W.cap_steps;
@@ -118,14 +169,22 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
         const int64_t* rp = A.rp + base;
         const int64_t* irp = A.irp + base;
         const int32_t nf = P.nfront ? P.nfront[I.g] : 0;
-        const int32_t my_src = lane < I.nsrc ? P.srcs[I.src_off + lane] : -1;
+        int32_t my_src[SPL];
+#pragma unroll
+        for (int s = 0; s < SPL; s++) {
+            const int b = lane * SPL + s;
+            my_src[s] = b < I.nsrc ? P.srcs[I.src_off + b] : -1;
+        }
 
         // sources: d = 0, sigma = 1, bucket 0
         if (threadIdx.x < 32) {
-            if (my_src >= 0) {
-                drow[(uint32_t)my_src << 5] = 0;
-                srow[(uint32_t)my_src << 5] = 1;
-                atomicOr(&bm[my_src >> 5], 1u << (my_src & 31));
+#pragma unroll
+            for (int s = 0; s < SPL; s++) {
+                if (my_src[s] >= 0) {
+                    dl0[((uint32_t)my_src[s] << SH) + s] = 0;
+                    sl0[((uint32_t)my_src[s] << SH) + s] = 1;
+                    atomicOr(&bm[my_src[s] >> 5], 1u << (my_src[s] & 31));
+                }
             }
         }
         if (threadIdx.x == 0) {
@@ -202,40 +261,67 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                 const int e2 = fetch_entry(&s_next, lane);
                 const LsEnt nxt = load_entry(order, e2, end);
                 const int u = cur.u;
-                const int32_t du = drow[(uint32_t)u << 5];
-                const bool act = (du == D);
-                if (__ballot_sync(FULL, act)) {
+                int32_t du[SPL];
+                ld_row<SPL>(dl0 + ((uint32_t)u << SH), du);
+                bool act[SPL], pull[SPL], any = false;
+#pragma unroll
+                for (int s = 0; s < SPL; s++) {
+                    act[s] = du[s] == D;
+                    pull[s] = act[s] && D > 0;
+                    any |= act[s];
+                }
+                if (__ballot_sync(FULL, any)) {
                     bool ovf = false;
-                    uint64_t acc = 0;
-                    const bool pull = act && D > 0;
+                    uint64_t acc[SPL];
+#pragma unroll
+                    for (int s = 0; s < SPL; s++) acc[s] = 0;
                     // sigma(s,u) = sum over parents v (d(v) + w(v,u) = D) of sigma(s,v) * m(v,u)
                     auto pull_group = [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk,
-                                          const int32_t* dv, int left) {
-                        uint64_t sp[UNROLL];
+                                          const int32_t (*dv)[SPL], int left) {
+                        uint64_t sp[UNROLL][SPL];
 #pragma unroll
                         for (int k = 0; k < UNROLL; k++) {
-                            const bool par = k < left && pull && dv[k] < D && dv[k] + ww[k] == D &&
-                                             (vv[k] >= nf || dv[k] == 0);
-                            sp[k] = par ? srow[(uint32_t)vv[k] << 5] : 0ull;
+                            bool par[SPL], anyp = false;
+#pragma unroll
+                            for (int s = 0; s < SPL; s++) {
+                                par[s] = k < left && pull[s] && dv[k][s] < D && dv[k][s] + ww[k] == D &&
+                                         (vv[k] >= nf || dv[k][s] == 0);
+                                anyp |= par[s];
+                            }
+                            uint64_t t[SPL];
+                            if (anyp) ld_row<SPL>(sl0 + ((uint32_t)vv[k] << SH), t);
+#pragma unroll
+                            for (int s = 0; s < SPL; s++) sp[k][s] = par[s] ? t[s] : 0ull;
                         }
 #pragma unroll
                         for (int k = 0; k < UNROLL; k++)
-                            if (sp[k]) acc = madd_ck(acc, sp[k], MULT ? mk[k] : 1ull, ovf);
+#pragma unroll
+                            for (int s = 0; s < SPL; s++)
+                                if (sp[k][s]) acc[s] = madd_ck(acc[s], sp[k][s], MULT ? mk[k] : 1ull, ovf);
                     };
                     // relax the out-arcs: lower tentative distances, mark improved heads
-                    auto relax_group = [&](const int32_t* vv, const int32_t* ww, const int32_t* dv, int left) {
+                    auto relax_group = [&](const int32_t* vv, const int32_t* ww, const int32_t (*dv)[SPL],
+                                           int left) {
 #pragma unroll
                         for (int k = 0; k < UNROLL; k++) {
                             if (k >= left) break;
                             const int64_t nd64 = (int64_t)D + ww[k];
                             const int32_t nd = nd64 < DINF ? (int32_t)nd64 : DINF;
-                            const bool imp = act && nd < dv[k];
-                            const unsigned im = __ballot_sync(FULL, imp);
+                            bool imp[SPL], anyi = false;
+#pragma unroll
+                            for (int s = 0; s < SPL; s++) {
+                                imp[s] = act[s] && nd < dv[k][s];
+                                anyi |= imp[s];
+                            }
+                            const unsigned im = __ballot_sync(FULL, anyi);
                             if (im) {
-                                int32_t* pd = &drow[(uint32_t)vv[k] << 5];
-                                if (imp) {
-                                    if (WEIGHTED) atomicMin(pd, nd);
-                                    else *pd = nd;
+                                int32_t* pd = dl0 + ((uint32_t)vv[k] << SH);
+#pragma unroll
+                                for (int s = 0; s < SPL; s++) {
+                                    if (imp[s]) {
+                                        if (WEIGHTED) atomicMin(pd + s, nd);
+                                        else pd[s] = nd;
+                                    }
                                 }
                                 if (lane == __ffs(im) - 1)
                                     mark_bucket(P, bm, bflag, W.bm_words, vv[k], nd, &s_maxpush);
@@ -243,8 +329,8 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                         }
                     };
                     if (FUSED) {
-                        for_arc_groups<UNROLL, WEIGHTED, MULT>(A.col, A.w, A.mu, cur.a0, cur.deg, drow, lane,
-                            [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk, const int32_t* dv,
+                        for_arc_groups<UNROLL, SPL, WEIGHTED, MULT>(A.col, A.w, A.mu, cur.a0, cur.deg, dl0, lane,
+                            [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk, const int32_t (*dv)[SPL],
                                 int left) {
                                 pull_group(vv, ww, mk, dv, left);
                                 relax_group(vv, ww, dv, left);
@@ -253,15 +339,17 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                         if (D > 0) {
                             const int64_t i0 = __ldg(irp + u);
                             const int32_t ideg = (int32_t)(__ldg(irp + u + 1) - i0);
-                            for_arc_groups<UNROLL, WEIGHTED, MULT>(A.icol, A.iw, A.imu, i0, ideg, drow, lane,
-                                [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk, const int32_t* dv,
-                                    int left) { pull_group(vv, ww, mk, dv, left); });
+                            for_arc_groups<UNROLL, SPL, WEIGHTED, MULT>(A.icol, A.iw, A.imu, i0, ideg, dl0, lane,
+                                [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk,
+                                    const int32_t (*dv)[SPL], int left) { pull_group(vv, ww, mk, dv, left); });
                         }
-                        for_arc_groups<UNROLL, WEIGHTED, false>(A.col, A.w, nullptr, cur.a0, cur.deg, drow, lane,
-                            [&](const int32_t* vv, const int32_t* ww, const uint64_t*, const int32_t* dv,
+                        for_arc_groups<UNROLL, SPL, WEIGHTED, false>(A.col, A.w, nullptr, cur.a0, cur.deg, dl0, lane,
+                            [&](const int32_t* vv, const int32_t* ww, const uint64_t*, const int32_t (*dv)[SPL],
                                 int left) { relax_group(vv, ww, dv, left); });
                     }
-                    if (pull) srow[(uint32_t)u << 5] = acc;
+#pragma unroll
+                    for (int s = 0; s < SPL; s++)
+                        if (pull[s]) sl0[((uint32_t)u << SH) + s] = acc[s];
                     if (__any_sync(FULL, ovf) && lane == 0) atomicOr(&P.flags[FLAG_SIGMA_OVF], 1u);
                 }
                 e = e2;
@@ -276,7 +364,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
         if (s_err) {
             // a list outgrew its bound: report it and leave the slot clean for the next batch
             if (threadIdx.x == 0) atomicOr(&P.flags[FLAG_CAPACITY], 1u);
-            for (int64_t i = threadIdx.x; i < (int64_t)n * LS_LANES; i += LS_THREADS) d[i] = DINF;
+            for (int64_t i = threadIdx.x; i < (int64_t)n * ROW; i += LS_THREADS) d[i] = DINF;
             for (int64_t i = threadIdx.x; i < (int64_t)P.nb * W.bm_words; i += LS_THREADS) bm[i] = 0u;
             for (int i = threadIdx.x; i < P.nb; i += LS_THREADS) bflag[i] = 0;
             if (P.mode == LS_SKEL && threadIdx.x == 0) {
@@ -299,30 +387,53 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                     const int e2 = fetch_entry(&s_next, lane);
                     const LsEnt nxt = load_entry(order, e2, end);
                     const int u = cur.u;
-                    const int32_t du = drow[(uint32_t)u << 5];
-                    const bool act = (du == D);
-                    if (__ballot_sync(FULL, act)) {
-                        DT acc = (DT)0;
-                        for_arc_groups<UNROLL, WEIGHTED, MULT>(A.col, A.w, A.mu, cur.a0, cur.deg, drow, lane,
-                            [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk, const int32_t* dv,
+                    int32_t du[SPL];
+                    ld_row<SPL>(dl0 + ((uint32_t)u << SH), du);
+                    bool act[SPL], any = false;
+#pragma unroll
+                    for (int s = 0; s < SPL; s++) {
+                        act[s] = du[s] == D;
+                        any |= act[s];
+                    }
+                    if (__ballot_sync(FULL, any)) {
+                        DT acc[SPL];
+#pragma unroll
+                        for (int s = 0; s < SPL; s++) acc[s] = (DT)0;
+                        for_arc_groups<UNROLL, SPL, WEIGHTED, MULT>(A.col, A.w, A.mu, cur.a0, cur.deg, dl0, lane,
+                            [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk, const int32_t (*dv)[SPL],
                                 int left) {
-                                DT cv[UNROLL];
+                                DT cv[UNROLL][SPL];
 #pragma unroll
                                 for (int k = 0; k < UNROLL; k++) {
-                                    const bool succ = k < left && act && dv[k] != DINF &&
-                                                      (int64_t)dv[k] == (int64_t)D + ww[k];
-                                    cv[k] = succ ? crow[(uint32_t)vv[k] << 5] : (DT)0;
+                                    bool sc[SPL], anys = false;
+#pragma unroll
+                                    for (int s = 0; s < SPL; s++) {
+                                        sc[s] = k < left && act[s] && dv[k][s] != DINF &&
+                                                (int64_t)dv[k][s] == (int64_t)D + ww[k];
+                                        anys |= sc[s];
+                                    }
+                                    DT t[SPL];
+                                    if (anys) ld_row<SPL>(cl0 + ((uint32_t)vv[k] << SH), t);
+#pragma unroll
+                                    for (int s = 0; s < SPL; s++) cv[k][s] = sc[s] ? t[s] : (DT)0;
                                 }
 #pragma unroll
-                                for (int k = 0; k < UNROLL; k++) acc += MULT ? (DT)mk[k] * cv[k] : cv[k];
+                                for (int k = 0; k < UNROLL; k++)
+#pragma unroll
+                                    for (int s = 0; s < SPL; s++) acc[s] += MULT ? (DT)mk[k] * cv[k][s] : cv[k][s];
                             });
                         double contrib = 0.0;
-                        if (act) {
-                            const DT sd = (DT)srow[(uint32_t)u << 5];
-                            const DT delta = sd * acc;
-                            const DT is_t = P.in_s ? (DT)P.in_s[base + u] : (DT)1;
-                            crow[(uint32_t)u << 5] = (is_t + delta) / sd;
-                            if (u != my_src) contrib = (double)delta;
+                        uint64_t su[SPL];
+                        ld_row<SPL>(sl0 + ((uint32_t)u << SH), su);
+                        const DT is_t = P.in_s ? (DT)P.in_s[base + u] : (DT)1;
+#pragma unroll
+                        for (int s = 0; s < SPL; s++) {
+                            if (act[s]) {
+                                const DT sd = (DT)su[s];
+                                const DT delta = sd * acc[s];
+                                cl0[((uint32_t)u << SH) + s] = (is_t + delta) / sd;
+                                if (u != my_src[s]) contrib += (double)delta;
+                            }
                         }
                         const double tot = warp_sum(contrib);
                         if (lane == 0 && bcs && tot != 0.0) {
@@ -337,30 +448,32 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                 }
                 __syncthreads();
             }
-        } else if (P.mode == LS_TABLE) {
-            // -------------------------------------------------------------- tables d_i[v][f], sigma_i[v][f]
-            const int64_t t0 = P.toff[I.g];
-            const int warp = threadIdx.x >> 5;
-            for (int v = warp; v < n; v += LS_THREADS / 32) {
-                if (lane < I.nsrc) {
-                    const int32_t dv = drow[(uint32_t)v << 5];
-                    const int64_t o = t0 + (int64_t)v * nf + I.aux + lane;
-                    P.td[o] = dv;
-                    P.ts[o] = dv == DINF ? 0ull : srow[(uint32_t)v << 5];
+        } else if constexpr (SPL == 1) {
+            if (P.mode == LS_TABLE) {
+                // ---------------------------------------------------------- tables d_i[v][f], sigma_i[v][f]
+                const int64_t t0 = P.toff[I.g];
+                const int warp = threadIdx.x >> 5;
+                for (int v = warp; v < n; v += LS_THREADS / 32) {
+                    if (lane < I.nsrc) {
+                        const int32_t dv = dl0[(uint32_t)v << SH];
+                        const int64_t o = t0 + (int64_t)v * nf + I.aux + lane;
+                        P.td[o] = dv;
+                        P.ts[o] = dv == DINF ? 0ull : sl0[(uint32_t)v << SH];
+                    }
                 }
-            }
-            __syncthreads();
-        } else if (P.mode == LS_SSSP) {
-            const int warp = threadIdx.x >> 5;
-            for (int v = warp; v < n; v += LS_THREADS / 32) {
-                if (lane < I.nsrc) {
-                    const int32_t dv = drow[(uint32_t)v << 5];
-                    const int64_t o = (int64_t)(I.src_off + lane) * P.dbg_n + v;
-                    P.dbg_d[o] = dv;
-                    P.dbg_s[o] = dv == DINF ? 0ull : srow[(uint32_t)v << 5];
+                __syncthreads();
+            } else if (P.mode == LS_SSSP) {
+                const int warp = threadIdx.x >> 5;
+                for (int v = warp; v < n; v += LS_THREADS / 32) {
+                    if (lane < I.nsrc) {
+                        const int32_t dv = dl0[(uint32_t)v << SH];
+                        const int64_t o = (int64_t)(I.src_off + lane) * P.dbg_n + v;
+                        P.dbg_d[o] = dv;
+                        P.dbg_s[o] = dv == DINF ? 0ull : sl0[(uint32_t)v << SH];
+                    }
                 }
+                __syncthreads();
             }
-            __syncthreads();
         }
 
         if (P.mode == LS_SKEL) {
@@ -372,7 +485,11 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
         } else {
             // restore "unreached" on every touched row
             const int warp = threadIdx.x >> 5;
-            for (int e = warp; e < olen; e += LS_THREADS / 32) drow[(uint32_t)order[e].u << 5] = DINF;
+            for (int e = warp; e < olen; e += LS_THREADS / 32) {
+                int32_t* pd = dl0 + ((uint32_t)order[e].u << SH);
+#pragma unroll
+                for (int s = 0; s < SPL; s++) pd[s] = DINF;
+            }
         }
         __syncthreads();
     }
@@ -394,10 +511,10 @@ __global__ void fill_i32_kernel(int32_t* p, int32_t v, int64_t n) {
         p[i] = v;
 }
 
-template <typename DT>
+template <typename DT, int SPL>
 void ls_launch_t(bool fused, bool weighted, bool mult, const LsArena& A, const LsParams& P, const LsSlots& W,
                  const LsItem* items, int nitems, int slots, cudaStream_t st) {
-#define LS_GO(F, WT, M) ls_kernel<DT, F, WT, M><<<slots, LS_THREADS, 0, st>>>(A, P, W, items, nitems)
+#define LS_GO(F, WT, M) ls_kernel<DT, SPL, F, WT, M><<<slots, LS_THREADS, 0, st>>>(A, P, W, items, nitems)
     if (fused) {
         if (!weighted) LS_GO(true, false, false);
         else if (!mult) LS_GO(true, true, false);
@@ -413,15 +530,21 @@ void ls_launch_t(bool fused, bool weighted, bool mult, const LsArena& A, const L
 }  // namespace
 
 void ls_launch(bool fp32_delta, bool fused, const LsArena& A, const LsParams& P, const LsSlots& W,
-               const LsItem* items, int nitems, int slots, cudaStream_t st) {
+               const LsItem* items, int nitems, int slots, cudaStream_t st, int spl) {
     if (nitems <= 0 || slots <= 0) return;
     // multiplicities > 1 only occur on skeleton arcs, whose weights then exceed 1 as well,
     // so a multiplicity array always comes with a weight array
     const bool mult = A.mu != nullptr;
     const bool weighted = A.w != nullptr;
     if (mult && !weighted) return;
-    if (fp32_delta) ls_launch_t<float>(fused, weighted, mult, A, P, W, items, nitems, slots, st);
-    else ls_launch_t<double>(fused, weighted, mult, A, P, W, items, nitems, slots, st);
+    if (spl == 2 && P.mode != LS_BRANDES) return;   // 64-source rows: Brandes passes only
+    if (spl == 2) {
+        if (fp32_delta) ls_launch_t<float, 2>(fused, weighted, mult, A, P, W, items, nitems, slots, st);
+        else ls_launch_t<double, 2>(fused, weighted, mult, A, P, W, items, nitems, slots, st);
+    } else {
+        if (fp32_delta) ls_launch_t<float, 1>(fused, weighted, mult, A, P, W, items, nitems, slots, st);
+        else ls_launch_t<double, 1>(fused, weighted, mult, A, P, W, items, nitems, slots, st);
+    }
 }
 
 void ls_reset_launch(const LsSlots& W, int slots, cudaStream_t st) {

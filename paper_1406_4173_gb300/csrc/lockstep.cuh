@@ -43,7 +43,7 @@ struct LsArena {
 struct LsItem {
     int32_t g;        // graph
     int32_t src_off;  // sources are srcs[src_off, src_off + nsrc) (graph-local ids)
-    int32_t nsrc;     // <= 32
+    int32_t nsrc;     // <= 32 * sources per lane
     int32_t aux;      // LS_TABLE: index of the batch's first frontier
 };
 
@@ -73,9 +73,9 @@ struct __align__(16) LsEnt {
 };
 
 struct LsSlots {
-    int32_t* d;                  // [slot][cap_n][32]
-    uint64_t* sg;                // [slot][cap_n][32]
-    void* dl;                    // [slot][cap_n][32] of DT: (I_{v in S} + delta) / sigma
+    int32_t* d;                  // [slot][cap_n][32 * spl]
+    uint64_t* sg;                // [slot][cap_n][32 * spl]
+    void* dl;                    // [slot][cap_n][32 * spl] of DT: (I_{v in S} + delta) / sigma
     int64_t cap_n;
     LsEnt* order;                // [slot][cap_order] settled (node, step) entries, in step order
     int64_t cap_order;
@@ -91,9 +91,10 @@ struct LsSlots {
     int32_t* hdr;                // [slot][4]: order length, steps, item, -
 };
 
-// Launch the lockstep kernel over `nitems` items with `slots` CTAs.
+// Launch the lockstep kernel over `nitems` items with `slots` CTAs.  spl = sources per lane
+// (1: 32-source batches, rows of 32; 2: 64-source batches, rows of 64, LS_BRANDES only).
 void ls_launch(bool fp32_delta, bool fused, const LsArena& A, const LsParams& P, const LsSlots& W,
-               const LsItem* items, int nitems, int slots, cudaStream_t st);
+               const LsItem* items, int nitems, int slots, cudaStream_t st, int spl = 1);
 
 // Restore the distance rows touched by LS_SKEL batches to "unreached".
 void ls_reset_launch(const LsSlots& W, int slots, cudaStream_t st);

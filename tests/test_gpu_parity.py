@@ -259,3 +259,38 @@ def test_source_shards_add_up(bc, world):
     parts_pp = sum(bc.brandes_pp(G, S, g.part, halve=False, shard=(r, world)).cpu().numpy() for r in range(world))
     assert rel_err(parts_pp, full_pp) < FP64_TOL
     assert rel_err(full_pp, full) < FP64_TOL
+
+
+# ----------------------------------------------------------------------------- 64-source batches
+@pytest.mark.parametrize("name,g", GRAPHS, ids=IDS)
+def test_brandes_64_source_batches(bc, name, g):
+    """Two sources per lane (rows of 64): same results as the oracle, FP64 and FP32."""
+    G = bc.graph_from_edgelist(g)
+    ref, _ = oracle.brandes(g)
+    assert rel_err(bc.brandes(G, batch=64).cpu().numpy(), ref) < FP64_TOL
+    assert rel_err(bc.brandes(G, precision="fp32", batch=64).cpu().numpy(), ref) < FP32_TOL
+    S = gen.sample_targets(g.n, 101, seed=41)
+    ref_s, _ = oracle.brandes(g, S)
+    assert rel_err(bc.brandes(G, S, batch=64).cpu().numpy(), ref_s) < FP64_TOL
+    # Brandes++ with all-singleton parts has no non-frontier nodes: 64-source Brandes_SK
+    assert rel_err(bc.brandes_pp(G, S, np.arange(g.n, dtype=np.int32), batch=64).cpu().numpy(), ref_s) < FP64_TOL
+
+
+def test_batched_graphs_64_source_batches(bc):
+    gs = [gen.erdos_renyi(int(n), min(1.0, 5.0 / max(n - 1, 1)), seed=200 + i) for i, n in
+          enumerate([64, 65, 130, 7, 400, 1, 2, 257])]
+    arena = bc.build_arena(gs)
+    got = bc.brandes_batched(arena, batch=64).cpu().numpy()
+    off = arena.node_ptr_host
+    for i, g in enumerate(gs):
+        ref, _ = oracle.brandes(g)
+        assert rel_err(got[off[i]:off[i + 1]], ref) < FP64_TOL, i
+
+
+def test_source_shards_64(bc):
+    g = gen.planted_partition(700, 7, 0.03, 0.002, seed=42)
+    S = gen.sample_targets(g.n, 333, seed=42)
+    G = bc.graph_from_edgelist(g)
+    full, _ = oracle.brandes(g, S, halve=False)
+    parts = sum(bc.brandes(G, S, halve=False, shard=(r, 3), batch=64).cpu().numpy() for r in range(3))
+    assert rel_err(parts, full) < FP64_TOL

@@ -20,9 +20,9 @@ def _free_port():
     return p
 
 
-def shard_bounds(nbatches, rank, world):
-    """Contiguous shard of source batches (the library's rule for shard_index/shard_count)."""
-    return nbatches * rank // world, nbatches * (rank + 1) // world
+def shard_bounds(nsources, rank, world):
+    """Contiguous shard of the sources (the library's rule for shard_index/shard_count)."""
+    return nsources * rank // world, nsources * (rank + 1) // world
 
 
 def _worker(rank, world, port, out_path):
@@ -33,9 +33,8 @@ def _worker(rank, world, port, out_path):
     from paper_1406_4173_gb300 import gen
     g = gen.planted_partition(400, 4, 0.05, 0.004, seed=21)
     S = gen.sample_targets(g.n, 150, seed=21)
-    nb = (len(S) + 31) // 32
-    b0, b1 = shard_bounds(nb, rank, world)
-    mine = S[b0 * 32: min(len(S), b1 * 32)]
+    s0, s1 = shard_bounds(len(S), rank, world)
+    mine = S[s0:s1]
     rest = np.setdiff1d(S, mine)
     order = np.concatenate([mine, rest]).astype(np.int32)
     part, _ = oracle.brandes(g, order, nsrc=len(mine), halve=False)
@@ -57,7 +56,7 @@ def test_source_shards_sum_to_full(tmp_path, world):
 
 
 def test_shard_bounds_cover_exactly():
-    for nb in (0, 1, 5, 63, 1563):
+    for nb in (0, 1, 5, 63, 1563, 50000):
         for world in (1, 2, 3, 8):
             cov = []
             for r in range(world):
