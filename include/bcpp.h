@@ -67,10 +67,10 @@ typedef struct {
 typedef struct {
     int32_t precision;         /* BCPP_FP64 (default) or BCPP_FP32_DELTA */
     int32_t halve_undirected;  /* 1 (default): halve undirected results; 0: ordered-pair sums */
-    int32_t batch;             /* sources per batch: 0 = auto (64 when 64-source batches still fill every
-                                * resident CTA, else 32), 32 or 64.  64 applies to plain Brandes passes
-                                * (bcpp_brandes, bcpp_brandes_batched, Brandes++ without non-frontier
-                                * nodes); Dijkstra_SK, Brandes_SK with Centrality and bcpp_sssp use 32. */
+    int32_t batch;             /* sources per batch: 0 = default (32), 32 or 64.  64 applies to plain
+                                * Brandes passes (bcpp_brandes, bcpp_brandes_batched, Brandes++ without
+                                * non-frontier nodes); Dijkstra_SK, Brandes_SK with Centrality and
+                                * bcpp_sssp use 32. */
     int32_t ctas_per_sm;       /* resident source batches per SM: 0 = auto */
     int32_t validate;          /* reserved: the CSR, S and the partition are always checked */
     int32_t host_buffers;      /* 1: array arguments are host pointers (copied in and out) */

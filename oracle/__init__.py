@@ -49,7 +49,8 @@ def _load():
             lib.orc_brandes.argtypes = [i32, i64, P, P, P, i32, P, i32, i32, i32, P, P]
             lib.orc_brandes_pp.argtypes = [i32, i64, P, P, P, i32, P, i32, i32, P, i32, i32, P, P, P]
             lib.orc_skeleton.argtypes = [i32, i64, P, P, P, i32, P, i32, P, i32, P, P, i64, P, P, P, P, P, P]
-            for f in (lib.orc_sssp, lib.orc_brandes, lib.orc_brandes_pp, lib.orc_skeleton):
+            lib.orc_distance_sum.argtypes = [i32, i64, P, P, i32, P, i32, P]
+            for f in (lib.orc_sssp, lib.orc_brandes, lib.orc_brandes_pp, lib.orc_skeleton, lib.orc_distance_sum):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -148,3 +149,15 @@ def skeleton(g, S, part, k: int | None = None):
         _check(rc, "skeleton")
         n_a = int(na[0])
         return nodes[: int(nsk[0])].copy(), (au[:n_a], av[:n_a], aw[:n_a], amu[:n_a]), bool(ovf[0])
+
+
+def distance_sum(g, sources) -> int:
+    """Sum over the given sources s and reachable t != s of (d(s,t) - 1), unit weights
+    (breadth-first search; the right-hand side of the path-length invariant)."""
+    lib = _load()
+    eu, ev, _ = _edges(g)
+    src = np.ascontiguousarray(sources, np.int32)
+    out = np.zeros(1, np.int64)
+    _check(lib.orc_distance_sum(g.n, g.m, _ptr(eu), _ptr(ev), int(g.directed), _ptr(src), int(src.shape[0]),
+                                _ptr(out)), "distance_sum")
+    return int(out[0])

@@ -606,3 +606,35 @@ int orc_skeleton(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, con
     skel_free(&K);
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------- public: path lengths */
+/* Sum over sources s = src[0..nsrc) and reachable t != s of (d(s,t) - 1), unit weights:
+ * the right-hand side of the invariant sum_v C(v) = sum_{s != t} (d(s,t) - 1) of Eq. 1
+ * (every shortest s-t path has d(s,t) - 1 interior nodes, each credited 1/sigma(s,t) per
+ * path).  Breadth-first search only; no path counts. */
+int orc_distance_sum(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, int32_t directed,
+                     const int32_t *src, int32_t nsrc, int64_t *out) {
+    if (n < 0 || m < 0 || !out) return ORC_EINVAL;
+    graph_t g;
+    if (graph_build(&g, n, m, eu, ev, NULL, NULL, !directed)) return ORC_ENOMEM;
+    int32_t *dist = malloc((size_t)(n ? n : 1) * sizeof(int32_t));
+    int32_t *queue = malloc((size_t)(n ? n : 1) * sizeof(int32_t));
+    if (!dist || !queue) { free(dist); free(queue); graph_free(&g); return ORC_ENOMEM; }
+    int64_t tot = 0;
+    for (int32_t i = 0; i < nsrc; i++) {
+        int32_t s = src[i];
+        if (s < 0 || s >= n) { free(dist); free(queue); graph_free(&g); return ORC_EINVAL; }
+        for (int32_t v = 0; v < n; v++) dist[v] = INF32;
+        int64_t head = 0, cnt = 0;
+        dist[s] = 0; queue[cnt++] = s;
+        while (head < cnt) {
+            int32_t u = queue[head++];
+            if (u != s) tot += dist[u] - 1;
+            for (int64_t p = g.off[u]; p < g.off[u + 1]; p++)
+                if (dist[g.adj[p]] == INF32) { dist[g.adj[p]] = dist[u] + 1; queue[cnt++] = g.adj[p]; }
+        }
+    }
+    *out = tot;
+    free(dist); free(queue); graph_free(&g);
+    return ORC_OK;
+}

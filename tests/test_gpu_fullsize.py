@@ -1,0 +1,130 @@
+"""GPU parity at the benchmark's full sizes (Chung-Lu n = 50,000, S = V; and the other
+workloads), on outputs the oracle can compute in seconds and on properties that hold at any
+size:
+
+- bit-exact distances and path counts from sampled sources;
+- the partial betweenness of a shard of sources (the first |S|/R targets, all targets as
+  destinations) in the benchmark's batching (64-source batches) against the oracle's;
+- Brandes++ = plain Brandes over all of S = V (the method's exactness, GPU vs GPU);
+- the path-length invariant sum_v C(v) = (1/2) sum_{s != t} (d(s,t) - 1) with the right-hand
+  side from the oracle's breadth-first searches (spawned worker processes, started before
+  any GPU call of the worker).
+"""
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1406_4173_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+FP64_TOL = 1e-12
+INF32 = np.iinfo(np.int32).max
+
+
+def rel_err(x, ref):
+    return float(np.max(np.abs(np.asarray(x) - ref) / np.maximum(np.abs(ref), 1.0)))
+
+
+def _dist_sum_chunk(args):
+    name, lo, hi = args
+    import oracle as orc
+    from paper_1406_4173_gb300 import gen as gn
+    g, _ = gn.workload(name)
+    return orc.distance_sum(g, np.arange(lo, hi, dtype=np.int32))
+
+
+@pytest.fixture(scope="module")
+def c2_invariant_rhs():
+    """sum over ordered pairs of (d - 1) on chunglu_50k, from the oracle in a spawned pool
+    (created before this module's first GPU call)."""
+    oracle.build()
+    g, _ = gen.workload("chunglu_50k")
+    chunks = [(i, min(g.n, i + 2500)) for i in range(0, g.n, 2500)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(16, mp.cpu_count())) as pool:
+        parts = pool.map(_dist_sum_chunk, [("chunglu_50k", lo, hi) for lo, hi in chunks])
+    return sum(parts)
+
+
+@pytest.fixture(scope="module")
+def bc(c2_invariant_rhs):
+    import torch
+    import paper_1406_4173_gb300 as m
+    from paper_1406_4173_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    return m
+
+
+@pytest.fixture(scope="module")
+def c2(bc):
+    g, _ = gen.workload("chunglu_50k")
+    return g, bc.graph_from_edgelist(g)
+
+
+def test_c2_sampled_sssp_bit_exact(bc, c2):
+    g, G = c2
+    src = np.linspace(0, g.n - 1, 40).astype(np.int32)
+    dist, sig = bc.sssp(G, src)
+    dist, sig = dist.cpu().numpy(), sig.cpu().numpy().view(np.uint64)
+    for i, s in enumerate(src):
+        d_ref, s_ref, _ = oracle.sssp(g, int(s))
+        assert np.array_equal(dist[i], d_ref) and np.array_equal(sig[i], s_ref)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", 2e-4)])
+def test_c2_shard_partial_vs_oracle(bc, c2, precision, tol):
+    g, G = c2
+    count = 200                                     # first 250 sources, all 50,000 targets
+    ns = g.n // count
+    ref, _ = oracle.brandes(g, None, nsrc=ns, halve=False)
+    got = bc.brandes(G, None, halve=False, shard=(0, count), batch=64, precision=precision).cpu().numpy()
+    assert rel_err(got, ref) < tol
+
+
+def test_c2_brandes_pp_equals_plain_and_invariant(bc, c2, c2_invariant_rhs):
+    g, G = c2
+    plain = bc.brandes(G).cpu().numpy()             # bench configuration: S = V, auto batching
+    pp = bc.brandes_pp(G, None, g.part).cpu().numpy()
+    assert rel_err(pp, plain) < FP64_TOL
+    total = float(np.sum(plain))
+    assert abs(total - c2_invariant_rhs / 2) <= 1e-12 * total
+
+
+def test_planted_2k_full(bc):
+    g, _ = gen.workload("planted_2k")
+    G = bc.graph_from_edgelist(g)
+    ref, _ = oracle.brandes(g)
+    assert rel_err(bc.brandes(G).cpu().numpy(), ref) < FP64_TOL
+    assert rel_err(bc.brandes_pp(G, None, g.part).cpu().numpy(), ref) < FP64_TOL
+
+
+def test_directed_100k_sampled(bc):
+    g, S = gen.workload("directed_100k")
+    G = bc.graph_from_edgelist(g)
+    src = S[:8]
+    dist, sig = bc.sssp(G, src)
+    dist, sig = dist.cpu().numpy(), sig.cpu().numpy().view(np.uint64)
+    for i, s in enumerate(src):
+        d_ref, s_ref, _ = oracle.sssp(g, int(s))
+        assert np.array_equal(dist[i], d_ref) and np.array_equal(sig[i], s_ref)
+    count = 100                                     # first 20 targets as sources
+    ns = len(S) // count
+    ref, _ = oracle.brandes(g, S, nsrc=ns)
+    got = bc.brandes(G, S, shard=(0, count)).cpu().numpy()
+    assert rel_err(got, ref) < FP64_TOL
+    plain = bc.brandes(G, S).cpu().numpy()
+    pp = bc.brandes_pp(G, S, g.part).cpu().numpy()
+    assert rel_err(pp, plain) < FP64_TOL
+
+
+def test_er_batch_4096_sampled(bc):
+    gs, _ = gen.workload("er_batch_4096")
+    arena = bc.build_arena(gs)
+    got = bc.brandes_batched(arena).cpu().numpy()
+    off = arena.node_ptr_host
+    for i in list(range(0, 4096, 97)) + [int(np.argmax([g.n for g in gs]))]:
+        ref, _ = oracle.brandes(gs[i])
+        assert rel_err(got[off[i]:off[i + 1]], ref) < FP64_TOL, i

@@ -294,3 +294,18 @@ def test_oracle_rejects_bad_inputs():
         oracle.brandes(w0)
     with pytest.raises(ValueError):
         oracle.brandes(g, np.array([1, 1], np.int32))
+
+
+def test_distance_sum_matches_definition():
+    for seed in range(3):
+        g = gen.erdos_renyi(70, 0.06, seed=seed)
+        src = np.arange(g.n, dtype=np.int32)
+        ref = 0
+        for s in src:
+            dist, _, _ = oracle.sssp(g, int(s))
+            ref += int(np.sum(dist[(dist != INF32) & (np.arange(g.n) != s)] - 1))
+        assert oracle.distance_sum(g, src) == ref
+    # closed form: path P_n, sum over ordered pairs of (|i-j| - 1)
+    n = 40
+    ref = sum(abs(i - j) - 1 for i in range(n) for j in range(n) if i != j)
+    assert oracle.distance_sum(gen.path(n), np.arange(n, dtype=np.int32)) == ref
