@@ -30,7 +30,6 @@ struct bcpp_ctx {
     uint32_t* hflags = nullptr;      // pinned host copy
     int64_t launches = 0;
     int order_factor = 8;            // settled-entry capacity per node of a batch (retry: worst case)
-    bool use_bfs = true;             // unit weights: lane-bitmask kernel (retry: general kernel)
     cudaEvent_t ev[8] = {};
 
     void* acquire(size_t bytes) {
@@ -349,7 +348,7 @@ int finish_status(bcpp_ctx* c, bcpp_stats* st) {
     CK_RC(sync_flags(c));
     if (st) st->sigma_overflow = c->hflags[FLAG_SIGMA_OVF] ? 1u : 0u;
     if (c->hflags[FLAG_INVALID]) return BCPP_EINVAL;
-    if (c->hflags[FLAG_CAPACITY] || c->hflags[FLAG_LEVELS]) return BCPP_ECAPACITY;
+    if (c->hflags[FLAG_CAPACITY]) return BCPP_ECAPACITY;
     if (c->hflags[FLAG_SIGMA_OVF]) return BCPP_EOVERFLOW_SIGMA;
     return BCPP_OK;
 }
@@ -458,14 +457,8 @@ int brandes_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, 
     P.flags = c->flags;
     Timer tb(c);
     tb.start();
-    if (!g->w && spl == 1 && c->use_bfs) {
-        bfs_init_slots(ws.W, slots, c->stream);
-        bfs_launch(fp32, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream);
-        c->launches += 2;
-    } else {
-        ls_launch(fp32, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream, spl);
-        c->launches++;
-    }
+    ls_launch(fp32, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream, spl);
+    c->launches++;
     tb.stop();
     CK_CUDA(cudaGetLastError());
     const bool halve = !g->directed && o.halve_undirected != 0;
@@ -847,14 +840,8 @@ int brandes_pp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t n
             P.item_counter = ws.counter.p;
             P.flags = c->flags;
             tbr.start();
-            if (!A.w && spl == 1 && c->use_bfs) {
-                bfs_init_slots(ws.W, slots, c->stream);
-                bfs_launch(fp32, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream);
-                c->launches += 2;
-            } else {
-                ls_launch(fp32, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream, spl);
-                c->launches++;
-            }
+            ls_launch(fp32, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream, spl);
+            c->launches++;
             tbr.stop();
             CK_CUDA(cudaGetLastError());
         }
@@ -973,14 +960,8 @@ int batched_dev(bcpp_ctx* c, int32_t ngraphs, const int64_t* node_ptr_dev, const
     P.item_counter = ws.counter.p;
     P.flags = c->flags;
     tb.start();
-    if (!g->w && spl == 1 && c->use_bfs) {
-        bfs_init_slots(ws.W, slots, c->stream);
-        bfs_launch(fp32, true, A, P, ws.W, items.p, nitems, slots, c->stream);
-        c->launches += 2;
-    } else {
-        ls_launch(fp32, true, A, P, ws.W, items.p, nitems, slots, c->stream, spl);
-        c->launches++;
-    }
+    ls_launch(fp32, true, A, P, ws.W, items.p, nitems, slots, c->stream, spl);
+    c->launches++;
     CK_CUDA(cudaGetLastError());
     combine_launch(ws.W.bc_sum, ws.W.bc_cmp, slots, n, n, o.halve_undirected ? 0.5 : 1.0, bc_out, c->stream);
     c->launches++;
@@ -1163,19 +1144,14 @@ int stage_graph(bcpp_ctx* c, const bcpp_graph* hg, StagedGraph& sg) {
 
 // A call whose per-batch settle lists outgrew the default capacity is run once more with the
 // worst-case capacity (one entry per node and source of a batch).
-// (A unit-weight batch deeper than the lane-bitmask kernel's 8-bit levels is rerun the same
-// way, with the general kernel.)
 template <class F>
 int with_capacity_retry(bcpp_ctx* c, F&& f) {
     c->order_factor = 8;
-    c->use_bfs = true;
     int rc = f();
     if (rc == BCPP_ECAPACITY) {
         c->order_factor = 64;
-        c->use_bfs = false;
         rc = f();
         c->order_factor = 8;
-        c->use_bfs = true;
     }
     return rc;
 }

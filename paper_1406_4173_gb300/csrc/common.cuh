@@ -17,7 +17,6 @@ enum : int {
     FLAG_CAPACITY = 1,      // a per-batch list outgrew its buffer
     FLAG_INVALID = 2,       // input validation failed
     FLAG_INVALID_WHY = 3,   // first reason code of an invalid input
-    FLAG_LEVELS = 4,        // a breadth-first batch went deeper than its 8-bit levels hold
     FLAG_COUNT = 8
 };
 

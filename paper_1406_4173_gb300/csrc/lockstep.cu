@@ -20,11 +20,20 @@
 // distance-row loads and then all its sigma (or c) loads together, bucket marks and
 // partial-sum updates are fire-and-forget atomics.
 #include "lockstep.cuh"
-#include "lockstep_dev.cuh"
 
 namespace bcpp {
 
 namespace {
+
+// Mark head v in the bucket of distance nd (fire-and-forget: a stale mark only costs a
+// visit that finds no lane at that distance).
+__device__ __forceinline__ void mark_bucket(const LsParams& P, uint32_t* bm, uint8_t* bflag, int64_t bm_words,
+                                            int v, int32_t nd, int* s_maxpush) {
+    const int bk = nd % P.nb;
+    atomicOr(&bm[(int64_t)bk * bm_words + (v >> 5)], 1u << (v & 31));
+    bflag[bk] = 1;
+    atomicMax(s_maxpush, nd);
+}
 
 // vector access to this lane's SPL consecutive values of one node row
 template <int SPL>
@@ -103,6 +112,20 @@ __device__ __forceinline__ void for_arc_groups(const int32_t* __restrict__ col, 
             f(vv, ww, mk, dv, cnt - j);
         }
     }
+}
+
+// Fetch the next entry index of the current step for this warp (dynamic scheduling).
+__device__ __forceinline__ int fetch_entry(int* s_next, int lane) {
+    int e = 0;
+    if (lane == 0) e = atomicAdd(s_next, 1);
+    return __shfl_sync(FULL, e, 0);
+}
+
+__device__ __forceinline__ LsEnt load_entry(const LsEnt* order, int e, int end) {
+    if (e < end) return order[e];
+    LsEnt z;
+    z.u = -1; z.deg = 0; z.a0 = 0;
+    return z;
 }
 
 template <typename DT, int SPL, bool FUSED, bool WEIGHTED, bool MULT>

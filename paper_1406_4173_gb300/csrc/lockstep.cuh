@@ -96,12 +96,6 @@ struct LsSlots {
 void ls_launch(bool fp32_delta, bool fused, const LsArena& A, const LsParams& P, const LsSlots& W,
                const LsItem* items, int nitems, int slots, cudaStream_t st, int spl = 1);
 
-// Unit-weight Brandes (LS_BRANDES only) with per-node lane bitmasks for the forward pass:
-// see bfs.cu.  Uses the same slots; bfs_init_slots prepares their layout.
-void bfs_launch(bool fp32_delta, bool fused, const LsArena& A, const LsParams& P, const LsSlots& W,
-                const LsItem* items, int nitems, int slots, cudaStream_t st);
-void bfs_init_slots(const LsSlots& W, int slots, cudaStream_t st);
-
 // Restore the distance rows touched by LS_SKEL batches to "unreached".
 void ls_reset_launch(const LsSlots& W, int slots, cudaStream_t st);
 
