@@ -294,3 +294,17 @@ def test_source_shards_64(bc):
     full, _ = oracle.brandes(g, S, halve=False)
     parts = sum(bc.brandes(G, S, halve=False, shard=(r, 3), batch=64).cpu().numpy() for r in range(3))
     assert rel_err(parts, full) < FP64_TOL
+
+
+def test_deep_unit_graphs(bc):
+    """Deep unit-weight graphs (hundreds of levels) against their closed forms."""
+    n = 600
+    i = np.arange(n)
+    G = bc.graph_from_edgelist(gen.path(n))
+    assert rel_err(bc.brandes(G).cpu().numpy(), i * (n - 1 - i)) < FP64_TOL
+    arena = bc.build_arena([gen.path(300), gen.cycle(700)])
+    got = bc.brandes_batched(arena).cpu().numpy()
+    ref_p = np.arange(300) * (299 - np.arange(300))
+    k = 350
+    assert rel_err(got[:300], ref_p) < FP64_TOL
+    assert rel_err(got[300:], np.full(700, (k - 1) ** 2 / 2)) < FP64_TOL
