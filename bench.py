@@ -414,7 +414,8 @@ def _run_single(args, bc, gen, g, S, ctx, flush, dev, ws, rank):
         cpu = {"value": 2.0 * ns_c * m / (tp + tpp), "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"first {ns_c} of {nS} sources (targets = S), oracle plain Brandes + Brandes++, "
                          f"{tp:.1f} s + {tpp:.1f} s"}
-        got = bc.brandes(G, Sarg, precision=prec, halve=False, shard=(0, count), ctx=ctx).cpu().numpy()
+        got = bc.brandes(G, Sarg, precision=prec, halve=False, shard=(0, count), ctx=ctx,
+                         order_sources=False).cpu().numpy()
         err_oracle = {"sources": ns_c, "max_rel_err_plain": _rel(got, ref_part)}
 
     return {

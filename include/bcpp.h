@@ -74,15 +74,18 @@ typedef struct {
     int32_t ctas_per_sm;       /* resident source batches per SM: 0 = auto */
     int32_t validate;          /* reserved: the CSR, S and the partition are always checked */
     int32_t host_buffers;      /* 1: array arguments are host pointers (copied in and out) */
-    int32_t order_sources;     /* 1 (default): batch targets of the same part together (Brandes++) */
+    int32_t order_sources;     /* 1 (default): batch the targets in order of their breadth-first level
+                                * from the highest-degree node (Brandes++: by part, then level), so that
+                                * a batch's sources are close; 0: batch S in the given order.  Only the
+                                * summation order changes, not the result. */
     int32_t shard_index;       /* with shard_count > 1: use only this shard's targets as sources */
     int32_t shard_count;       /* 0 or 1: every target is a source.  Otherwise the targets, in the order
                                 * used for batching, are split into shard_count contiguous shards
                                 * (shard r: positions [|S| r / R, |S| (r+1) / R)); only shard_index's
                                 * targets are sources and the result is that shard's partial sum
                                 * (targets stay all of S), so the shards' results add up to the
-                                * unsharded result (multi-GPU source sharding).  Plain Brandes batches
-                                * S in the given order; Brandes++ in the order of order_sources. */
+                                * unsharded result (multi-GPU source sharding).  The order is the one
+                                * of order_sources (with order_sources = 0: S as given). */
 } bcpp_opts;
 
 typedef struct {

@@ -236,7 +236,7 @@ def csr_validate(G: Graph, ctx: Context | None = None) -> None:
 # ----------------------------------------------------------------------------- betweenness
 def brandes(G: Graph, S=None, precision: str = "fp64", halve: bool = True, ctx: Context | None = None,
             ctas_per_sm: int = 0, out=None, stats: bool = False, allow_overflow: bool = False, shard=None,
-            batch: int = 0):
+            batch: int = 0, order_sources: bool = True):
     """Plain Brandes, target set S (None = all nodes).  Returns a float64 device tensor [n]
     (and the stats dict when stats=True).  shard=(index, count) computes one shard's partial
     sum over the sources (the shards add up to the full result)."""
@@ -248,7 +248,7 @@ def brandes(G: Graph, S=None, precision: str = "fp64", halve: bool = True, ctx: 
     bc = out if out is not None else torch.empty(G.n, dtype=torch.float64, device=dev)
     st = c_stats()
     cg = G.c()
-    o = _opts(precision, halve, ctas_per_sm, shard=shard, batch=batch)
+    o = _opts(precision, halve, ctas_per_sm, shard=shard, batch=batch, order_sources=order_sources)
     rc = load_library().bcpp_brandes(ctx.handle, ctypes.byref(cg), None if nS == 0 else St.data_ptr(), nS,
                                      ctypes.byref(o), bc.data_ptr(), ctypes.byref(st))
     _check(rc, allow_overflow)

@@ -173,6 +173,32 @@ __global__ void sort_keys_by_part_kernel(const int32_t* S, int64_t nS, const int
     }
 }
 
+// highest-degree node (smallest id on ties): max of (degree << 32 | ~id)
+__global__ void hub_kernel(const int64_t* rp, int32_t n, unsigned long long* best) {
+    unsigned long long b = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long key = ((unsigned long long)(rp[v + 1] - rp[v]) << 32) | (0xffffffffu - (uint32_t)v);
+        b = key > b ? key : b;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long x = __shfl_xor_sync(FULL, b, o);
+        b = x > b ? x : b;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(best, b);
+}
+
+// keys[i] = level[S[i]] (or part[S[i]] with part), vals[i] = S[i]
+__global__ void level_keys_kernel(const int32_t* S, int64_t ns, const int32_t* level, uint64_t* keys, uint32_t* vals) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += (int64_t)gridDim.x * blockDim.x) {
+        keys[i] = (uint64_t)(uint32_t)level[S[i]];
+        vals[i] = (uint32_t)S[i];
+    }
+}
+__global__ void part_keys_kernel(const uint32_t* vals, int64_t ns, const int32_t* part, uint64_t* keys) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += (int64_t)gridDim.x * blockDim.x)
+        keys[i] = (uint64_t)part[vals[i]];
+}
+
 __global__ void i64_from_i32_kernel(const int32_t* in, int64_t* out, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = in[i];
@@ -376,6 +402,70 @@ int build_in_csr(bcpp_ctx* c, const bcpp_graph* g, InCsr& T) {
     return BCPP_OK;
 }
 
+// Order the targets so that every batch holds sources close to each other: stable sort by
+// shortest-path level from the highest-degree node (one single-source run of the lockstep
+// kernel), then, when a partition is given, by part.  Fewer distinct levels per node and batch
+// means fewer settled (node, step) entries.  Only the batching order changes, not the result.
+int order_targets(bcpp_ctx* c, const bcpp_graph* g, const int64_t* irp, const int32_t* icol, const uint32_t* iw,
+                  uint64_t wmax, const int32_t* S, int64_t ns, const int32_t* part, int32_t k, DBuf<int32_t>& out) {
+    const int32_t n = g->n;
+    DBuf<unsigned long long> best(c, 1);
+    CK_ALLOC(best);
+    CK_CUDA(cudaMemsetAsync(best.p, 0, sizeof(unsigned long long), c->stream));
+    hub_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, c->stream>>>(g->row_ptr, n, best.p);
+    c->launches++;
+    unsigned long long hb = 0;
+    CK_RC(to_host(c, &hb, best.p, 1));
+    const int32_t hub = (int32_t)(0xffffffffu - (uint32_t)(hb & 0xffffffffull));
+    // levels from the hub
+    DBuf<int32_t> level(c, n), src(c, 1);
+    DBuf<uint64_t> lsig(c, n);
+    DBuf<LsItem> item(c, 1);
+    DBuf<int64_t> node_off(c, 2);
+    CK_ALLOC(level); CK_ALLOC(src); CK_ALLOC(lsig); CK_ALLOC(item); CK_ALLOC(node_off);
+    const LsItem hi{0, 0, 1, 0};
+    const int64_t hoff[2] = {0, n};
+    CK_RC(to_dev(c, item.p, &hi, 1));
+    CK_RC(to_dev(c, node_off.p, hoff, 2));
+    CK_RC(to_dev(c, src.p, &hub, 1));
+    const int nb = g->w ? (int)wmax + 1 : 2;
+    SlotWs ws;
+    CK_RC(alloc_slots(c, ws, 1, n, nb, false, 0));
+    LsArena A{};
+    A.rp = g->row_ptr; A.col = g->col; A.w = (const int32_t*)g->w;
+    A.irp = irp; A.icol = icol; A.iw = (const int32_t*)iw;
+    A.node_off = node_off.p;
+    LsParams P{};
+    P.mode = LS_SSSP;
+    P.nb = nb;
+    P.srcs = src.p;
+    P.dbg_d = level.p;
+    P.dbg_s = lsig.p;
+    P.dbg_n = n;
+    P.item_counter = ws.counter.p;
+    P.flags = c->flags;
+    ls_launch(false, !g->directed, A, P, ws.W, item.p, 1, 1, c->stream);
+    c->launches++;
+    // stable sorts: by level, then by part
+    DBuf<uint64_t> keys(c, ns), kb(c, ns);
+    DBuf<uint32_t> vals(c, ns), vb(c, ns);
+    DBuf<int64_t> hist(c, radix_hist_elems(ns)), tmp(c, scan_tmp_elems(radix_hist_elems(ns)));
+    CK_ALLOC(keys); CK_ALLOC(kb); CK_ALLOC(vals); CK_ALLOC(vb); CK_ALLOC(hist); CK_ALLOC(tmp);
+    const unsigned blocks = (unsigned)std::min<int64_t>((ns + 255) / 256, 8192);
+    level_keys_kernel<<<blocks, 256, 0, c->stream>>>(S, ns, level.p, keys.p, vals.p);
+    radix_sort_pairs(keys.p, vals.p, kb.p, vb.p, ns, 31, hist.p, tmp.p, c->stream, c->launches);
+    c->launches++;
+    if (part) {
+        part_keys_kernel<<<blocks, 256, 0, c->stream>>>(vals.p, ns, part, keys.p);
+        radix_sort_pairs(keys.p, vals.p, kb.p, vb.p, ns, bits_for((uint64_t)k), hist.p, tmp.p, c->stream, c->launches);
+        c->launches++;
+    }
+    CK_ALLOC(out.alloc(c, ns));
+    CK_CUDA(cudaMemcpyAsync(out.p, vals.p, ns * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
+    CK_CUDA(cudaGetLastError());
+    return BCPP_OK;
+}
+
 // --------------------------------------------------------------------------- plain Brandes
 int brandes_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, const bcpp_opts& o, double* bc_out,
                 bcpp_stats* st) {
@@ -416,7 +506,13 @@ int brandes_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, 
     }
     InCsr T;
     if (g->directed) CK_RC(build_in_csr(c, g, T));
-    // items: batches of 32 targets in the given order
+    DBuf<int32_t> ordered;
+    if (o.order_sources && ns > 2 * LS_LANES) {
+        CK_RC(order_targets(c, g, g->directed ? T.rp.p : g->row_ptr, g->directed ? T.col.p : g->col,
+                            g->directed ? (g->w ? T.w.p : nullptr) : g->w, wmax, srcs, ns, nullptr, 0, ordered));
+        srcs = ordered.p;
+    }
+    // items: batches of 32 targets (ordered when requested)
     int64_t s0, s1;
     shard_sources(o, ns, s0, s1);
     const int spl = choose_spl(c, s1 - s0, o);
@@ -739,18 +835,9 @@ int brandes_pp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t n
     {
         DBuf<int32_t> Sord;
         const int32_t* Suse = Sp;
-        if (o.order_sources) {
-            DBuf<uint64_t> keys(c, ns), kb(c, ns);
-            DBuf<uint32_t> vals(c, ns), vb(c, ns);
-            DBuf<int64_t> hist(c, radix_hist_elems(ns)), tmp(c, scan_tmp_elems(radix_hist_elems(ns)));
-            CK_ALLOC(keys); CK_ALLOC(kb); CK_ALLOC(vals); CK_ALLOC(vb); CK_ALLOC(hist); CK_ALLOC(tmp);
-            sort_keys_by_part_kernel<<<(unsigned)std::min<int64_t>((ns + 255) / 256, 8192), 256, 0, c->stream>>>(
-                Sp, ns, part, keys.p, vals.p);
-            c->launches++;
-            radix_sort_pairs(keys.p, vals.p, kb.p, vb.p, ns, bits_for((uint64_t)k), hist.p, tmp.p, c->stream,
-                             c->launches);
-            CK_ALLOC(Sord.alloc(c, ns));
-            CK_CUDA(cudaMemcpyAsync(Sord.p, vals.p, ns * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
+        if (o.order_sources && ns > 2 * LS_LANES) {
+            CK_RC(order_targets(c, g, g->directed ? Tin.rp.p : g->row_ptr, g->directed ? Tin.col.p : g->col,
+                                g->directed ? (g->w ? Tin.w.p : nullptr) : g->w, wmax, Sp, ns, part, k, Sord));
             Suse = Sord.p;
         }
         sk_target_ids(Suse, (int32_t)ns, K.skid.p, tsk.p, tcnt.p, c->stream);

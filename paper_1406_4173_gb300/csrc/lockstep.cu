@@ -19,6 +19,8 @@
 // the next entry is fetched while the current one is processed, a group of arcs issues all its
 // distance-row loads and then all its sigma (or c) loads together, bucket marks and
 // partial-sum updates are fire-and-forget atomics.
+#include <type_traits>
+
 #include "lockstep.cuh"
 
 namespace bcpp {
@@ -73,15 +75,40 @@ __device__ __forceinline__ void ld_row(const float* p, float (&x)[SPL]) {
     }
 }
 
-// Visit the arcs [a0, a0 + deg) of one row in groups of UNROLL: 32 heads (and weights and
-// multiplicities) come in one coalesced load and are broadcast by shuffle; the distance rows
-// of a whole group (dl0 = this lane's slice of the slot's distance array) are loaded before
-// the group is handed to f, which then issues its own dependent loads for the whole group.
+// One group of U arcs starting at chunk position j: heads (and weights and multiplicities)
+// are broadcast by shuffle from the chunk's registers, then the distance rows of the whole
+// group are loaded before the group is handed to f (with its size as a compile-time tag), so
+// f can issue its own dependent loads for the whole group at once.
+template <int U, int SPL, bool WEIGHTED, bool MULT, class F>
+__device__ __forceinline__ void arc_group(int32_t mv, int32_t mw, uint64_t mm, int j, int cnt, const int32_t* dl0,
+                                          F&& f) {
+    constexpr int SH = SPL == 1 ? 5 : 6;
+    int32_t vv[U], ww[U], dv[U][SPL];
+    uint64_t mk[U];
+#pragma unroll
+    for (int k = 0; k < U; k++) {
+        vv[k] = __shfl_sync(FULL, mv, (j + k) & 31);
+        ww[k] = WEIGHTED ? __shfl_sync(FULL, mw, (j + k) & 31) : 1;
+        mk[k] = MULT ? shfl_u64(mm, (j + k) & 31) : 1ull;
+    }
+#pragma unroll
+    for (int k = 0; k < U; k++) {
+        if (j + k < cnt) {
+            ld_row<SPL>(dl0 + ((uint32_t)vv[k] << SH), dv[k]);
+        } else {
+#pragma unroll
+            for (int s = 0; s < SPL; s++) dv[k][s] = DINF;
+        }
+    }
+    f(std::integral_constant<int, U>{}, vv, ww, mk, dv, cnt - j);
+}
+
+// Visit the arcs [a0, a0 + deg) of one row: 32 heads per coalesced load, then groups of
+// UNROLL arcs, or of UNROLL / 2 when at most that many are left (low-degree rows waste less).
 template <int UNROLL, int SPL, bool WEIGHTED, bool MULT, class F>
 __device__ __forceinline__ void for_arc_groups(const int32_t* __restrict__ col, const int32_t* __restrict__ w,
                                                const uint64_t* __restrict__ mu, int64_t a0, int32_t deg,
                                                const int32_t* dl0, int lane, F&& f) {
-    constexpr int SH = SPL == 1 ? 5 : 6;
     for (int32_t c0 = 0; c0 < deg; c0 += 32) {
         const int cnt = min(32, deg - c0);
         int32_t mv = 0, mw = 1;
@@ -91,25 +118,14 @@ __device__ __forceinline__ void for_arc_groups(const int32_t* __restrict__ col, 
             if (WEIGHTED) mw = __ldg(w + a0 + c0 + lane);
             if (MULT) mm = __ldg(mu + a0 + c0 + lane);
         }
-        for (int j = 0; j < cnt; j += UNROLL) {
-            int32_t vv[UNROLL], ww[UNROLL], dv[UNROLL][SPL];
-            uint64_t mk[UNROLL];
-#pragma unroll
-            for (int k = 0; k < UNROLL; k++) {
-                vv[k] = __shfl_sync(FULL, mv, (j + k) & 31);
-                ww[k] = WEIGHTED ? __shfl_sync(FULL, mw, (j + k) & 31) : 1;
-                mk[k] = MULT ? shfl_u64(mm, (j + k) & 31) : 1ull;
+        for (int j = 0; j < cnt;) {
+            if (cnt - j > UNROLL / 2) {
+                arc_group<UNROLL, SPL, WEIGHTED, MULT>(mv, mw, mm, j, cnt, dl0, f);
+                j += UNROLL;
+            } else {
+                arc_group<UNROLL / 2, SPL, WEIGHTED, MULT>(mv, mw, mm, j, cnt, dl0, f);
+                j += UNROLL / 2;
             }
-#pragma unroll
-            for (int k = 0; k < UNROLL; k++) {
-                if (j + k < cnt) {
-                    ld_row<SPL>(dl0 + ((uint32_t)vv[k] << SH), dv[k]);
-                } else {
-#pragma unroll
-                    for (int s = 0; s < SPL; s++) dv[k][s] = DINF;
-                }
-            }
-            f(vv, ww, mk, dv, cnt - j);
         }
     }
 }
@@ -276,11 +292,12 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
 #pragma unroll
                     for (int s = 0; s < SPL; s++) acc[s] = 0;
                     // sigma(s,u) = sum over parents v (d(v) + w(v,u) = D) of sigma(s,v) * m(v,u)
-                    auto pull_group = [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk,
+                    auto pull_group = [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t* mk,
                                           const int32_t (*dv)[SPL], int left) {
-                        uint64_t sp[UNROLL][SPL];
+                        constexpr int U = decltype(tag)::value;
+                        uint64_t sp[U][SPL];
 #pragma unroll
-                        for (int k = 0; k < UNROLL; k++) {
+                        for (int k = 0; k < U; k++) {
                             bool par[SPL], anyp = false;
 #pragma unroll
                             for (int s = 0; s < SPL; s++) {
@@ -294,16 +311,17 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                             for (int s = 0; s < SPL; s++) sp[k][s] = par[s] ? t[s] : 0ull;
                         }
 #pragma unroll
-                        for (int k = 0; k < UNROLL; k++)
+                        for (int k = 0; k < U; k++)
 #pragma unroll
                             for (int s = 0; s < SPL; s++)
                                 if (sp[k][s]) acc[s] = madd_ck(acc[s], sp[k][s], MULT ? mk[k] : 1ull, ovf);
                     };
                     // relax the out-arcs: lower tentative distances, mark improved heads
-                    auto relax_group = [&](const int32_t* vv, const int32_t* ww, const int32_t (*dv)[SPL],
+                    auto relax_group = [&](auto tag, const int32_t* vv, const int32_t* ww, const int32_t (*dv)[SPL],
                                            int left) {
+                        constexpr int U = decltype(tag)::value;
 #pragma unroll
-                        for (int k = 0; k < UNROLL; k++) {
+                        for (int k = 0; k < U; k++) {
                             if (k >= left) break;
                             const int64_t nd64 = (int64_t)D + ww[k];
                             const int32_t nd = nd64 < DINF ? (int32_t)nd64 : DINF;
@@ -330,22 +348,22 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                     };
                     if (FUSED) {
                         for_arc_groups<UNROLL, SPL, WEIGHTED, MULT>(A.col, A.w, A.mu, cur.a0, cur.deg, dl0, lane,
-                            [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk, const int32_t (*dv)[SPL],
-                                int left) {
-                                pull_group(vv, ww, mk, dv, left);
-                                relax_group(vv, ww, dv, left);
+                            [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t* mk,
+                                const int32_t (*dv)[SPL], int left) {
+                                pull_group(tag, vv, ww, mk, dv, left);
+                                relax_group(tag, vv, ww, dv, left);
                             });
                     } else {
                         if (D > 0) {
                             const int64_t i0 = __ldg(irp + u);
                             const int32_t ideg = (int32_t)(__ldg(irp + u + 1) - i0);
                             for_arc_groups<UNROLL, SPL, WEIGHTED, MULT>(A.icol, A.iw, A.imu, i0, ideg, dl0, lane,
-                                [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk,
-                                    const int32_t (*dv)[SPL], int left) { pull_group(vv, ww, mk, dv, left); });
+                                [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t* mk,
+                                    const int32_t (*dv)[SPL], int left) { pull_group(tag, vv, ww, mk, dv, left); });
                         }
                         for_arc_groups<UNROLL, SPL, WEIGHTED, false>(A.col, A.w, nullptr, cur.a0, cur.deg, dl0, lane,
-                            [&](const int32_t* vv, const int32_t* ww, const uint64_t*, const int32_t (*dv)[SPL],
-                                int left) { relax_group(vv, ww, dv, left); });
+                            [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t*,
+                                const int32_t (*dv)[SPL], int left) { relax_group(tag, vv, ww, dv, left); });
                     }
 #pragma unroll
                     for (int s = 0; s < SPL; s++)
@@ -400,11 +418,12 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
 #pragma unroll
                         for (int s = 0; s < SPL; s++) acc[s] = (DT)0;
                         for_arc_groups<UNROLL, SPL, WEIGHTED, MULT>(A.col, A.w, A.mu, cur.a0, cur.deg, dl0, lane,
-                            [&](const int32_t* vv, const int32_t* ww, const uint64_t* mk, const int32_t (*dv)[SPL],
-                                int left) {
-                                DT cv[UNROLL][SPL];
+                            [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t* mk,
+                                const int32_t (*dv)[SPL], int left) {
+                                constexpr int U = decltype(tag)::value;
+                                DT cv[U][SPL];
 #pragma unroll
-                                for (int k = 0; k < UNROLL; k++) {
+                                for (int k = 0; k < U; k++) {
                                     bool sc[SPL], anys = false;
 #pragma unroll
                                     for (int s = 0; s < SPL; s++) {
@@ -418,7 +437,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                                     for (int s = 0; s < SPL; s++) cv[k][s] = sc[s] ? t[s] : (DT)0;
                                 }
 #pragma unroll
-                                for (int k = 0; k < UNROLL; k++)
+                                for (int k = 0; k < U; k++)
 #pragma unroll
                                     for (int s = 0; s < SPL; s++) acc[s] += MULT ? (DT)mk[k] * cv[k][s] : cv[k][s];
                             });
