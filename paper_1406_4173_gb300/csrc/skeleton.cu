@@ -254,9 +254,12 @@ __global__ void target_ids_kernel(const int32_t* S, int32_t nS, const int32_t* s
     if (threadIdx.x == 0) *cnt = base;
 }
 
-// One warp per (non-frontier node, slot): lanes are the slot's sources.  Forward: the
-// distance and count through the entry frontiers; backward: the dependency through the exit
-// frontiers that stay on a shortest path (Eq. 13).
+// One warp per group of CV non-frontier nodes and one slot; lanes are the slot's sources.
+// Forward: the distance and count through the entry frontiers; backward: the dependency
+// through the exit frontiers that stay on a shortest path (Eq. 13).  A frontier's state row
+// (d, sigma, c of the 32 sources) is read once per group and used for all CV nodes.
+constexpr int CV = 4;
+
 template <typename DT>
 __global__ void __launch_bounds__(256)
 centrality_kernel(const CentralityUnit* __restrict__ units, SkTables T, const uint32_t* __restrict__ pnodes,
@@ -271,44 +274,90 @@ centrality_kernel(const CentralityUnit* __restrict__ units, SkTables T, const ui
     const int64_t t0 = T.toff[i];
     const int32_t ps = T.pstart[i];
     const int64_t sb = skbase[i];
-    const int32_t* d = d_all + (int64_t)slot * cap_n * 32 + sb * 32;
-    const uint64_t* sg = sg_all + (int64_t)slot * cap_n * 32 + sb * 32;
-    const DT* dl = dl_all + (int64_t)slot * cap_n * 32 + sb * 32;
+    const int32_t* d = d_all + (int64_t)slot * cap_n * 32 + sb * 32 + lane;
+    const uint64_t* sg = sg_all + (int64_t)slot * cap_n * 32 + sb * 32 + lane;
+    const DT* dl = dl_all + (int64_t)slot * cap_n * 32 + sb * 32 + lane;
     bool ovf = false;
-    for (int32_t vl = U.v0 + warp; vl < U.v1; vl += nw) {
-        const int32_t* te = T.td + t0 + (int64_t)vl * nfi;
-        const uint64_t* se = T.ts + t0 + (int64_t)vl * nfi;
-        const int32_t* tx = T.tdr + t0 + (int64_t)vl * nfi;
-        const uint64_t* sx = T.tsr + t0 + (int64_t)vl * nfi;
-        int64_t dv = DINF;
-        uint64_t sv = 0;
+    for (int32_t vb = U.v0 + warp * CV; vb < U.v1; vb += nw * CV) {
+        const int nv = min(CV, U.v1 - vb);
+        const int64_t row0 = t0 + (int64_t)vb * nfi;     // table row of node vb; node vb+j at row0 + j*nfi
+        int64_t dv[CV];
+        uint64_t sv[CV];
+#pragma unroll
+        for (int j = 0; j < CV; j++) { dv[j] = DINF; sv[j] = 0; }
         for (int32_t f = 0; f < nfi; f++) {
-            const int32_t dfv = te[f];
-            if (dfv == DINF) continue;
-            const int32_t dsf = d[(int64_t)f * 32 + lane];
+            int32_t dfv[CV];
+            bool any = false;
+#pragma unroll
+            for (int j = 0; j < CV; j++) {
+                dfv[j] = j < nv ? T.td[row0 + (int64_t)j * nfi + f] : DINF;
+                any |= dfv[j] != DINF;
+            }
+            if (!any) continue;
+            const int32_t dsf = d[(int64_t)f * 32];
             if (dsf == DINF) continue;
-            const int64_t c = (int64_t)dsf + dfv;
-            if (c < dv) { dv = c; sv = 0; }
-            if (c == dv) sv = madd_ck(sv, sg[(int64_t)f * 32 + lane], se[f], ovf);
-        }
-        DT acc = (DT)0;
-        if (sv != 0) {
-            for (int32_t f = 0; f < nfi; f++) {
-                const int32_t dvf = tx[f];
-                if (dvf == DINF) continue;
-                const int32_t dsf = d[(int64_t)f * 32 + lane];
-                if (dsf == DINF || dv + dvf != (int64_t)dsf) continue;
-                acc += (DT)sx[f] * dl[(int64_t)f * 32 + lane];
+            bool tight[CV], need = false;
+#pragma unroll
+            for (int j = 0; j < CV; j++) {
+                tight[j] = false;
+                if (dfv[j] != DINF) {
+                    const int64_t c = (int64_t)dsf + dfv[j];
+                    if (c < dv[j]) { dv[j] = c; sv[j] = 0; }
+                    tight[j] = c == dv[j];
+                    need |= tight[j];
+                }
+            }
+            if (need) {
+                const uint64_t ssf = sg[(int64_t)f * 32];
+#pragma unroll
+                for (int j = 0; j < CV; j++)
+                    if (tight[j]) sv[j] = madd_ck(sv[j], ssf, T.ts[row0 + (int64_t)j * nfi + f], ovf);
             }
         }
-        const double delta = (double)((DT)sv * acc);
-        const double tot = warp_sum(delta);
-        if (lane == 0 && tot != 0.0) {
-            const int64_t ix = (int64_t)slot * cap_bc + pnodes[ps + vl];
-            double s = bc_sum[ix], c = bc_cmp[ix];
-            neumaier_add(s, c, tot);
-            bc_sum[ix] = s;
-            bc_cmp[ix] = c;
+        DT acc[CV];
+        bool live = false;
+#pragma unroll
+        for (int j = 0; j < CV; j++) {
+            acc[j] = (DT)0;
+            live |= sv[j] != 0;
+        }
+        if (__any_sync(FULL, live)) {
+            for (int32_t f = 0; f < nfi; f++) {
+                int32_t dvf[CV];
+                bool any = false;
+#pragma unroll
+                for (int j = 0; j < CV; j++) {
+                    dvf[j] = (j < nv && sv[j] != 0) ? T.tdr[row0 + (int64_t)j * nfi + f] : DINF;
+                    any |= dvf[j] != DINF;
+                }
+                if (!any) continue;
+                const int32_t dsf = d[(int64_t)f * 32];
+                if (dsf == DINF) continue;
+                bool on[CV], need = false;
+#pragma unroll
+                for (int j = 0; j < CV; j++) {
+                    on[j] = dvf[j] != DINF && dv[j] + dvf[j] == (int64_t)dsf;
+                    need |= on[j];
+                }
+                if (need) {
+                    const DT cf = dl[(int64_t)f * 32];
+#pragma unroll
+                    for (int j = 0; j < CV; j++)
+                        if (on[j]) acc[j] += (DT)T.tsr[row0 + (int64_t)j * nfi + f] * cf;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < CV; j++) {
+            const double delta = (double)((DT)sv[j] * acc[j]);
+            const double tot = warp_sum(delta);
+            if (lane == 0 && j < nv && tot != 0.0) {
+                const int64_t ix = (int64_t)slot * cap_bc + pnodes[ps + vb + j];
+                double s0 = bc_sum[ix], c0 = bc_cmp[ix];
+                neumaier_add(s0, c0, tot);
+                bc_sum[ix] = s0;
+                bc_cmp[ix] = c0;
+            }
         }
     }
     if (__any_sync(FULL, ovf) && lane == 0) atomicOr(&flags[FLAG_SIGMA_OVF], 1u);
