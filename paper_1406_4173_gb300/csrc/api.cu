@@ -293,10 +293,20 @@ int64_t slot_bytes(int64_t cap_n, int nb, bool fp32, int order_factor = 8, int s
            2 * (cap_n + 4098) * 4 + (int64_t)nb * bm_words * 4 + nb;
 }
 
-// Choose how many slots (resident batches) to run, within the memory budget.
-int choose_slots(bcpp_ctx* c, int nitems, int ctas_per_sm, int64_t per_slot, int64_t per_slot_bc) {
+// CTAs per batch: with fewer batches than resident CTAs (two per SM), 2 or 4 CTAs of a
+// thread-block cluster share each batch so that every SM has work.
+int choose_cluster(const bcpp_ctx* c, int nitems, const bcpp_opts& o) {
+    const int cps = o.ctas_per_sm > 0 ? o.ctas_per_sm : 2;
+    const int64_t target = (int64_t)cps * c->num_sms;
+    int cl = 1;
+    while (cl < 4 && (int64_t)nitems * cl * 2 <= target) cl *= 2;
+    return cl;
+}
+
+// Choose how many slots (batches in flight, cl CTAs each) to run, within the memory budget.
+int choose_slots(bcpp_ctx* c, int nitems, int ctas_per_sm, int64_t per_slot, int64_t per_slot_bc, int cl = 1) {
     int cps = ctas_per_sm > 0 ? ctas_per_sm : 2;
-    int slots = std::min<int64_t>(nitems, (int64_t)cps * c->num_sms);
+    int slots = std::min<int64_t>(nitems, std::max<int64_t>(1, (int64_t)cps * c->num_sms / cl));
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     int64_t reusable = 0;
@@ -444,7 +454,7 @@ int order_targets(bcpp_ctx* c, const bcpp_graph* g, const int64_t* irp, const in
     P.dbg_n = n;
     P.item_counter = ws.counter.p;
     P.flags = c->flags;
-    ls_launch(false, !g->directed, A, P, ws.W, item.p, 1, 1, c->stream);
+    ls_launch(false, !g->directed, A, P, ws.W, item.p, 1, 1, c->stream, 1, 4);   // one batch: 4-CTA cluster
     c->launches++;
     // stable sorts: by level, then by part
     DBuf<uint64_t> keys(c, ns), kb(c, ns);
@@ -530,8 +540,9 @@ int brandes_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, 
     const int64_t hoff[2] = {0, n};
     CK_RC(to_dev(c, node_off.p, hoff, 2));
     const int nb = g->w ? (int)wmax + 1 : 2;
+    const int cl = spl == 1 ? choose_cluster(c, nitems, o) : 1;
     const int slots =
-        choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(n, nb, fp32, c->order_factor, spl), (int64_t)n * 16);
+        choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(n, nb, fp32, c->order_factor, spl), (int64_t)n * 16, cl);
     SlotWs ws;
     CK_RC(alloc_slots(c, ws, slots, n, nb, fp32, n, spl));
     LsArena A{};
@@ -553,7 +564,7 @@ int brandes_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, 
     P.flags = c->flags;
     Timer tb(c);
     tb.start();
-    ls_launch(fp32, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream, spl);
+    ls_launch(fp32, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream, spl, cl);
     c->launches++;
     tb.stop();
     CK_CUDA(cudaGetLastError());
@@ -865,9 +876,10 @@ int brandes_pp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t n
     const int spl = hunits.empty() ? choose_spl(c, s1 - s0, o) : 1;
     std::vector<LsItem> hitems = make_items(0, s0, s1, 32 * spl);
     const int nitems = (int)hitems.size();
+    const int cl = (nitems > 0 && spl == 1) ? choose_cluster(c, nitems, o) : 1;
     const int slots = nitems > 0 ? choose_slots(c, nitems, o.ctas_per_sm,
                                                 slot_bytes(std::max(N, 1), nb, fp32, c->order_factor, spl),
-                                                (int64_t)n * 16)
+                                                (int64_t)n * 16, cl)
                                  : 1;
     CK_RC(alloc_slots(c, ws, slots, std::max(N, 1), nb, fp32, n, spl));
     slots_used = slots;
@@ -927,7 +939,7 @@ int brandes_pp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t n
             P.item_counter = ws.counter.p;
             P.flags = c->flags;
             tbr.start();
-            ls_launch(fp32, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream, spl);
+            ls_launch(fp32, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream, spl, cl);
             c->launches++;
             tbr.stop();
             CK_CUDA(cudaGetLastError());
@@ -943,7 +955,7 @@ int brandes_pp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t n
             P.items_static = 1;
             P.flags = c->flags;
             tbr.start();
-            ls_launch(fp32, !g->directed, A, P, ws.W, items.p + c0, cn, cn, c->stream);
+            ls_launch(fp32, !g->directed, A, P, ws.W, items.p + c0, cn, cn, c->stream, 1, cl);
             c->launches++;
             tbr.stop();
             CK_CUDA(cudaGetLastError());

@@ -19,22 +19,25 @@
 // the next entry is fetched while the current one is processed, a group of arcs issues all its
 // distance-row loads and then all its sigma (or c) loads together, bucket marks and
 // partial-sum updates are fire-and-forget atomics.
+#include <cooperative_groups.h>
 #include <type_traits>
 
 #include "lockstep.cuh"
 
 namespace bcpp {
 
+namespace cg = cooperative_groups;
+
 namespace {
 
 // Mark head v in the bucket of distance nd (fire-and-forget: a stale mark only costs a
 // visit that finds no lane at that distance).
 __device__ __forceinline__ void mark_bucket(const LsParams& P, uint32_t* bm, uint8_t* bflag, int64_t bm_words,
-                                            int v, int32_t nd, int* s_maxpush) {
+                                            int v, int32_t nd, int* maxpush) {
     const int bk = nd % P.nb;
     atomicOr(&bm[(int64_t)bk * bm_words + (v >> 5)], 1u << (v & 31));
     bflag[bk] = 1;
-    atomicMax(s_maxpush, nd);
+    atomicMax(maxpush, nd);
 }
 
 // vector access to this lane's SPL consecutive values of one node row
@@ -130,10 +133,16 @@ __device__ __forceinline__ void for_arc_groups(const int32_t* __restrict__ col, 
     }
 }
 
+// Scalar control state of one batch; with a cluster it lives in the leader CTA's shared memory
+// and the other CTAs reach it through distributed shared memory.
+struct LsCtl {
+    int item, pos, next, D, done, maxpush, nsteps, err, end;
+};
+
 // Fetch the next entry index of the current step for this warp (dynamic scheduling).
-__device__ __forceinline__ int fetch_entry(int* s_next, int lane) {
+__device__ __forceinline__ int fetch_entry(int* next, int lane) {
     int e = 0;
-    if (lane == 0) e = atomicAdd(s_next, 1);
+    if (lane == 0) e = atomicAdd(next, 1);
     return __shfl_sync(FULL, e, 0);
 }
 
@@ -144,12 +153,28 @@ __device__ __forceinline__ LsEnt load_entry(const LsEnt* order, int e, int end) 
     return z;
 }
 
-template <typename DT, int SPL, bool FUSED, bool WEIGHTED, bool MULT>
+template <typename DT, int SPL, int CL, bool FUSED, bool WEIGHTED, bool MULT>
 __global__ void __launch_bounds__(LS_THREADS, 2)
 ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __restrict__ items, int nitems) {
-    __shared__ int s_item, s_pos, s_next, s_D, s_done, s_maxpush, s_nsteps, s_err, s_end;
+    // CL CTAs (a thread-block cluster when CL > 1) share one batch and one slot
+    __shared__ LsCtl s_ctl;
+    LsCtl* ctl = &s_ctl;
+    int crank = 0;
+    if constexpr (CL > 1) {
+        cg::cluster_group cluster = cg::this_cluster();
+        crank = (int)cluster.block_rank();
+        ctl = cluster.map_shared_rank(&s_ctl, 0);
+    }
+    auto sync = [&]() {
+        if constexpr (CL == 1) __syncthreads();
+        else cg::this_cluster().sync();
+    };
+    constexpr int GT = CL * LS_THREADS;            // threads sharing the batch
+    const int gtid = crank * LS_THREADS + (int)threadIdx.x;
+    const int gwarp = gtid >> 5;
+    const bool leader = gtid == 0;
     const int lane = threadIdx.x & 31;
-    const int slot = blockIdx.x;
+    const int slot = blockIdx.x / CL;
     constexpr int ROW = 32 * SPL;                 // sources per node row
     constexpr int SH = SPL == 1 ? 5 : 6;          // log2(ROW)
     // arcs handled per group (bounded by the 64 registers of two resident 512-thread CTAs)
@@ -171,13 +196,13 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
 
     bool first = true;
     for (;;) {
-        if (threadIdx.x == 0) {
-            if (P.items_static) s_item = first ? slot : nitems;
-            else s_item = atomicAdd(P.item_counter, 1);
+        if (leader) {
+            if (P.items_static) ctl->item = first ? slot : nitems;
+            else ctl->item = atomicAdd(P.item_counter, 1);
         }
         first = false;
-        __syncthreads();
-        const int it = s_item;
+        sync();
+        const int it = ctl->item;
         if (it >= nitems) break;
         const LsItem I = items[it];
         const int64_t base = A.node_off[I.g];
@@ -193,7 +218,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
         }
 
         // sources: d = 0, sigma = 1, bucket 0
-        if (threadIdx.x < 32) {
+        if (gtid < 32) {
 #pragma unroll
             for (int s = 0; s < SPL; s++) {
                 if (my_src[s] >= 0) {
@@ -203,50 +228,50 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                 }
             }
         }
-        if (threadIdx.x == 0) {
+        if (leader) {
             bflag[0] = 1;
-            s_pos = 0; s_D = 0; s_maxpush = 0; s_nsteps = 0; s_err = 0;
+            ctl->pos = 0; ctl->D = 0; ctl->maxpush = 0; ctl->nsteps = 0; ctl->err = 0;
         }
-        __syncthreads();
+        sync();
 
         // ------------------------------------------------------------------ forward
         for (;;) {
-            if (threadIdx.x == 0) {
-                int D = s_D;
-                while (D <= s_maxpush && bflag[D % P.nb] == 0) D++;
-                s_D = D;
-                s_done = (D > s_maxpush) || s_err;
-                if (!s_done) {
+            if (leader) {
+                int D = ctl->D;
+                while (D <= ctl->maxpush && bflag[D % P.nb] == 0) D++;
+                ctl->D = D;
+                ctl->done = (D > ctl->maxpush) || ctl->err;
+                if (!ctl->done) {
                     bflag[D % P.nb] = 0;
-                    if (s_nsteps >= W.cap_steps) {
-                        s_err = 1; s_done = 1;
+                    if (ctl->nsteps >= W.cap_steps) {
+                        ctl->err = 1; ctl->done = 1;
                     } else {
-                        step_d[s_nsteps] = D;
-                        step_beg[s_nsteps] = s_pos;
-                        s_next = s_pos;
+                        step_d[ctl->nsteps] = D;
+                        step_beg[ctl->nsteps] = ctl->pos;
+                        ctl->next = ctl->pos;
                     }
                 }
             }
-            __syncthreads();
-            if (s_done) break;
-            const int32_t D = s_D;
-            const int beg = s_next;
+            sync();
+            if (ctl->done) break;
+            const int32_t D = ctl->D;
+            const int beg = ctl->next;
             // collect bucket D into the order list
             {
                 uint32_t* bmD = bm + (int64_t)(D % P.nb) * W.bm_words;
                 const int nwords = (n + 31) >> 5;
                 const int nwr = (nwords + 31) & ~31;
-                for (int wi = threadIdx.x; wi < nwr; wi += LS_THREADS) {
+                for (int wi = gtid; wi < nwr; wi += GT) {
                     uint32_t x = wi < nwords ? bmD[wi] : 0u;
                     if (x) bmD[wi] = 0u;
                     const int c = __popc(x);
                     const int incl = warp_incl_scan(c, lane);
                     const int tot = __shfl_sync(FULL, incl, 31);
                     int bpos = 0;
-                    if (lane == 31 && tot) bpos = atomicAdd(&s_pos, tot);
+                    if (lane == 31 && tot) bpos = atomicAdd(&ctl->pos, tot);
                     bpos = __shfl_sync(FULL, bpos, 31);
                     if (tot && bpos + tot > W.cap_order) {
-                        if (lane == 0) atomicExch(&s_err, 1);
+                        if (lane == 0) atomicExch(&ctl->err, 1);
                         continue;
                     }
                     int p = bpos + incl - c;
@@ -257,24 +282,24 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                     }
                 }
             }
-            __syncthreads();
-            if (threadIdx.x == 0) s_end = min(s_pos, (int)W.cap_order);
-            __syncthreads();
-            if (s_err) break;
-            const int end = s_end;
+            sync();
+            if (leader) ctl->end = min(ctl->pos, (int)W.cap_order);
+            sync();
+            if (ctl->err) break;
+            const int end = ctl->end;
             // attach every entry's out-arc range (independent loads, all threads)
-            for (int e = beg + threadIdx.x; e < end; e += LS_THREADS) {
+            for (int e = beg + gtid; e < end; e += GT) {
                 const int32_t u = order[e].u;
                 const int64_t a0 = __ldg(rp + u);
                 order[e].a0 = a0;
                 order[e].deg = (int32_t)(__ldg(rp + u + 1) - a0);
             }
-            __syncthreads();
+            sync();
             // settle the nodes of step D
-            int e = fetch_entry(&s_next, lane);
+            int e = fetch_entry(&ctl->next, lane);
             LsEnt cur = load_entry(order, e, end);
             while (e < end) {
-                const int e2 = fetch_entry(&s_next, lane);
+                const int e2 = fetch_entry(&ctl->next, lane);
                 const LsEnt nxt = load_entry(order, e2, end);
                 const int u = cur.u;
                 int32_t du[SPL];
@@ -342,7 +367,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                                     }
                                 }
                                 if (lane == __ffs(im) - 1)
-                                    mark_bucket(P, bm, bflag, W.bm_words, vv[k], nd, &s_maxpush);
+                                    mark_bucket(P, bm, bflag, W.bm_words, vv[k], nd, &ctl->maxpush);
                             }
                         }
                     };
@@ -373,36 +398,36 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                 e = e2;
                 cur = nxt;
             }
-            __syncthreads();
-            if (threadIdx.x == 0) { s_nsteps++; s_D = D + 1; }
+            sync();
+            if (leader) { ctl->nsteps++; ctl->D = D + 1; }
         }
-        __syncthreads();
-        const int nsteps = s_nsteps;
-        const int olen = min(s_pos, (int)W.cap_order);
-        if (s_err) {
+        sync();
+        const int nsteps = ctl->nsteps;
+        const int olen = min(ctl->pos, (int)W.cap_order);
+        if (ctl->err) {
             // a list outgrew its bound: report it and leave the slot clean for the next batch
-            if (threadIdx.x == 0) atomicOr(&P.flags[FLAG_CAPACITY], 1u);
-            for (int64_t i = threadIdx.x; i < (int64_t)n * ROW; i += LS_THREADS) d[i] = DINF;
-            for (int64_t i = threadIdx.x; i < (int64_t)P.nb * W.bm_words; i += LS_THREADS) bm[i] = 0u;
-            for (int i = threadIdx.x; i < P.nb; i += LS_THREADS) bflag[i] = 0;
-            if (P.mode == LS_SKEL && threadIdx.x == 0) {
+            if (leader) atomicOr(&P.flags[FLAG_CAPACITY], 1u);
+            for (int64_t i = gtid; i < (int64_t)n * ROW; i += GT) d[i] = DINF;
+            for (int64_t i = gtid; i < (int64_t)P.nb * W.bm_words; i += GT) bm[i] = 0u;
+            for (int i = gtid; i < P.nb; i += GT) bflag[i] = 0;
+            if (P.mode == LS_SKEL && leader) {
                 W.hdr[slot * 4 + 0] = 0; W.hdr[slot * 4 + 1] = 0; W.hdr[slot * 4 + 2] = it;
             }
-            __syncthreads();
+            sync();
             continue;
         }
 
         if (P.mode == LS_BRANDES || P.mode == LS_SKEL) {
             // -------------------------------------------------------------- backward
             for (int st = nsteps - 1; st >= 0; st--) {
-                if (threadIdx.x == 0) s_next = step_beg[st];
-                __syncthreads();
+                if (leader) ctl->next = step_beg[st];
+                sync();
                 const int32_t D = step_d[st];
                 const int end = (st + 1 < nsteps) ? step_beg[st + 1] : olen;
-                int e = fetch_entry(&s_next, lane);
+                int e = fetch_entry(&ctl->next, lane);
                 LsEnt cur = load_entry(order, e, end);
                 while (e < end) {
-                    const int e2 = fetch_entry(&s_next, lane);
+                    const int e2 = fetch_entry(&ctl->next, lane);
                     const LsEnt nxt = load_entry(order, e2, end);
                     const int u = cur.u;
                     int32_t du[SPL];
@@ -465,14 +490,13 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                     e = e2;
                     cur = nxt;
                 }
-                __syncthreads();
+                sync();
             }
         } else if constexpr (SPL == 1) {
             if (P.mode == LS_TABLE) {
                 // ---------------------------------------------------------- tables d_i[v][f], sigma_i[v][f]
                 const int64_t t0 = P.toff[I.g];
-                const int warp = threadIdx.x >> 5;
-                for (int v = warp; v < n; v += LS_THREADS / 32) {
+                for (int v = gwarp; v < n; v += GT / 32) {
                     if (lane < I.nsrc) {
                         const int32_t dv = dl0[(uint32_t)v << SH];
                         const int64_t o = t0 + (int64_t)v * nf + I.aux + lane;
@@ -480,10 +504,9 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                         P.ts[o] = dv == DINF ? 0ull : sl0[(uint32_t)v << SH];
                     }
                 }
-                __syncthreads();
+                sync();
             } else if (P.mode == LS_SSSP) {
-                const int warp = threadIdx.x >> 5;
-                for (int v = warp; v < n; v += LS_THREADS / 32) {
+                for (int v = gwarp; v < n; v += GT / 32) {
                     if (lane < I.nsrc) {
                         const int32_t dv = dl0[(uint32_t)v << SH];
                         const int64_t o = (int64_t)(I.src_off + lane) * P.dbg_n + v;
@@ -491,27 +514,28 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                         P.dbg_s[o] = dv == DINF ? 0ull : sl0[(uint32_t)v << SH];
                     }
                 }
-                __syncthreads();
+                sync();
             }
         }
 
         if (P.mode == LS_SKEL) {
-            if (threadIdx.x == 0) {
+            if (leader) {
                 W.hdr[slot * 4 + 0] = olen;
                 W.hdr[slot * 4 + 1] = nsteps;
                 W.hdr[slot * 4 + 2] = it;
             }
         } else {
             // restore "unreached" on every touched row
-            const int warp = threadIdx.x >> 5;
-            for (int e = warp; e < olen; e += LS_THREADS / 32) {
+            for (int e = gwarp; e < olen; e += GT / 32) {
                 int32_t* pd = dl0 + ((uint32_t)order[e].u << SH);
 #pragma unroll
                 for (int s = 0; s < SPL; s++) pd[s] = DINF;
             }
         }
-        __syncthreads();
+        sync();
     }
+    // with a cluster, the leader's shared memory must outlive the other CTAs' last reads
+    sync();
 }
 
 __global__ void ls_reset_kernel(const LsSlots W) {
@@ -530,26 +554,54 @@ __global__ void fill_i32_kernel(int32_t* p, int32_t v, int64_t n) {
         p[i] = v;
 }
 
-template <typename DT, int SPL>
+template <typename DT, int SPL, int CL, bool F, bool WT, bool M>
+void ls_go(const LsArena& A, const LsParams& P, const LsSlots& W, const LsItem* items, int nitems, int slots,
+           cudaStream_t st) {
+    if constexpr (CL == 1) {
+        ls_kernel<DT, SPL, 1, F, WT, M><<<slots, LS_THREADS, 0, st>>>(A, P, W, items, nitems);
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(slots * CL));
+        cfg.blockDim = dim3(LS_THREADS);
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, ls_kernel<DT, SPL, CL, F, WT, M>, A, P, W, items, nitems);
+    }
+}
+
+template <typename DT, int SPL, int CL>
 void ls_launch_t(bool fused, bool weighted, bool mult, const LsArena& A, const LsParams& P, const LsSlots& W,
                  const LsItem* items, int nitems, int slots, cudaStream_t st) {
-#define LS_GO(F, WT, M) ls_kernel<DT, SPL, F, WT, M><<<slots, LS_THREADS, 0, st>>>(A, P, W, items, nitems)
     if (fused) {
-        if (!weighted) LS_GO(true, false, false);
-        else if (!mult) LS_GO(true, true, false);
-        else LS_GO(true, true, true);
+        if (!weighted) ls_go<DT, SPL, CL, true, false, false>(A, P, W, items, nitems, slots, st);
+        else if (!mult) ls_go<DT, SPL, CL, true, true, false>(A, P, W, items, nitems, slots, st);
+        else ls_go<DT, SPL, CL, true, true, true>(A, P, W, items, nitems, slots, st);
     } else {
-        if (!weighted) LS_GO(false, false, false);
-        else if (!mult) LS_GO(false, true, false);
-        else LS_GO(false, true, true);
+        if (!weighted) ls_go<DT, SPL, CL, false, false, false>(A, P, W, items, nitems, slots, st);
+        else if (!mult) ls_go<DT, SPL, CL, false, true, false>(A, P, W, items, nitems, slots, st);
+        else ls_go<DT, SPL, CL, false, true, true>(A, P, W, items, nitems, slots, st);
     }
-#undef LS_GO
+}
+
+template <typename DT>
+void ls_launch_dt(int spl, int cl, bool fused, bool weighted, bool mult, const LsArena& A, const LsParams& P,
+                  const LsSlots& W, const LsItem* items, int nitems, int slots, cudaStream_t st) {
+    if (spl == 2) ls_launch_t<DT, 2, 1>(fused, weighted, mult, A, P, W, items, nitems, slots, st);
+    else if (cl == 4) ls_launch_t<DT, 1, 4>(fused, weighted, mult, A, P, W, items, nitems, slots, st);
+    else if (cl == 2) ls_launch_t<DT, 1, 2>(fused, weighted, mult, A, P, W, items, nitems, slots, st);
+    else ls_launch_t<DT, 1, 1>(fused, weighted, mult, A, P, W, items, nitems, slots, st);
 }
 
 }  // namespace
 
 void ls_launch(bool fp32_delta, bool fused, const LsArena& A, const LsParams& P, const LsSlots& W,
-               const LsItem* items, int nitems, int slots, cudaStream_t st, int spl) {
+               const LsItem* items, int nitems, int slots, cudaStream_t st, int spl, int cl) {
     if (nitems <= 0 || slots <= 0) return;
     // multiplicities > 1 only occur on skeleton arcs, whose weights then exceed 1 as well,
     // so a multiplicity array always comes with a weight array
@@ -557,13 +609,9 @@ void ls_launch(bool fp32_delta, bool fused, const LsArena& A, const LsParams& P,
     const bool weighted = A.w != nullptr;
     if (mult && !weighted) return;
     if (spl == 2 && P.mode != LS_BRANDES) return;   // 64-source rows: Brandes passes only
-    if (spl == 2) {
-        if (fp32_delta) ls_launch_t<float, 2>(fused, weighted, mult, A, P, W, items, nitems, slots, st);
-        else ls_launch_t<double, 2>(fused, weighted, mult, A, P, W, items, nitems, slots, st);
-    } else {
-        if (fp32_delta) ls_launch_t<float, 1>(fused, weighted, mult, A, P, W, items, nitems, slots, st);
-        else ls_launch_t<double, 1>(fused, weighted, mult, A, P, W, items, nitems, slots, st);
-    }
+    if (cl != 1 && cl != 2 && cl != 4) return;
+    if (fp32_delta) ls_launch_dt<float>(spl, cl, fused, weighted, mult, A, P, W, items, nitems, slots, st);
+    else ls_launch_dt<double>(spl, cl, fused, weighted, mult, A, P, W, items, nitems, slots, st);
 }
 
 void ls_reset_launch(const LsSlots& W, int slots, cudaStream_t st) {

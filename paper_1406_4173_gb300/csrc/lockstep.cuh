@@ -1,7 +1,7 @@
 // Lockstep multi-source shortest paths with path counts and dependency accumulation.
 //
-// One CTA owns a batch of up to 32 sources ("lanes") of one graph.  Its state lives in a
-// private slot of device memory laid out node-major, lane-minor ([node][32]), so the 32
+// One CTA (or a cluster of 2 or 4 CTAs) owns a batch of up to 32 sources ("lanes") of one
+// graph.  Its state lives in a private slot of device memory laid out node-major, lane-minor ([node][32]), so the 32
 // sources of a node are one 128-byte line for distances and two for path counts: a warp
 // reads one node's row for all its sources with a single coalesced access, and every lane
 // follows the same adjacency list.  Settling proceeds in exact distance order with circular
@@ -91,10 +91,12 @@ struct LsSlots {
     int32_t* hdr;                // [slot][4]: order length, steps, item, -
 };
 
-// Launch the lockstep kernel over `nitems` items with `slots` CTAs.  spl = sources per lane
-// (1: 32-source batches, rows of 32; 2: 64-source batches, rows of 64, LS_BRANDES only).
+// Launch the lockstep kernel over `nitems` items with `slots` batches in flight.  spl = sources
+// per lane (1: 32-source batches, rows of 32; 2: 64-source batches, rows of 64, LS_BRANDES
+// only).  cl = CTAs per batch (1, 2 or 4; with 2 or 4 they form a thread-block cluster that
+// shares the batch's control state through distributed shared memory; spl = 1 only).
 void ls_launch(bool fp32_delta, bool fused, const LsArena& A, const LsParams& P, const LsSlots& W,
-               const LsItem* items, int nitems, int slots, cudaStream_t st, int spl = 1);
+               const LsItem* items, int nitems, int slots, cudaStream_t st, int spl = 1, int cl = 1);
 
 // Restore the distance rows touched by LS_SKEL batches to "unreached".
 void ls_reset_launch(const LsSlots& W, int slots, cudaStream_t st);

@@ -308,3 +308,18 @@ def test_deep_unit_graphs(bc):
     k = 350
     assert rel_err(got[:300], ref_p) < FP64_TOL
     assert rel_err(got[300:], np.full(700, (k - 1) ** 2 / 2)) < FP64_TOL
+
+
+
+# ----------------------------------------------------------------------------- CTA clusters per batch
+def test_two_cta_clusters(bc):
+    """Between 77 and 152 batches the library runs 2-CTA clusters per batch (4 with fewer,
+    1 with more): plain Brandes and Brandes++ against the oracle in that regime."""
+    g = gen.planted_partition(4000, 8, 0.006, 0.0004, seed=51, wmax=3)
+    G = bc.graph_from_edgelist(g)
+    ref, _ = oracle.brandes(g)                      # 125 batches of 32
+    assert rel_err(bc.brandes(G).cpu().numpy(), ref) < FP64_TOL
+    S = gen.sample_targets(g.n, 3000, seed=52)      # 94 batches
+    ref_s, _ = oracle.brandes(g, S)
+    assert rel_err(bc.brandes(G, S).cpu().numpy(), ref_s) < FP64_TOL
+    assert rel_err(bc.brandes_pp(G, S, g.part).cpu().numpy(), ref_s) < FP64_TOL
