@@ -78,6 +78,8 @@ typedef struct {
                                 * from the highest-degree node (Brandes++: by part, then level), so that
                                 * a batch's sources are close; 0: batch S in the given order.  Only the
                                 * summation order changes, not the result. */
+    int32_t cluster;           /* CTAs per source batch: 0 = auto (2 or 4, as a thread-block cluster, when
+                                * batches are fewer than resident CTAs), or 1, 2, 4 (32-source batches) */
     int32_t shard_index;       /* with shard_count > 1: use only this shard's targets as sources */
     int32_t shard_count;       /* 0 or 1: every target is a source.  Otherwise the targets, in the order
                                 * used for batching, are split into shard_count contiguous shards
@@ -151,6 +153,24 @@ int bcpp_brandes(bcpp_ctx *ctx, const bcpp_graph *g, const int32_t *S, int32_t n
 int bcpp_brandes_pp(bcpp_ctx *ctx, const bcpp_graph *g, const int32_t *S, int32_t nS,
                     const int32_t *part, int32_t k, const bcpp_opts *opts, double *bc_out,
                     bcpp_stats *stats);
+
+/* Brandes++ for separate source and destination sets: the step of Brandes++All (Sec. 5, Alg. 3)
+ * written Brandes_SK(G_sk, S_sc, S_dest), followed by Centrality.  bc_out[n] receives
+ * sum over s in Ssrc, t in Sdst, s != t, of sigma(s,t|v)/sigma(s,t) (halved for undirected graphs
+ * when halve_undirected is set, as for the other calls).  Every node of Ssrc and Sdst is made a
+ * singleton part (the expansion of Sec. 5), the sources are Ssrc, and the indicator of Eq. 7 /
+ * Eq. 12 / Eq. 13 marks Sdst.  Each list must be distinct and in [0,n); the lists may overlap.
+ * An empty list gives all zeros. */
+int bcpp_brandes_pp_st(bcpp_ctx *ctx, const bcpp_graph *g, const int32_t *Ssrc, int32_t nsrc,
+                       const int32_t *Sdst, int32_t ndst, const int32_t *part, int32_t k,
+                       const bcpp_opts *opts, double *bc_out, bcpp_stats *stats);
+
+/* Brandes++All (Sec. 5, Alg. 3): full betweenness (all ordered pairs, halved for undirected
+ * graphs by default) as the sum over every ordered pair of parts (i, j) of the step above with
+ * S_sc = P_i and S_dest = P_j (k^2 skeleton passes).  Exact: equals bcpp_brandes with S = V.
+ * stats->skel_edges receives the number of (i, j) passes run. */
+int bcpp_brandes_pp_all(bcpp_ctx *ctx, const bcpp_graph *g, const int32_t *part, int32_t k,
+                        const bcpp_opts *opts, double *bc_out, bcpp_stats *stats);
 
 /* Full betweenness (S = V of each graph) of num_graphs independent undirected graphs in one
  * launch.  `arena` is their disjoint union as one CSR (global node ids); graph g owns the

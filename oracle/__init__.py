@@ -50,7 +50,9 @@ def _load():
             lib.orc_brandes_pp.argtypes = [i32, i64, P, P, P, i32, P, i32, i32, P, i32, i32, P, P, P]
             lib.orc_skeleton.argtypes = [i32, i64, P, P, P, i32, P, i32, P, i32, P, P, i64, P, P, P, P, P, P]
             lib.orc_distance_sum.argtypes = [i32, i64, P, P, i32, P, i32, P]
-            for f in (lib.orc_sssp, lib.orc_brandes, lib.orc_brandes_pp, lib.orc_skeleton, lib.orc_distance_sum):
+            lib.orc_brandes_st.argtypes = [i32, i64, P, P, P, i32, P, i32, P, i32, i32, P, P]
+            for f in (lib.orc_sssp, lib.orc_brandes, lib.orc_brandes_pp, lib.orc_skeleton, lib.orc_distance_sum,
+                      lib.orc_brandes_st):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -161,3 +163,19 @@ def distance_sum(g, sources) -> int:
     _check(lib.orc_distance_sum(g.n, g.m, _ptr(eu), _ptr(ev), int(g.directed), _ptr(src), int(src.shape[0]),
                                 _ptr(out)), "distance_sum")
     return int(out[0])
+
+
+def brandes_st(g, src, dst, halve: bool | None = None):
+    """Plain Brandes for source set `src` and destination set `dst`: sum over s in src, t in dst,
+    s != t, of sigma(s,t|v)/sigma(s,t).  Returns (bc, overflow)."""
+    lib = _load()
+    eu, ev, ew = _edges(g)
+    a = np.ascontiguousarray(src, np.int32)
+    b = np.ascontiguousarray(dst, np.int32)
+    if halve is None:
+        halve = not g.directed
+    bc = np.empty(g.n, np.float64)
+    ovf = np.zeros(1, np.uint32)
+    _check(lib.orc_brandes_st(g.n, g.m, _ptr(eu), _ptr(ev), _ptr(ew), int(g.directed), _ptr(a), int(a.shape[0]),
+                              _ptr(b), int(b.shape[0]), int(bool(halve)), _ptr(bc), _ptr(ovf)), "brandes_st")
+    return bc, bool(ovf[0])

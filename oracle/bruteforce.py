@@ -107,3 +107,26 @@ def betweenness(g, S=None, halve=None):
     if halve:
         bc = [x / 2 for x in bc]
     return bc
+
+
+def betweenness_st(g, src, dst, halve=None):
+    """Exact sum over s in src, t in dst, s != t, of (#shortest s-t paths through v) / (#shortest
+    s-t paths), as Fractions; halved for undirected graphs by default."""
+    if halve is None:
+        halve = not g.directed
+    sset, tset = set(int(x) for x in src), set(int(x) for x in dst)
+    sp = shortest_paths(g)
+    bc = [Fraction(0)] * g.n
+    for (s, t), paths in sp.items():
+        if s not in sset or t not in tset:
+            continue
+        through = [0] * g.n
+        for p in paths:
+            for v in p[1:-1]:
+                through[v] += 1
+        for v in range(g.n):
+            if through[v]:
+                bc[v] += Fraction(through[v], len(paths))
+    if halve:
+        bc = [x / 2 for x in bc]
+    return bc

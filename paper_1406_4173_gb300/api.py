@@ -38,7 +38,8 @@ class c_graph(ctypes.Structure):
 class c_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("halve_undirected", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("validate", ctypes.c_int32), ("host_buffers", ctypes.c_int32),
-                ("order_sources", ctypes.c_int32), ("shard_index", ctypes.c_int32), ("shard_count", ctypes.c_int32)]
+                ("order_sources", ctypes.c_int32), ("cluster", ctypes.c_int32), ("shard_index", ctypes.c_int32),
+                ("shard_count", ctypes.c_int32)]
 
 
 class c_stats(ctypes.Structure):
@@ -54,7 +55,7 @@ class c_stats(ctypes.Structure):
 
 EXPORTS = ["bcpp_default_opts", "bcpp_strerror", "bcpp_create", "bcpp_destroy", "bcpp_workspace_bytes",
            "bcpp_csr_build", "bcpp_csr_validate", "bcpp_brandes", "bcpp_brandes_pp", "bcpp_brandes_batched",
-           "bcpp_sssp", "bcpp_skeleton", "bcpp_brandes_noalloc"]
+           "bcpp_sssp", "bcpp_skeleton", "bcpp_brandes_noalloc", "bcpp_brandes_pp_st", "bcpp_brandes_pp_all"]
 
 _lib = None
 _lock = threading.Lock()
@@ -88,6 +89,8 @@ def load_library(path: str | None = None):
             "bcpp_skeleton": (ctypes.c_int, [P, G, P, i32, P, i32, P, ctypes.POINTER(i32), i64, P, P, P, P,
                                              ctypes.POINTER(i64), O]),
             "bcpp_brandes_noalloc": (ctypes.c_int, [G, P, i32, i32, P, P]),
+            "bcpp_brandes_pp_st": (ctypes.c_int, [P, G, P, i32, P, i32, P, i32, O, P, ST]),
+            "bcpp_brandes_pp_all": (ctypes.c_int, [P, G, P, i32, O, P, ST]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -175,7 +178,7 @@ class Graph:
 
 
 def _opts(precision="fp64", halve=True, ctas_per_sm=0, host=False, order_sources=True, shard=None,
-          batch=0) -> c_opts:
+          batch=0, cluster=0) -> c_opts:
     o = c_opts()
     load_library().bcpp_default_opts(ctypes.byref(o))
     o.precision = {"fp64": BCPP_FP64, "fp32": BCPP_FP32_DELTA, "fp32_delta": BCPP_FP32_DELTA}[precision]
@@ -186,6 +189,7 @@ def _opts(precision="fp64", halve=True, ctas_per_sm=0, host=False, order_sources
     if shard is not None:
         o.shard_index, o.shard_count = int(shard[0]), int(shard[1])
     o.batch = int(batch)
+    o.cluster = int(cluster)
     return o
 
 
@@ -236,7 +240,7 @@ def csr_validate(G: Graph, ctx: Context | None = None) -> None:
 # ----------------------------------------------------------------------------- betweenness
 def brandes(G: Graph, S=None, precision: str = "fp64", halve: bool = True, ctx: Context | None = None,
             ctas_per_sm: int = 0, out=None, stats: bool = False, allow_overflow: bool = False, shard=None,
-            batch: int = 0, order_sources: bool = True):
+            batch: int = 0, order_sources: bool = True, cluster: int = 0):
     """Plain Brandes, target set S (None = all nodes).  Returns a float64 device tensor [n]
     (and the stats dict when stats=True).  shard=(index, count) computes one shard's partial
     sum over the sources (the shards add up to the full result)."""
@@ -248,7 +252,8 @@ def brandes(G: Graph, S=None, precision: str = "fp64", halve: bool = True, ctx: 
     bc = out if out is not None else torch.empty(G.n, dtype=torch.float64, device=dev)
     st = c_stats()
     cg = G.c()
-    o = _opts(precision, halve, ctas_per_sm, shard=shard, batch=batch, order_sources=order_sources)
+    o = _opts(precision, halve, ctas_per_sm, shard=shard, batch=batch, order_sources=order_sources,
+              cluster=cluster)
     rc = load_library().bcpp_brandes(ctx.handle, ctypes.byref(cg), None if nS == 0 else St.data_ptr(), nS,
                                      ctypes.byref(o), bc.data_ptr(), ctypes.byref(st))
     _check(rc, allow_overflow)
@@ -257,7 +262,7 @@ def brandes(G: Graph, S=None, precision: str = "fp64", halve: bool = True, ctx: 
 
 def brandes_pp(G: Graph, S, part, k: int | None = None, precision: str = "fp64", halve: bool = True,
                ctx: Context | None = None, ctas_per_sm: int = 0, order_sources: bool = True, out=None,
-               stats: bool = False, allow_overflow: bool = False, shard=None, batch: int = 0):
+               stats: bool = False, allow_overflow: bool = False, shard=None, batch: int = 0, cluster: int = 0):
     """Brandes++ (Build_SK, Brandes_SK, Centrality) for target set S (None = all nodes) and
     node partition `part` with values in [0, k)."""
     torch = _torch()
@@ -271,9 +276,50 @@ def brandes_pp(G: Graph, S, part, k: int | None = None, precision: str = "fp64",
     bc = out if out is not None else torch.empty(G.n, dtype=torch.float64, device=dev)
     st = c_stats()
     cg = G.c()
-    o = _opts(precision, halve, ctas_per_sm, order_sources=order_sources, shard=shard, batch=batch)
+    o = _opts(precision, halve, ctas_per_sm, order_sources=order_sources, shard=shard, batch=batch, cluster=cluster)
     rc = load_library().bcpp_brandes_pp(ctx.handle, ctypes.byref(cg), None if nS == 0 else St.data_ptr(), nS,
                                         pt.data_ptr(), int(k), ctypes.byref(o), bc.data_ptr(), ctypes.byref(st))
+    _check(rc, allow_overflow)
+    return (bc, st.as_dict()) if stats else bc
+
+
+def brandes_pp_st(G: Graph, Ssrc, Sdst, part, k: int | None = None, precision: str = "fp64", halve: bool = True,
+                  ctx: Context | None = None, out=None, stats: bool = False, allow_overflow: bool = False):
+    """Brandes++ with separate source and destination sets (Alg. 3's Brandes_SK(G_sk, S_sc, S_dest)
+    plus Centrality): sum over s in Ssrc, t in Sdst, s != t."""
+    torch = _torch()
+    ctx = ctx or default_context()
+    dev = G.row_ptr.device
+    a, b = _dev_i32(Ssrc, dev), _dev_i32(Sdst, dev)
+    pt = _dev_i32(part, dev)
+    if k is None:
+        k = int(pt.max().item()) + 1 if pt.numel() else 0
+    bc = out if out is not None else torch.empty(G.n, dtype=torch.float64, device=dev)
+    st = c_stats()
+    cg = G.c()
+    o = _opts(precision, halve)
+    rc = load_library().bcpp_brandes_pp_st(ctx.handle, ctypes.byref(cg), a.data_ptr() if a.numel() else None,
+                                           int(a.numel()), b.data_ptr() if b.numel() else None, int(b.numel()),
+                                           pt.data_ptr(), int(k), ctypes.byref(o), bc.data_ptr(), ctypes.byref(st))
+    _check(rc, allow_overflow)
+    return (bc, st.as_dict()) if stats else bc
+
+
+def brandes_pp_all(G: Graph, part, k: int | None = None, precision: str = "fp64", halve: bool = True,
+                   ctx: Context | None = None, out=None, stats: bool = False, allow_overflow: bool = False):
+    """Brandes++All (Alg. 3): full betweenness as the sum over all ordered pairs of parts."""
+    torch = _torch()
+    ctx = ctx or default_context()
+    dev = G.row_ptr.device
+    pt = _dev_i32(part, dev)
+    if k is None:
+        k = int(pt.max().item()) + 1 if pt.numel() else 0
+    bc = out if out is not None else torch.empty(G.n, dtype=torch.float64, device=dev)
+    st = c_stats()
+    cg = G.c()
+    o = _opts(precision, halve)
+    rc = load_library().bcpp_brandes_pp_all(ctx.handle, ctypes.byref(cg), pt.data_ptr(), int(k), ctypes.byref(o),
+                                            bc.data_ptr(), ctypes.byref(st))
     _check(rc, allow_overflow)
     return (bc, st.as_dict()) if stats else bc
 

@@ -165,14 +165,6 @@ void iota(int32_t* p, int64_t n, cudaStream_t st) {
     iota_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, st>>>(p, n);
 }
 
-__global__ void sort_keys_by_part_kernel(const int32_t* S, int64_t nS, const int32_t* part, uint64_t* keys,
-                                         uint32_t* vals) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nS; i += (int64_t)gridDim.x * blockDim.x) {
-        keys[i] = (uint64_t)part[S[i]];
-        vals[i] = (uint32_t)S[i];
-    }
-}
-
 // highest-degree node (smallest id on ties): max of (degree << 32 | ~id)
 __global__ void hub_kernel(const int64_t* rp, int32_t n, unsigned long long* best) {
     unsigned long long b = 0;
@@ -197,6 +189,32 @@ __global__ void level_keys_kernel(const int32_t* S, int64_t ns, const int32_t* l
 __global__ void part_keys_kernel(const uint32_t* vals, int64_t ns, const int32_t* part, uint64_t* keys) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += (int64_t)gridDim.x * blockDim.x)
         keys[i] = (uint64_t)part[vals[i]];
+}
+
+__global__ void or_flags_kernel(const uint8_t* a, const uint8_t* b, int32_t n, int32_t* f) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        f[i] = (a[i] | b[i]) ? 1 : 0;
+}
+__global__ void compact_kernel(const int32_t* f, const int64_t* pos, int32_t n, int32_t* out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (f[i]) out[pos[i]] = (int32_t)i;
+}
+__global__ void part_flag_kernel(const int32_t* part, int32_t n, int32_t j, uint8_t* flag) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = part[i] == j ? 1 : 0;
+}
+// (sum, comp) += x, Neumaier, element-wise
+__global__ void accumulate_kernel(const double* x, int32_t n, double* sum, double* comp) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = sum[i], c = comp[i];
+        neumaier_add(s, c, x[i]);
+        sum[i] = s;
+        comp[i] = c;
+    }
+}
+__global__ void finish_kernel(const double* sum, const double* comp, int32_t n, double scale, double* out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (sum[i] + comp[i]) * scale;
 }
 
 __global__ void i64_from_i32_kernel(const int32_t* in, int64_t* out, int64_t n) {
@@ -296,6 +314,7 @@ int64_t slot_bytes(int64_t cap_n, int nb, bool fp32, int order_factor = 8, int s
 // CTAs per batch: with fewer batches than resident CTAs (two per SM), 2 or 4 CTAs of a
 // thread-block cluster share each batch so that every SM has work.
 int choose_cluster(const bcpp_ctx* c, int nitems, const bcpp_opts& o) {
+    if (o.cluster == 1 || o.cluster == 2 || o.cluster == 4) return o.cluster;
     const int cps = o.ctas_per_sm > 0 ? o.ctas_per_sm : 2;
     const int64_t target = (int64_t)cps * c->num_sms;
     int cl = 1;
@@ -794,49 +813,21 @@ int build_sk(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS_eff,
 }
 
 // --------------------------------------------------------------------------- Brandes++
-int brandes_pp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, const int32_t* part, int32_t k,
-                   const bcpp_opts& o, double* bc_out, bcpp_stats* st) {
-    CK_RC(check_graph_struct(g));
+// Brandes++ core (Alg. 1 steps, and Alg. 3's Brandes_SK(G_sk, S_sc, S_dest) + Centrality):
+// every node of Ssing becomes a singleton part, the sources are Ssrc (a subset of Ssing), and
+// dflag marks the destinations (the indicator of Eq. 7 / Eq. 12 / Eq. 13).  bc_out receives the
+// partial betweenness of these (source, destination) pairs times `scale`.
+int brandes_pp_core(bcpp_ctx* c, const bcpp_graph* g, uint64_t wmax, const InCsr* Tin, const int32_t* Ssing,
+                    int32_t nsing, const int32_t* Ssrc, int32_t nsrc, const uint8_t* dflag, const int32_t* part,
+                    int32_t k, const bcpp_opts& o, double scale, double* bc_out, bcpp_stats* st, Timer& tb, Timer& tbr,
+                    Timer& tce) {
     const int32_t n = g->n;
-    if (nS < 0 || (nS > 0 && !S) || (n > 0 && (!bc_out || !part)) || k < 0 || (n > 0 && k == 0)) return BCPP_EINVAL;
     const bool fp32 = o.precision == BCPP_FP32_DELTA;
-    Timer tt(c), tb(c), tbr(c), tce(c);
-    tt.start();
-    CK_RC(reset_flags(c));
-    uint64_t wmax = 1;
-    CK_RC(validate_csr(c, g, &wmax));
-    const int64_t ns = nS > 0 ? nS : n;
-    DBuf<uint8_t> in_s(c, n);
-    CK_ALLOC(in_s);
-    DBuf<int32_t> Sall;
-    const int32_t* Sp = S;
-    if (nS > 0) {
-        DBuf<uint32_t> cnt(c, n);
-        CK_ALLOC(cnt);
-        CK_CUDA(cudaMemsetAsync(in_s.p, 0, (size_t)std::max(n, 1), c->stream));
-        CK_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)std::max(n, 1) * 4, c->stream));
-        targets_check(S, nS, n, in_s.p, cnt.p, c->flags, c->stream);
-        c->launches++;
-    } else {
-        CK_CUDA(cudaMemsetAsync(in_s.p, 1, (size_t)std::max(n, 1), c->stream));
-        CK_ALLOC(Sall.alloc(c, n));
-        iota(Sall.p, n, c->stream);
-        c->launches++;
-        Sp = Sall.p;
-    }
-    CK_RC(sync_flags(c));
-    if (c->hflags[FLAG_INVALID]) return BCPP_EINVAL;
-    if (ns < 2 || n == 0) {
-        if (n > 0) CK_CUDA(cudaMemsetAsync(bc_out, 0, (size_t)n * sizeof(double), c->stream));
-        CK_CUDA(cudaStreamSynchronize(c->stream));
-        return BCPP_OK;
-    }
-    InCsr Tin;
-    if (g->directed) CK_RC(build_in_csr(c, g, Tin));
-    // Step 1: Build_SK on P'
+    const int64_t ns = nsrc;
+    // Step 1: Build_SK on P' (every node of Ssing a singleton part)
     tb.start();
     Skeleton K;
-    CK_RC(build_sk(c, g, Sp, (int32_t)ns, part, k, wmax, g->directed ? &Tin : nullptr, o, K));
+    CK_RC(build_sk(c, g, Ssing, nsing, part, k, wmax, Tin, o, K));
     tb.stop();
     // Step 2 + 3: Brandes_SK from every target, Centrality of the non-frontier nodes
     const int32_t N = K.N;
@@ -845,10 +836,10 @@ int brandes_pp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t n
     CK_ALLOC(tsk); CK_ALLOC(tcnt);
     {
         DBuf<int32_t> Sord;
-        const int32_t* Suse = Sp;
+        const int32_t* Suse = Ssrc;
         if (o.order_sources && ns > 2 * LS_LANES) {
-            CK_RC(order_targets(c, g, g->directed ? Tin.rp.p : g->row_ptr, g->directed ? Tin.col.p : g->col,
-                                g->directed ? (g->w ? Tin.w.p : nullptr) : g->w, wmax, Sp, ns, part, k, Sord));
+            CK_RC(order_targets(c, g, g->directed ? Tin->rp.p : g->row_ptr, g->directed ? Tin->col.p : g->col,
+                                g->directed ? (g->w ? Tin->w.p : nullptr) : g->w, wmax, Ssrc, ns, part, k, Sord));
             Suse = Sord.p;
         }
         sk_target_ids(Suse, (int32_t)ns, K.skid.p, tsk.p, tcnt.p, c->stream);
@@ -886,7 +877,7 @@ int brandes_pp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t n
     if (nitems > 0) {
         DBuf<uint8_t> sk_in_s(c, N);
         CK_ALLOC(sk_in_s);
-        sk_gather_flags(N, K.sknode.p, in_s.p, sk_in_s.p, c->stream);
+        sk_gather_flags(N, K.sknode.p, dflag, sk_in_s.p, c->stream);
         c->launches++;
         // skeleton in-arcs for directed graphs
         DBuf<int64_t> irp;
@@ -971,21 +962,205 @@ int brandes_pp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t n
             c->launches++;
         }
     }
-    const bool halve = !g->directed && o.halve_undirected != 0;
-    combine_launch(ws.W.bc_sum, ws.W.bc_cmp, slots_used, n, n, halve ? 0.5 : 1.0, bc_out, c->stream);
+    combine_launch(ws.W.bc_sum, ws.W.bc_cmp, slots_used, n, n, scale, bc_out, c->stream);
     c->launches++;
-    int rc = finish_status(c, st);
-    tt.stop();
     if (st) {
         st->skel_nodes = K.N;
         st->skel_edges = K.edges;
         st->k = K.k_nonempty;
         st->lcs = K.lcs;
         st->table_entries = K.table_entries;
+    }
+    CK_CUDA(cudaGetLastError());
+    return BCPP_OK;
+}
+
+int brandes_pp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, const int32_t* part, int32_t k,
+                   const bcpp_opts& o, double* bc_out, bcpp_stats* st) {
+    CK_RC(check_graph_struct(g));
+    const int32_t n = g->n;
+    if (nS < 0 || (nS > 0 && !S) || (n > 0 && (!bc_out || !part)) || k < 0 || (n > 0 && k == 0)) return BCPP_EINVAL;
+    Timer tt(c);
+    tt.start();
+    CK_RC(reset_flags(c));
+    uint64_t wmax = 1;
+    CK_RC(validate_csr(c, g, &wmax));
+    const int64_t ns = nS > 0 ? nS : n;
+    DBuf<uint8_t> in_s(c, n);
+    CK_ALLOC(in_s);
+    DBuf<int32_t> Sall;
+    const int32_t* Sp = S;
+    if (nS > 0) {
+        DBuf<uint32_t> cnt(c, n);
+        CK_ALLOC(cnt);
+        CK_CUDA(cudaMemsetAsync(in_s.p, 0, (size_t)std::max(n, 1), c->stream));
+        CK_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)std::max(n, 1) * 4, c->stream));
+        targets_check(S, nS, n, in_s.p, cnt.p, c->flags, c->stream);
+        c->launches++;
+    } else {
+        CK_CUDA(cudaMemsetAsync(in_s.p, 1, (size_t)std::max(n, 1), c->stream));
+        CK_ALLOC(Sall.alloc(c, n));
+        iota(Sall.p, n, c->stream);
+        c->launches++;
+        Sp = Sall.p;
+    }
+    CK_RC(sync_flags(c));
+    if (c->hflags[FLAG_INVALID]) return BCPP_EINVAL;
+    if (ns < 2 || n == 0) {
+        if (n > 0) CK_CUDA(cudaMemsetAsync(bc_out, 0, (size_t)n * sizeof(double), c->stream));
+        CK_CUDA(cudaStreamSynchronize(c->stream));
+        return BCPP_OK;
+    }
+    InCsr Tin;
+    if (g->directed) CK_RC(build_in_csr(c, g, Tin));
+    Timer tb(c), tbr(c), tce(c);
+    const bool halve = !g->directed && o.halve_undirected != 0;
+    int rc = brandes_pp_core(c, g, wmax, &Tin, Sp, (int32_t)ns, Sp, (int32_t)ns, in_s.p, part, k, o, halve ? 0.5 : 1.0,
+                             bc_out, st, tb, tbr, tce);
+    if (rc) return rc;
+    rc = finish_status(c, st);
+    tt.stop();
+    if (st) {
         st->ms_build_sk = tb.acc;
         st->ms_brandes_sk = tbr.acc;
         st->ms_centrality = tce.acc;
         st->ms_total = tt.acc;
+    }
+    return rc;
+}
+
+// Brandes++ for separate source and destination sets (Alg. 3's Brandes_SK(G_sk, S_sc, S_dest)
+// followed by Centrality): every node of S_sc and S_dest is a singleton part.
+int brandes_pp_st_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* Ssrc, int32_t nsrc, const int32_t* Sdst,
+                      int32_t ndst, const int32_t* part, int32_t k, const bcpp_opts& o, double* bc_out,
+                      bcpp_stats* st) {
+    CK_RC(check_graph_struct(g));
+    const int32_t n = g->n;
+    if (nsrc < 0 || ndst < 0 || (nsrc > 0 && !Ssrc) || (ndst > 0 && !Sdst) || (n > 0 && (!bc_out || !part)) || k < 0 ||
+        (n > 0 && k == 0))
+        return BCPP_EINVAL;
+    Timer tt(c);
+    tt.start();
+    CK_RC(reset_flags(c));
+    uint64_t wmax = 1;
+    CK_RC(validate_csr(c, g, &wmax));
+    if (nsrc == 0 || ndst == 0 || n == 0) {
+        if (n > 0) CK_CUDA(cudaMemsetAsync(bc_out, 0, (size_t)n * sizeof(double), c->stream));
+        CK_CUDA(cudaStreamSynchronize(c->stream));
+        return BCPP_OK;
+    }
+    DBuf<uint8_t> sflag(c, n), dflag(c, n);
+    DBuf<uint32_t> cnt(c, n);
+    CK_ALLOC(sflag); CK_ALLOC(dflag); CK_ALLOC(cnt);
+    CK_CUDA(cudaMemsetAsync(sflag.p, 0, (size_t)n, c->stream));
+    CK_CUDA(cudaMemsetAsync(dflag.p, 0, (size_t)n, c->stream));
+    CK_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)n * 4, c->stream));
+    targets_check(Ssrc, nsrc, n, sflag.p, cnt.p, c->flags, c->stream);
+    CK_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)n * 4, c->stream));
+    targets_check(Sdst, ndst, n, dflag.p, cnt.p, c->flags, c->stream);
+    c->launches += 2;
+    CK_RC(sync_flags(c));
+    if (c->hflags[FLAG_INVALID]) return BCPP_EINVAL;
+    // singletons: S_sc u S_dest, in node order
+    DBuf<int32_t> f(c, n), uni(c, n);
+    DBuf<int64_t> pos(c, (int64_t)n + 1), tmp(c, scan_tmp_elems((int64_t)n + 1));
+    CK_ALLOC(f); CK_ALLOC(uni); CK_ALLOC(pos); CK_ALLOC(tmp);
+    const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 8192);
+    or_flags_kernel<<<blocks, 256, 0, c->stream>>>(sflag.p, dflag.p, n, f.p);
+    exclusive_scan<int32_t>(f.p, pos.p, n, pos.p + n, tmp.p, c->stream, c->launches);
+    compact_kernel<<<blocks, 256, 0, c->stream>>>(f.p, pos.p, n, uni.p);
+    c->launches += 2;
+    int64_t nuni = 0;
+    CK_RC(to_host(c, &nuni, pos.p + n, 1));
+    InCsr Tin;
+    if (g->directed) CK_RC(build_in_csr(c, g, Tin));
+    Timer tb(c), tbr(c), tce(c);
+    const bool halve = !g->directed && o.halve_undirected != 0;
+    int rc = brandes_pp_core(c, g, wmax, &Tin, uni.p, (int32_t)nuni, Ssrc, nsrc, dflag.p, part, k, o,
+                             halve ? 0.5 : 1.0, bc_out, st, tb, tbr, tce);
+    if (rc) return rc;
+    rc = finish_status(c, st);
+    tt.stop();
+    if (st) {
+        st->ms_build_sk = tb.acc;
+        st->ms_brandes_sk = tbr.acc;
+        st->ms_centrality = tce.acc;
+        st->ms_total = tt.acc;
+    }
+    return rc;
+}
+
+// Brandes++All (Alg. 3): for every ordered pair of parts (i, j), Brandes_SK with S_sc = P_i
+// and S_dest = P_j on the skeleton where both parts are expanded into singletons, then
+// Centrality; C(v) is the sum of the k^2 partial results (Sec. 5).
+int brandes_pp_all_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* part, int32_t k, const bcpp_opts& o,
+                       double* bc_out, bcpp_stats* st) {
+    CK_RC(check_graph_struct(g));
+    const int32_t n = g->n;
+    if ((n > 0 && (!bc_out || !part)) || k < 0 || (n > 0 && k == 0)) return BCPP_EINVAL;
+    Timer tt(c);
+    tt.start();
+    CK_RC(reset_flags(c));
+    uint64_t wmax = 1;
+    CK_RC(validate_csr(c, g, &wmax));
+    if (n == 0) return BCPP_OK;
+    std::vector<int32_t> hp(n);
+    CK_RC(to_host(c, hp.data(), part, n));
+    for (int32_t v = 0; v < n; v++)
+        if (hp[v] < 0 || hp[v] >= k) return BCPP_EINVAL;
+    // nodes grouped by part
+    std::vector<int64_t> off((size_t)k + 1, 0);
+    for (int32_t v = 0; v < n; v++) off[hp[v] + 1]++;
+    for (int32_t i = 0; i < k; i++) off[i + 1] += off[i];
+    std::vector<int32_t> byp(n), fill(off.begin(), off.end() - 1);
+    for (int32_t v = 0; v < n; v++) byp[fill[hp[v]]++] = v;
+    DBuf<int32_t> dbyp(c, n), pair(c, n);
+    DBuf<uint8_t> dflag(c, n);
+    DBuf<double> tmp(c, n), sum(c, n), comp(c, n);
+    CK_ALLOC(dbyp); CK_ALLOC(pair); CK_ALLOC(dflag); CK_ALLOC(tmp); CK_ALLOC(sum); CK_ALLOC(comp);
+    CK_RC(to_dev(c, dbyp.p, byp.data(), n));
+    CK_CUDA(cudaMemsetAsync(sum.p, 0, (size_t)n * sizeof(double), c->stream));
+    CK_CUDA(cudaMemsetAsync(comp.p, 0, (size_t)n * sizeof(double), c->stream));
+    InCsr Tin;
+    if (g->directed) CK_RC(build_in_csr(c, g, Tin));
+    Timer tb(c), tbr(c), tce(c);
+    const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 8192);
+    int64_t calls = 0;
+    for (int32_t j = 0; j < k; j++) {
+        const int32_t nj = (int32_t)(off[j + 1] - off[j]);
+        if (nj == 0) continue;
+        part_flag_kernel<<<blocks, 256, 0, c->stream>>>(part, n, j, dflag.p);
+        c->launches++;
+        for (int32_t i = 0; i < k; i++) {
+            const int32_t ni = (int32_t)(off[i + 1] - off[i]);
+            if (ni == 0 || (i == j && ni < 2)) continue;
+            // singletons: P_i followed by P_j (P_i alone when i == j)
+            CK_CUDA(cudaMemcpyAsync(pair.p, dbyp.p + off[i], (size_t)ni * 4, cudaMemcpyDeviceToDevice, c->stream));
+            int32_t nsing = ni;
+            if (i != j) {
+                CK_CUDA(cudaMemcpyAsync(pair.p + ni, dbyp.p + off[j], (size_t)nj * 4, cudaMemcpyDeviceToDevice,
+                                        c->stream));
+                nsing += nj;
+            }
+            CK_RC(brandes_pp_core(c, g, wmax, &Tin, pair.p, nsing, pair.p, ni, dflag.p, part, k, o, 1.0, tmp.p,
+                                  nullptr, tb, tbr, tce));
+            accumulate_kernel<<<blocks, 256, 0, c->stream>>>(tmp.p, n, sum.p, comp.p);
+            c->launches++;
+            calls++;
+        }
+    }
+    const bool halve = !g->directed && o.halve_undirected != 0;
+    finish_kernel<<<blocks, 256, 0, c->stream>>>(sum.p, comp.p, n, halve ? 0.5 : 1.0, bc_out);
+    c->launches++;
+    int rc = finish_status(c, st);
+    tt.stop();
+    if (st) {
+        st->k = k;
+        st->ms_build_sk = tb.acc;
+        st->ms_brandes_sk = tbr.acc;
+        st->ms_centrality = tce.acc;
+        st->ms_total = tt.acc;
+        st->skel_edges = calls;   // number of (i, j) Brandes_SK runs
     }
     return rc;
 }
@@ -1268,6 +1443,7 @@ void bcpp_default_opts(bcpp_opts* o) {
     o->validate = 1;
     o->host_buffers = 0;
     o->order_sources = 1;
+    o->cluster = 0;
     o->shard_index = 0;
     o->shard_count = 0;
 }
@@ -1378,6 +1554,60 @@ int bcpp_brandes_pp(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t 
             rc = BCPP_ECUDA;
     } else {
         rc = with_capacity_retry(c, [&] { return brandes_pp_dev(c, g, S, nS, part, k, o, bc_out, stats); });
+    }
+    if (stats) stats->kernel_launches = c->launches - l0;
+    return rc;
+}
+
+int bcpp_brandes_pp_st(bcpp_ctx* c, const bcpp_graph* g, const int32_t* Ssrc, int32_t nsrc, const int32_t* Sdst,
+                       int32_t ndst, const int32_t* part, int32_t k, const bcpp_opts* opts, double* bc_out,
+                       bcpp_stats* stats) {
+    if (!c || !g) return BCPP_EINVAL;
+    const bcpp_opts o = opts_or_default(opts);
+    const int64_t l0 = c->launches;
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    int rc;
+    if (o.host_buffers) {
+        StagedGraph sg;
+        DBuf<int32_t> ds, dd, dpart;
+        DBuf<double> dbc;
+        const int32_t *ps = nullptr, *pd = nullptr, *pp = nullptr;
+        rc = stage_graph(c, g, sg);
+        if (!rc) rc = stage_in(c, ds, Ssrc, nsrc, &ps);
+        if (!rc) rc = stage_in(c, dd, Sdst, ndst, &pd);
+        if (!rc) rc = stage_in(c, dpart, part, g->n, &pp);
+        if (!rc && !dbc.alloc(c, g->n)) rc = BCPP_ENOMEM;
+        if (!rc)
+            rc = with_capacity_retry(c, [&] { return brandes_pp_st_dev(c, &sg.g, ps, nsrc, pd, ndst, pp, k, o, dbc.p, stats); });
+        if ((rc == BCPP_OK || rc == BCPP_EOVERFLOW_SIGMA) && g->n > 0 && to_host(c, bc_out, dbc.p, g->n) != BCPP_OK)
+            rc = BCPP_ECUDA;
+    } else {
+        rc = with_capacity_retry(c, [&] { return brandes_pp_st_dev(c, g, Ssrc, nsrc, Sdst, ndst, part, k, o, bc_out, stats); });
+    }
+    if (stats) stats->kernel_launches = c->launches - l0;
+    return rc;
+}
+
+int bcpp_brandes_pp_all(bcpp_ctx* c, const bcpp_graph* g, const int32_t* part, int32_t k, const bcpp_opts* opts,
+                        double* bc_out, bcpp_stats* stats) {
+    if (!c || !g) return BCPP_EINVAL;
+    const bcpp_opts o = opts_or_default(opts);
+    const int64_t l0 = c->launches;
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    int rc;
+    if (o.host_buffers) {
+        StagedGraph sg;
+        DBuf<int32_t> dpart;
+        DBuf<double> dbc;
+        const int32_t* pp = nullptr;
+        rc = stage_graph(c, g, sg);
+        if (!rc) rc = stage_in(c, dpart, part, g->n, &pp);
+        if (!rc && !dbc.alloc(c, g->n)) rc = BCPP_ENOMEM;
+        if (!rc) rc = with_capacity_retry(c, [&] { return brandes_pp_all_dev(c, &sg.g, pp, k, o, dbc.p, stats); });
+        if ((rc == BCPP_OK || rc == BCPP_EOVERFLOW_SIGMA) && g->n > 0 && to_host(c, bc_out, dbc.p, g->n) != BCPP_OK)
+            rc = BCPP_ECUDA;
+    } else {
+        rc = with_capacity_retry(c, [&] { return brandes_pp_all_dev(c, g, part, k, o, bc_out, stats); });
     }
     if (stats) stats->kernel_launches = c->launches - l0;
     return rc;

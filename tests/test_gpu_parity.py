@@ -323,3 +323,29 @@ def test_two_cta_clusters(bc):
     ref_s, _ = oracle.brandes(g, S)
     assert rel_err(bc.brandes(G, S).cpu().numpy(), ref_s) < FP64_TOL
     assert rel_err(bc.brandes_pp(G, S, g.part).cpu().numpy(), ref_s) < FP64_TOL
+
+
+
+# ----------------------------------------------------------------------------- Alg. 3
+@pytest.mark.parametrize("name,g", GRAPHS[:4], ids=IDS[:4])
+def test_brandes_pp_st_equals_oracle(bc, name, g):
+    G = bc.graph_from_edgelist(g)
+    src = gen.sample_targets(g.n, 60, seed=61)
+    dst = gen.sample_targets(g.n, 90, seed=62)
+    ref, _ = oracle.brandes_st(g, src, dst)
+    got = bc.brandes_pp_st(G, src, dst, g.part).cpu().numpy()
+    assert rel_err(got, ref) < FP64_TOL
+
+
+@pytest.mark.parametrize("directed,wmax", [(False, None), (False, 5), (True, 7)])
+def test_brandes_pp_all_equals_brandes(bc, directed, wmax):
+    if directed:
+        g = gen.chung_lu_communities(400, [100] * 4, 2.3, 5.0, 0.85, seed=63, directed=True, wmax=wmax)
+    else:
+        g = gen.planted_partition(400, 5, 0.05, 0.003, seed=64, wmax=wmax)
+    G = bc.graph_from_edgelist(g)
+    ref, _ = oracle.brandes(g)
+    got, st = bc.brandes_pp_all(G, g.part, stats=True)
+    assert rel_err(got.cpu().numpy(), ref) < FP64_TOL
+    k = int(g.part.max()) + 1
+    assert st["skel_edges"] == k * k

@@ -309,3 +309,29 @@ def test_distance_sum_matches_definition():
     n = 40
     ref = sum(abs(i - j) - 1 for i in range(n) for j in range(n) if i != j)
     assert oracle.distance_sum(gen.path(n), np.arange(n, dtype=np.int32)) == ref
+
+
+
+# ----------------------------------------------------------------------------- sources -> destinations (Alg. 3 pairs)
+@pytest.mark.parametrize("name,g", SMALL[::3], ids=[c[0] for c in SMALL[::3]])
+def test_brandes_st_equals_bruteforce(name, g):
+    rng = np.random.default_rng(len(name) + 7)
+    src = np.sort(rng.choice(g.n, size=max(1, g.n // 2), replace=False))
+    dst = np.sort(rng.choice(g.n, size=max(1, g.n // 2), replace=False))
+    ref = [float(x) for x in bf.betweenness_st(g, src, dst)]
+    got, _ = oracle.brandes_st(g, src, dst)
+    assert rel_err(got, ref) < 1e-12
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_pairs_of_parts_sum_to_full_betweenness(seed):
+    """Sec. 5: summing the (P_i -> P_j) pair sets over all ordered pairs of parts gives C."""
+    g = gen.planted_partition(120, 4, 0.12, 0.01, seed=seed, wmax=3)
+    full, _ = oracle.brandes(g, halve=False)
+    tot = np.zeros(g.n)
+    for i in range(4):
+        for j in range(4):
+            Pi, Pj = np.nonzero(g.part == i)[0], np.nonzero(g.part == j)[0]
+            x, _ = oracle.brandes_st(g, Pi, Pj, halve=False)
+            tot += x
+    assert rel_err(tot, full) < 1e-12
