@@ -75,11 +75,12 @@ typedef struct {
     int32_t validate;          /* reserved: the CSR, S and the partition are always checked */
     int32_t host_buffers;      /* 1: array arguments are host pointers (copied in and out) */
     int32_t order_sources;     /* 1 (default): batch the targets in order of their breadth-first level
-                                * from the highest-degree node (Brandes++: by part, then level), so that
-                                * a batch's sources are close; 0: batch S in the given order.  Only the
-                                * summation order changes, not the result. */
-    int32_t cluster;           /* CTAs per source batch: 0 = auto (2 or 4, as a thread-block cluster, when
-                                * batches are fewer than resident CTAs), or 1, 2, 4 (32-source batches) */
+                                * from the highest-degree node (plain Brandes: unit weights only;
+                                * Brandes++: by part, then level), so that a batch's sources are close;
+                                * 0: batch S in the given order.  Only the summation order changes. */
+    int32_t cluster;           /* CTAs per source batch: 0 = auto (4 as a thread-block cluster when there
+                                * are at most half as many batches as resident CTAs, 2 when fewer than
+                                * resident CTAs, else 1), or 1, 2, 4 (32-source batches) */
     int32_t shard_index;       /* with shard_count > 1: use only this shard's targets as sources */
     int32_t shard_count;       /* 0 or 1: every target is a source.  Otherwise the targets, in the order
                                 * used for batching, are split into shard_count contiguous shards

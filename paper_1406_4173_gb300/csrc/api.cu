@@ -313,13 +313,14 @@ int64_t slot_bytes(int64_t cap_n, int nb, bool fp32, int order_factor = 8, int s
 
 // CTAs per batch: with fewer batches than resident CTAs (two per SM), 2 or 4 CTAs of a
 // thread-block cluster share each batch so that every SM has work.
+// (Measured on GB300: with 63 or 128 batches, 4-CTA clusters beat 2-CTA ones.)
 int choose_cluster(const bcpp_ctx* c, int nitems, const bcpp_opts& o) {
     if (o.cluster == 1 || o.cluster == 2 || o.cluster == 4) return o.cluster;
     const int cps = o.ctas_per_sm > 0 ? o.ctas_per_sm : 2;
-    const int64_t target = (int64_t)cps * c->num_sms;
-    int cl = 1;
-    while (cl < 4 && (int64_t)nitems * cl * 2 <= target) cl *= 2;
-    return cl;
+    const int64_t resident = (int64_t)cps * c->num_sms;
+    if (2 * (int64_t)nitems <= resident) return 4;
+    if ((int64_t)nitems < resident) return 2;
+    return 1;
 }
 
 // Choose how many slots (batches in flight, cl CTAs each) to run, within the memory budget.
@@ -536,7 +537,7 @@ int brandes_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, 
     InCsr T;
     if (g->directed) CK_RC(build_in_csr(c, g, T));
     DBuf<int32_t> ordered;
-    if (o.order_sources && ns > 2 * LS_LANES) {
+    if (o.order_sources && ns > 2 * LS_LANES && !g->w) {   // measured to help on unit weights only
         CK_RC(order_targets(c, g, g->directed ? T.rp.p : g->row_ptr, g->directed ? T.col.p : g->col,
                             g->directed ? (g->w ? T.w.p : nullptr) : g->w, wmax, srcs, ns, nullptr, 0, ordered));
         srcs = ordered.p;
