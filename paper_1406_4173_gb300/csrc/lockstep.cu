@@ -111,17 +111,12 @@ __device__ __forceinline__ void arc_group(int32_t mv, int32_t mw, uint64_t mm, i
 template <int UNROLL, int SPL, bool WEIGHTED, bool MULT, class F>
 __device__ __forceinline__ void for_arc_groups(const int32_t* __restrict__ col, const int32_t* __restrict__ w,
                                                const uint64_t* __restrict__ mu, int64_t a0, int32_t deg,
-                                               const int32_t* dl0, int lane, F&& f, bool pre = false,
-                                               int32_t pre_v = 0, int32_t pre_w = 1) {
+                                               const int32_t* dl0, int lane, F&& f) {
     for (int32_t c0 = 0; c0 < deg; c0 += 32) {
         const int cnt = min(32, deg - c0);
         int32_t mv = 0, mw = 1;
         uint64_t mm = 1;
-        if (c0 == 0 && pre) {             // first 32 heads (and weights) already requested
-            mv = pre_v;
-            mw = pre_w;
-            if (MULT && lane < cnt) mm = __ldg(mu + a0 + lane);
-        } else if (lane < cnt) {
+        if (lane < cnt) {
             mv = __ldg(col + a0 + c0 + lane);
             if (WEIGHTED) mw = __ldg(w + a0 + c0 + lane);
             if (MULT) mm = __ldg(mu + a0 + c0 + lane);
@@ -156,33 +151,6 @@ __device__ __forceinline__ LsEnt load_entry(const LsEnt* order, int e, int end) 
     LsEnt z;
     z.u = -1; z.deg = 0; z.a0 = 0;
     return z;
-}
-
-// An entry whose node row (distances of the batch's sources) and first 32 out-arc heads have
-// already been requested, so that a warp starts on it without a dependent round trip.
-template <int SPL>
-struct Ahead {
-    LsEnt ent;
-    int32_t du[SPL];
-    int32_t mv, mw;
-};
-
-template <int SPL, bool WEIGHTED>
-__device__ __forceinline__ void request(Ahead<SPL>& a, const LsEnt& ent, bool valid, const int32_t* dl0,
-                                        const int32_t* __restrict__ col, const int32_t* __restrict__ w, int lane) {
-    constexpr int SH = SPL == 1 ? 5 : 6;
-    a.ent = ent;
-    a.mv = 0;
-    a.mw = 1;
-#pragma unroll
-    for (int s = 0; s < SPL; s++) a.du[s] = DINF;
-    if (valid) {
-        ld_row<SPL>(dl0 + ((uint32_t)ent.u << SH), a.du);
-        if (lane < min(32, ent.deg)) {
-            a.mv = __ldg(col + ent.a0 + lane);
-            if (WEIGHTED) a.mw = __ldg(w + ent.a0 + lane);
-        }
-    }
 }
 
 template <typename DT, int SPL, int CL, bool FUSED, bool WEIGHTED, bool MULT>
@@ -328,23 +296,14 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
             }
             sync();
             // settle the nodes of step D
-            // two-deep pipeline: entry i is processed while entry i+1's row and heads and entry
-            // i+2's record are in flight
             int e = fetch_entry(&ctl->next, lane);
-            Ahead<SPL> ah;
-            request<SPL, WEIGHTED>(ah, load_entry(order, e, end), e < end, dl0, A.col, A.w, lane);
-            int e1 = fetch_entry(&ctl->next, lane);
-            LsEnt ent1 = load_entry(order, e1, end);
+            LsEnt cur = load_entry(order, e, end);
             while (e < end) {
-                const LsEnt cur = ah.ent;
-                int32_t du[SPL];
-#pragma unroll
-                for (int s = 0; s < SPL; s++) du[s] = ah.du[s];
-                const int32_t pre_v = ah.mv, pre_w = ah.mw;
-                request<SPL, WEIGHTED>(ah, ent1, e1 < end, dl0, A.col, A.w, lane);
                 const int e2 = fetch_entry(&ctl->next, lane);
-                const LsEnt ent2 = load_entry(order, e2, end);
+                const LsEnt nxt = load_entry(order, e2, end);
                 const int u = cur.u;
+                int32_t du[SPL];
+                ld_row<SPL>(dl0 + ((uint32_t)u << SH), du);
                 bool act[SPL], pull[SPL], any = false;
 #pragma unroll
                 for (int s = 0; s < SPL; s++) {
@@ -418,7 +377,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                                 const int32_t (*dv)[SPL], int left) {
                                 pull_group(tag, vv, ww, mk, dv, left);
                                 relax_group(tag, vv, ww, dv, left);
-                            }, true, pre_v, pre_w);
+                            });
                     } else {
                         if (D > 0) {
                             const int64_t i0 = __ldg(irp + u);
@@ -429,17 +388,15 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                         }
                         for_arc_groups<UNROLL, SPL, WEIGHTED, false>(A.col, A.w, nullptr, cur.a0, cur.deg, dl0, lane,
                             [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t*,
-                                const int32_t (*dv)[SPL], int left) { relax_group(tag, vv, ww, dv, left); },
-                            true, pre_v, pre_w);
+                                const int32_t (*dv)[SPL], int left) { relax_group(tag, vv, ww, dv, left); });
                     }
 #pragma unroll
                     for (int s = 0; s < SPL; s++)
                         if (pull[s]) sl0[((uint32_t)u << SH) + s] = acc[s];
                     if (__any_sync(FULL, ovf) && lane == 0) atomicOr(&P.flags[FLAG_SIGMA_OVF], 1u);
                 }
-                e = e1;
-                e1 = e2;
-                ent1 = ent2;
+                e = e2;
+                cur = nxt;
             }
             sync();
             if (leader) { ctl->nsteps++; ctl->D = D + 1; }
@@ -468,20 +425,13 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                 const int32_t D = step_d[st];
                 const int end = (st + 1 < nsteps) ? step_beg[st + 1] : olen;
                 int e = fetch_entry(&ctl->next, lane);
-                Ahead<SPL> ah;
-                request<SPL, WEIGHTED>(ah, load_entry(order, e, end), e < end, dl0, A.col, A.w, lane);
-                int e1 = fetch_entry(&ctl->next, lane);
-                LsEnt ent1 = load_entry(order, e1, end);
+                LsEnt cur = load_entry(order, e, end);
                 while (e < end) {
-                    const LsEnt cur = ah.ent;
-                    int32_t du[SPL];
-#pragma unroll
-                    for (int s = 0; s < SPL; s++) du[s] = ah.du[s];
-                    const int32_t pre_v = ah.mv, pre_w = ah.mw;
-                    request<SPL, WEIGHTED>(ah, ent1, e1 < end, dl0, A.col, A.w, lane);
                     const int e2 = fetch_entry(&ctl->next, lane);
-                    const LsEnt ent2 = load_entry(order, e2, end);
+                    const LsEnt nxt = load_entry(order, e2, end);
                     const int u = cur.u;
+                    int32_t du[SPL];
+                    ld_row<SPL>(dl0 + ((uint32_t)u << SH), du);
                     bool act[SPL], any = false;
 #pragma unroll
                     for (int s = 0; s < SPL; s++) {
@@ -515,7 +465,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                                 for (int k = 0; k < U; k++)
 #pragma unroll
                                     for (int s = 0; s < SPL; s++) acc[s] += MULT ? (DT)mk[k] * cv[k][s] : cv[k][s];
-                            }, true, pre_v, pre_w);
+                            });
                         double contrib = 0.0;
                         uint64_t su[SPL];
                         ld_row<SPL>(sl0 + ((uint32_t)u << SH), su);
@@ -537,9 +487,8 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                             atomicAdd(&bcs[ix], tot);
                         }
                     }
-                    e = e1;
-                    e1 = e2;
-                    ent1 = ent2;
+                    e = e2;
+                    cur = nxt;
                 }
                 sync();
             }
