@@ -316,7 +316,7 @@ int64_t slot_bytes(int64_t cap_n, int nb, bool fp32, int order_factor = 8, int s
 // (Measured on GB300: with 63 or 128 batches, 4-CTA clusters beat 2-CTA ones.)
 int choose_cluster(const bcpp_ctx* c, int nitems, const bcpp_opts& o) {
     if (o.cluster == 1 || o.cluster == 2 || o.cluster == 4) return o.cluster;
-    const int cps = o.ctas_per_sm > 0 ? o.ctas_per_sm : 2;
+    const int cps = o.ctas_per_sm > 0 ? o.ctas_per_sm : LS_MIN_CTAS;
     const int64_t resident = (int64_t)cps * c->num_sms;
     if (2 * (int64_t)nitems <= resident) return 4;
     if ((int64_t)nitems < resident) return 2;
@@ -325,7 +325,7 @@ int choose_cluster(const bcpp_ctx* c, int nitems, const bcpp_opts& o) {
 
 // Choose how many slots (batches in flight, cl CTAs each) to run, within the memory budget.
 int choose_slots(bcpp_ctx* c, int nitems, int ctas_per_sm, int64_t per_slot, int64_t per_slot_bc, int cl = 1) {
-    int cps = ctas_per_sm > 0 ? ctas_per_sm : 2;
+    int cps = ctas_per_sm > 0 ? ctas_per_sm : LS_MIN_CTAS;
     int slots = std::min<int64_t>(nitems, std::max<int64_t>(1, (int64_t)cps * c->num_sms / cl));
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);

@@ -154,7 +154,7 @@ __device__ __forceinline__ LsEnt load_entry(const LsEnt* order, int e, int end) 
 }
 
 template <typename DT, int SPL, int CL, bool FUSED, bool WEIGHTED, bool MULT>
-__global__ void __launch_bounds__(LS_THREADS, 2)
+__global__ void __launch_bounds__(LS_THREADS, LS_MIN_CTAS)
 ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __restrict__ items, int nitems) {
     // CL CTAs (a thread-block cluster when CL > 1) share one batch and one slot
     __shared__ LsCtl s_ctl;
@@ -178,7 +178,10 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
     constexpr int ROW = 32 * SPL;                 // sources per node row
     constexpr int SH = SPL == 1 ? 5 : 6;          // log2(ROW)
     // arcs handled per group (bounded by the 64 registers of two resident 512-thread CTAs)
-    constexpr int UNROLL = SPL == 1 ? ((WEIGHTED && FUSED) ? (MULT ? 4 : 6) : (MULT ? 6 : 8))
+#ifndef BCPP_LS_UNROLL
+#define BCPP_LS_UNROLL 8
+#endif
+    constexpr int UNROLL = SPL == 1 ? ((WEIGHTED && FUSED) ? (MULT ? 4 : 6) : (MULT ? 6 : BCPP_LS_UNROLL))
                                     : ((WEIGHTED && FUSED) ? (MULT ? 2 : 3) : (MULT ? 3 : 4));
 
     int32_t* d = W.d + (int64_t)slot * W.cap_n * ROW;

@@ -22,7 +22,11 @@
 namespace bcpp {
 
 constexpr int LS_LANES = 32;
-constexpr int LS_THREADS = 512;
+#ifndef BCPP_LS_THREADS
+#define BCPP_LS_THREADS 512
+#endif
+constexpr int LS_THREADS = BCPP_LS_THREADS;                 // threads per CTA
+constexpr int LS_MIN_CTAS = 1024 / LS_THREADS;              // resident CTAs per SM (64 registers)
 
 enum LsMode : int { LS_BRANDES = 0, LS_SKEL = 1, LS_TABLE = 2, LS_SSSP = 3 };
 
