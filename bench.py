@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the cpu_baseline leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="skip the captured-plan (CUDA graph) measurement")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner")
     return ap.parse_args()
 
 
@@ -361,6 +363,36 @@ def _run_single(args, bc, gen, g, S, ctx, flush, dev, ws, rank):
             "max_rel_err_fp32_vs_fp64": _rel(got32, ref64)}
     fp32["speedup_fp32_over_fp64_plain"] = fp32["plain_fp64_ms"] / fp32["plain_ms"]
 
+    # captured plans (CUDA graphs): plain Brandes replays the whole evaluation; the Brandes++
+    # plan replays Brandes_SK + Centrality + combine on the skeleton built at plan creation
+    graph = None
+    if not args.no_graph:
+        pl = bc.plan_brandes(G, Sarg, precision=prec, ctx=ctx)
+        pp_plan = bc.plan_brandes_pp(G, Sarg, part, precision=prec, ctx=ctx)
+        try:
+            tpl, tpp, kpl, kpp = [], [], 0, 0
+            for _ in range(2):
+                flush.fill_(1)
+                xg, sg1 = pl.launch(stats=True)
+                flush.fill_(1)
+                xq, sg2 = pp_plan.launch(stats=True)
+                tpl.append(sg1["ms_total"])
+                tpp.append(sg2["ms_total"])
+                kpl, kpp = sg1["kernel_launches"], sg2["kernel_launches"]
+            graph = {"plain_ms": min(tpl), "pp_per_source_ms": min(tpp),
+                     "kernels_per_replay": {"plain": kpl, "brandes_pp": kpp},
+                     "max_rel_err_vs_direct": max(_rel(xg.cpu().numpy(), a), _rel(xq.cpu().numpy(), a)),
+                     "note": "Brandes++ replay excludes Build_SK (run once at plan creation)"}
+        finally:
+            pl.close()
+            pp_plan.close()
+
+    # launch-shape autotuner on a sample of the sources
+    tune = None
+    if not args.no_autotune:
+        tuned, times = bc.autotune(G, Sarg, precision=prec, ctx=ctx)
+        tune = {"tuned": tuned, "candidates_ms": {f"batch{b}_cluster{c}": t for (b, c), t in times.items()}}
+
     # roofline of the dominant kernel (lockstep forward+backward of plain Brandes)
     sample = np.linspace(0, n - 1, 32).astype(np.int32)
     dist_s, _ = bc.sssp(G, sample, allow_overflow=True)
@@ -437,6 +469,8 @@ def _run_single(args, bc, gen, g, S, ctx, flush, dev, ws, rank):
         "max_rel_err_pp_vs_plain": pp_vs_plain,
         "rel_err_vs_oracle": err_oracle,
         "fp32_delta": fp32,
+        "cuda_graph": graph,
+        "autotune": tune,
         "wall_s": wall,
         "gpu_launches": launches,
         "roofline": roofline,
@@ -500,6 +534,8 @@ def _run_batched(args, bc, graphs, ctx, flush, dev, ws, rank):
         "plain": {"teps": value / ws, "ms": ms},
         "rel_err_vs_oracle": err_oracle,
         "fp32_delta": fp32,
+        "cuda_graph": graph,
+        "autotune": tune,
         "wall_s": wall, "gpu_launches": launches, "roofline": None, "cpu_baseline": cpu, "e2e": None,
         "clocks": clocks,
     }

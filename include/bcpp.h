@@ -198,6 +198,63 @@ int bcpp_skeleton(bcpp_ctx *ctx, const bcpp_graph *g, const int32_t *S, int32_t 
                   int64_t cap_arcs, int32_t *au, int32_t *av, int32_t *aw, uint64_t *amu,
                   int64_t *n_arcs_out, const bcpp_opts *opts);
 
+/* Autotuner for the launch shape of the shortest-path kernels (the paper has none: the source
+ * batch width and the CTAs per batch are this implementation's knobs).  Runs plain Brandes on
+ * (g, S) once per candidate shape -- 32-source batches on 1, 2 or 4 CTAs (a thread-block
+ * cluster), and 64-source batches on 1 CTA, in this order -- over the same bounded sample of
+ * the sources (the first of R source shards, R = max(1, batches / (2 x resident CTAs)), so the
+ * sample fills the GPU at least twice over, or is all of S), and writes into *tuned a copy of
+ * *opts (NULL: defaults) whose `batch` and `cluster` are the fastest candidate's.  ms_out
+ * (host, may be NULL) receives the candidates' kernel times in milliseconds
+ * [BCPP_AUTOTUNE_CANDIDATES] (-1 when |S| < 2).  The tuned options apply to bcpp_brandes,
+ * bcpp_brandes_pp and the plans on the same graph.  Errors as for bcpp_brandes;
+ * opts->host_buffers must be 0. */
+#define BCPP_AUTOTUNE_CANDIDATES 4
+int bcpp_autotune(bcpp_ctx *ctx, const bcpp_graph *g, const int32_t *S, int32_t nS,
+                  const bcpp_opts *opts, bcpp_opts *tuned, float *ms_out);
+
+/* ---------------------------------------------------------------------------------------
+ * Captured plans (CUDA graphs).  The paper has no counterpart: this is the repeated-evaluation
+ * form of bcpp_brandes and bcpp_brandes_pp for a service that evaluates the same graph many
+ * times.  Creating a plan takes every host decision of one evaluation once (input checks,
+ * sizes, source batches and their order, workspace; for Brandes++ all of Build_SK) and records
+ * the evaluation's device work as a CUDA graph; bcpp_plan_launch replays it with one graph
+ * launch instead of one launch per kernel and no host decision in between.
+ *
+ * A plan keeps the pointers it was created with (g's arrays, S, part, bc_out) and the workspace
+ * it sized (taken from the context's pool until bcpp_plan_destroy).  Destroy every plan before
+ * its context.  opts->host_buffers must be 0 (device pointers only).
+ * --------------------------------------------------------------------------------------- */
+typedef struct bcpp_plan bcpp_plan;
+
+/* Plain-Brandes plan: each launch computes what bcpp_brandes(ctx, g, S, nS, opts, bc_out)
+ * computes from the CURRENT contents of g's arrays and of S.  Between launches the caller may
+ * rewrite them (another target set of the same size; another graph with the same n, num_arcs,
+ * directedness and weights present or absent, max weight not above the one at creation).
+ * Every launch first re-checks the graph and S on the device (a separate small graph) and
+ * returns BCPP_EINVAL without computing when they are invalid.  On success *plan receives the
+ * plan; on error *plan = NULL and nothing is held. */
+int bcpp_plan_brandes(bcpp_ctx *ctx, const bcpp_graph *g, const int32_t *S, int32_t nS,
+                      const bcpp_opts *opts, double *bc_out, bcpp_plan **plan);
+
+/* Brandes++ plan: Build_SK (Alg. 1 step 1) runs once at creation; each launch replays
+ * Brandes_SK, Centrality and the combine on that skeleton and writes what bcpp_brandes_pp
+ * would.  g, S and part must not change while the plan lives: the skeleton depends on all
+ * three (a changed input needs a new plan). */
+int bcpp_plan_brandes_pp(bcpp_ctx *ctx, const bcpp_graph *g, const int32_t *S, int32_t nS,
+                         const int32_t *part, int32_t k, const bcpp_opts *opts, double *bc_out,
+                         bcpp_plan **plan);
+
+/* Replay the plan on the context's stream and wait for it.  Status as for the direct call
+ * (a batch whose settled-entry list outgrows its bound makes the plan rebuild itself once
+ * with the worst-case bound and replay, so BCPP_ECAPACITY is not returned for that).  stats
+ * (may be NULL): ms_total = device time of the launch, kernel_launches = kernels in the
+ * captured graph, and for Brandes++ the skeleton sizes of creation. */
+int bcpp_plan_launch(bcpp_plan *plan, bcpp_stats *stats);
+
+/* Free the plan's graphs and return its workspace to the context.  NULL is ignored. */
+void bcpp_plan_destroy(bcpp_plan *plan);
+
 /* Limits of bcpp_brandes_noalloc (sizes of its static scratch array). */
 #define BCPP_NOALLOC_MAX_NODES 4096
 #define BCPP_NOALLOC_MAX_WEIGHT 15

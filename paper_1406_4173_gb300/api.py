@@ -55,7 +55,8 @@ class c_stats(ctypes.Structure):
 
 EXPORTS = ["bcpp_default_opts", "bcpp_strerror", "bcpp_create", "bcpp_destroy", "bcpp_workspace_bytes",
            "bcpp_csr_build", "bcpp_csr_validate", "bcpp_brandes", "bcpp_brandes_pp", "bcpp_brandes_batched",
-           "bcpp_sssp", "bcpp_skeleton", "bcpp_brandes_noalloc", "bcpp_brandes_pp_st", "bcpp_brandes_pp_all"]
+           "bcpp_sssp", "bcpp_skeleton", "bcpp_brandes_noalloc", "bcpp_brandes_pp_st", "bcpp_brandes_pp_all",
+           "bcpp_plan_brandes", "bcpp_plan_brandes_pp", "bcpp_plan_launch", "bcpp_plan_destroy", "bcpp_autotune"]
 
 _lib = None
 _lock = threading.Lock()
@@ -91,6 +92,11 @@ def load_library(path: str | None = None):
             "bcpp_brandes_noalloc": (ctypes.c_int, [G, P, i32, i32, P, P]),
             "bcpp_brandes_pp_st": (ctypes.c_int, [P, G, P, i32, P, i32, P, i32, O, P, ST]),
             "bcpp_brandes_pp_all": (ctypes.c_int, [P, G, P, i32, O, P, ST]),
+            "bcpp_plan_brandes": (ctypes.c_int, [P, G, P, i32, O, P, ctypes.POINTER(ctypes.c_void_p)]),
+            "bcpp_plan_brandes_pp": (ctypes.c_int, [P, G, P, i32, P, i32, O, P, ctypes.POINTER(ctypes.c_void_p)]),
+            "bcpp_plan_launch": (ctypes.c_int, [P, ST]),
+            "bcpp_plan_destroy": (None, [P]),
+            "bcpp_autotune": (ctypes.c_int, [P, G, P, i32, O, O, ctypes.POINTER(ctypes.c_float)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -330,6 +336,100 @@ class Arena:
     node_ptr: "object"      # int64 device [G+1]
     node_ptr_host: np.ndarray
     graph: Graph
+
+
+AUTOTUNE_CANDIDATES = [(32, 1), (32, 2), (32, 4), (64, 1)]   # (batch, cluster), as in bcpp_autotune
+
+
+def autotune(G: Graph, S=None, precision: str = "fp64", ctx: Context | None = None, order_sources: bool = True):
+    """Time the launch-shape candidates on a sample of the sources (bcpp_autotune).  Returns
+    ({"batch": b, "cluster": c}, {(batch, cluster): ms}) -- pass the first as keyword arguments
+    to brandes / brandes_pp / plan_brandes."""
+    ctx = ctx or default_context()
+    dev = G.row_ptr.device
+    St = _dev_i32(S, dev)
+    nS = 0 if St is None else int(St.numel())
+    o = _opts(precision, True, order_sources=order_sources)
+    t = c_opts()
+    ms = (ctypes.c_float * len(AUTOTUNE_CANDIDATES))()
+    cg = G.c()
+    rc = load_library().bcpp_autotune(ctx.handle, ctypes.byref(cg), None if nS == 0 else St.data_ptr(), nS,
+                                      ctypes.byref(o), ctypes.byref(t), ms)
+    _check(rc, allow_overflow=True)
+    return {"batch": int(t.batch), "cluster": int(t.cluster)}, dict(zip(AUTOTUNE_CANDIDATES, [float(x) for x in ms]))
+
+
+class Plan:
+    """A captured evaluation (bcpp_plan_brandes / bcpp_plan_brandes_pp): ``launch()`` replays its
+    CUDA graph and returns the output tensor.  The plan holds references to the tensors it
+    reads (graph arrays, targets ``S``, partition) and writes (``out``).  For a plain-Brandes
+    plan, ``S`` (and the graph arrays) may be rewritten in place between launches, keeping their
+    sizes; a Brandes++ plan's inputs must not change."""
+
+    def __init__(self, handle, ctx, out, keep):
+        self.handle = handle
+        self.ctx = ctx
+        self.out = out
+        self._keep = keep
+        self.S = keep.get("S")
+
+    def launch(self, stats: bool = False, allow_overflow: bool = False):
+        st = c_stats()
+        rc = load_library().bcpp_plan_launch(self.handle, ctypes.byref(st))
+        _check(rc, allow_overflow)
+        return (self.out, st.as_dict()) if stats else self.out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().bcpp_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan_brandes(G: Graph, S=None, precision: str = "fp64", halve: bool = True, ctx: Context | None = None,
+                 out=None, batch: int = 0, order_sources: bool = True, cluster: int = 0, ctas_per_sm: int = 0,
+                 shard=None) -> Plan:
+    """Capture plain Brandes on (G, S) into a replayable plan (bcpp_plan_brandes)."""
+    torch = _torch()
+    ctx = ctx or default_context()
+    dev = G.row_ptr.device
+    St = _dev_i32(S, dev)
+    nS = 0 if St is None else int(St.numel())
+    bc = out if out is not None else torch.empty(G.n, dtype=torch.float64, device=dev)
+    cg = G.c()
+    o = _opts(precision, halve, ctas_per_sm, shard=shard, batch=batch, order_sources=order_sources, cluster=cluster)
+    h = ctypes.c_void_p()
+    rc = load_library().bcpp_plan_brandes(ctx.handle, ctypes.byref(cg), None if nS == 0 else St.data_ptr(), nS,
+                                          ctypes.byref(o), bc.data_ptr(), ctypes.byref(h))
+    _check(rc)
+    return Plan(h, ctx, bc, {"G": G, "S": St})
+
+
+def plan_brandes_pp(G: Graph, S, part, k: int | None = None, precision: str = "fp64", halve: bool = True,
+                    ctx: Context | None = None, out=None, batch: int = 0, order_sources: bool = True,
+                    cluster: int = 0, ctas_per_sm: int = 0, shard=None) -> Plan:
+    """Build the skeleton and capture Brandes++'s per-source work into a plan (bcpp_plan_brandes_pp)."""
+    torch = _torch()
+    ctx = ctx or default_context()
+    dev = G.row_ptr.device
+    St = _dev_i32(S, dev)
+    nS = 0 if St is None else int(St.numel())
+    pt = _dev_i32(part, dev)
+    if k is None:
+        k = int(pt.max().item()) + 1 if pt.numel() else 0
+    bc = out if out is not None else torch.empty(G.n, dtype=torch.float64, device=dev)
+    cg = G.c()
+    o = _opts(precision, halve, ctas_per_sm, shard=shard, batch=batch, order_sources=order_sources, cluster=cluster)
+    h = ctypes.c_void_p()
+    rc = load_library().bcpp_plan_brandes_pp(ctx.handle, ctypes.byref(cg), None if nS == 0 else St.data_ptr(), nS,
+                                             pt.data_ptr(), int(k), ctypes.byref(o), bc.data_ptr(), ctypes.byref(h))
+    _check(rc)
+    return Plan(h, ctx, bc, {"G": G, "S": St, "part": pt})
 
 
 def build_arena(graphs, ctx: Context | None = None) -> Arena:

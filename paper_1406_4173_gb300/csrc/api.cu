@@ -298,6 +298,8 @@ struct SlotWs {
     DBuf<double> bcs, bcc;
     DBuf<int> counter;
     LsSlots W{};
+    int slots = 0, nb = 0;
+    int64_t rows = 0;
 };
 
 int64_t order_capacity(int64_t cap_n, int order_factor, int spl) {
@@ -338,7 +340,25 @@ int choose_slots(bcpp_ctx* c, int nitems, int ctas_per_sm, int64_t per_slot, int
     return std::max(1, slots);
 }
 
-int alloc_slots(bcpp_ctx* c, SlotWs& S, int slots, int64_t cap_n, int nb, bool fp32, int64_t cap_bc, int spl = 1) {
+// Initial slot state: distances unreached, bucket bitmaps and headers empty, partial sums 0,
+// batch counter 0.  Device work only (no host synchronization), so it can be captured.
+int init_slots(bcpp_ctx* c, SlotWs& S) {
+    const LsSlots& W = S.W;
+    if (W.cap_bc > 0) {
+        CK_CUDA(cudaMemsetAsync(S.bcs.p, 0, (size_t)S.slots * W.cap_bc * sizeof(double), c->stream));
+        CK_CUDA(cudaMemsetAsync(S.bcc.p, 0, (size_t)S.slots * W.cap_bc * sizeof(double), c->stream));
+    }
+    fill_i32(S.d.p, DINF, (int64_t)S.slots * S.rows * 32, c->stream);
+    c->launches++;
+    CK_CUDA(cudaMemsetAsync(S.bm.p, 0, (size_t)S.slots * S.nb * W.bm_words * sizeof(uint32_t), c->stream));
+    CK_CUDA(cudaMemsetAsync(S.bflag.p, 0, (size_t)S.slots * S.nb, c->stream));
+    CK_CUDA(cudaMemsetAsync(S.hdr.p, 0, (size_t)S.slots * 4 * sizeof(int32_t), c->stream));
+    CK_CUDA(cudaMemsetAsync(S.counter.p, 0, sizeof(int), c->stream));
+    return BCPP_OK;
+}
+
+int alloc_slots(bcpp_ctx* c, SlotWs& S, int slots, int64_t cap_n, int nb, bool fp32, int64_t cap_bc, int spl = 1,
+                bool init = true) {
     if (cap_n >= (1 << 25)) return BCPP_EINVAL;   // 32-bit row offsets inside a slot
     const int64_t cap_order = order_capacity(cap_n, c->order_factor, spl);
     const int64_t rows = cap_n * spl;              // rows of 32 values
@@ -357,15 +377,10 @@ int alloc_slots(bcpp_ctx* c, SlotWs& S, int slots, int64_t cap_n, int nb, bool f
     if (cap_bc > 0) {
         CK_ALLOC(S.bcs.alloc(c, (int64_t)slots * cap_bc));
         CK_ALLOC(S.bcc.alloc(c, (int64_t)slots * cap_bc));
-        CK_CUDA(cudaMemsetAsync(S.bcs.p, 0, (size_t)slots * cap_bc * sizeof(double), c->stream));
-        CK_CUDA(cudaMemsetAsync(S.bcc.p, 0, (size_t)slots * cap_bc * sizeof(double), c->stream));
     }
-    fill_i32(S.d.p, DINF, (int64_t)slots * rows * 32, c->stream);
-    c->launches++;
-    CK_CUDA(cudaMemsetAsync(S.bm.p, 0, (size_t)slots * nb * bm_words * sizeof(uint32_t), c->stream));
-    CK_CUDA(cudaMemsetAsync(S.bflag.p, 0, (size_t)slots * nb, c->stream));
-    CK_CUDA(cudaMemsetAsync(S.hdr.p, 0, (size_t)slots * 4 * sizeof(int32_t), c->stream));
-    CK_CUDA(cudaMemsetAsync(S.counter.p, 0, sizeof(int), c->stream));
+    S.slots = slots;
+    S.nb = nb;
+    S.rows = rows;
     LsSlots& W = S.W;
     W.d = S.d.p; W.sg = S.sg.p; W.dl = S.dl.p; W.cap_n = cap_n;
     W.order = S.order.p; W.cap_order = cap_order;
@@ -375,7 +390,7 @@ int alloc_slots(bcpp_ctx* c, SlotWs& S, int slots, int64_t cap_n, int nb, bool f
     W.bc_cmp = cap_bc > 0 ? S.bcc.p : nullptr;
     W.cap_bc = cap_bc;
     W.hdr = S.hdr.p;
-    return BCPP_OK;
+    return init ? init_slots(c, S) : BCPP_OK;
 }
 
 struct Timer {
@@ -414,183 +429,290 @@ struct InCsr {
     DBuf<int64_t> rp;
     DBuf<int32_t> col;
     DBuf<uint32_t> w;
+    DBuf<int64_t> cnt, tmp;
 };
-int build_in_csr(bcpp_ctx* c, const bcpp_graph* g, InCsr& T) {
+int in_csr_alloc(bcpp_ctx* c, const bcpp_graph* g, InCsr& T) {
     const int32_t n = g->n;
     CK_ALLOC(T.rp.alloc(c, (int64_t)n + 1));
     CK_ALLOC(T.col.alloc(c, g->num_arcs));
     if (g->w) CK_ALLOC(T.w.alloc(c, g->num_arcs));
-    DBuf<int64_t> cnt(c, (int64_t)n + 1), tmp(c, scan_tmp_elems((int64_t)n + 1));
-    CK_ALLOC(cnt); CK_ALLOC(tmp);
-    CK_CUDA(cudaMemsetAsync(cnt.p, 0, ((size_t)n + 1) * sizeof(int64_t), c->stream));
-    csr_transpose_count(n, g->row_ptr, g->col, cnt.p, c->stream);
-    exclusive_scan<int64_t>(cnt.p, T.rp.p, (int64_t)n + 1, nullptr, tmp.p, c->stream, c->launches);
-    CK_CUDA(cudaMemcpyAsync(cnt.p, T.rp.p, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, c->stream));
-    csr_transpose_fill(n, g->row_ptr, g->col, g->w, cnt.p, T.col.p, g->w ? T.w.p : nullptr, c->stream);
+    CK_ALLOC(T.cnt.alloc(c, (int64_t)n + 1));
+    CK_ALLOC(T.tmp.alloc(c, scan_tmp_elems((int64_t)n + 1)));
+    return BCPP_OK;
+}
+int in_csr_emit(bcpp_ctx* c, const bcpp_graph* g, InCsr& T) {
+    const int32_t n = g->n;
+    CK_CUDA(cudaMemsetAsync(T.cnt.p, 0, ((size_t)n + 1) * sizeof(int64_t), c->stream));
+    csr_transpose_count(n, g->row_ptr, g->col, T.cnt.p, c->stream);
+    exclusive_scan<int64_t>(T.cnt.p, T.rp.p, (int64_t)n + 1, nullptr, T.tmp.p, c->stream, c->launches);
+    CK_CUDA(cudaMemcpyAsync(T.cnt.p, T.rp.p, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, c->stream));
+    csr_transpose_fill(n, g->row_ptr, g->col, g->w, T.cnt.p, T.col.p, g->w ? T.w.p : nullptr, c->stream);
     c->launches += 2;
     CK_CUDA(cudaGetLastError());
     return BCPP_OK;
+}
+int build_in_csr(bcpp_ctx* c, const bcpp_graph* g, InCsr& T) {
+    CK_RC(in_csr_alloc(c, g, T));
+    return in_csr_emit(c, g, T);
 }
 
 // Order the targets so that every batch holds sources close to each other: stable sort by
 // shortest-path level from the highest-degree node (one single-source run of the lockstep
 // kernel), then, when a partition is given, by part.  Fewer distinct levels per node and batch
 // means fewer settled (node, step) entries.  Only the batching order changes, not the result.
-int order_targets(bcpp_ctx* c, const bcpp_graph* g, const int64_t* irp, const int32_t* icol, const uint32_t* iw,
-                  uint64_t wmax, const int32_t* S, int64_t ns, const int32_t* part, int32_t k, DBuf<int32_t>& out) {
+struct OrderWs {
+    int64_t ns = 0;
+    int32_t n = 0, k = 0;
+    const int32_t* S = nullptr;
+    const int32_t* part = nullptr;
+    const int64_t* rp = nullptr;
+    DBuf<unsigned long long> best;
+    DBuf<int32_t> level, src;
+    DBuf<uint64_t> lsig;
+    DBuf<LsItem> item;
+    DBuf<int64_t> node_off;
+    SlotWs ws;
+    LsArena A{};
+    LsParams P{};
+    DBuf<uint64_t> keys, kb;
+    DBuf<uint32_t> vals, vb;
+    DBuf<int64_t> hist, tmp;
+    DBuf<int32_t> out;        // the ordered targets
+};
+
+__global__ void hub_src_kernel(const unsigned long long* best, int32_t* src) {
+    src[0] = (int32_t)(0xffffffffu - (uint32_t)(best[0] & 0xffffffffull));
+}
+
+int order_prepare(bcpp_ctx* c, const bcpp_graph* g, const int64_t* irp, const int32_t* icol, const uint32_t* iw,
+                  uint64_t wmax, const int32_t* S, int64_t ns, const int32_t* part, int32_t k, OrderWs& w) {
     const int32_t n = g->n;
-    DBuf<unsigned long long> best(c, 1);
-    CK_ALLOC(best);
-    CK_CUDA(cudaMemsetAsync(best.p, 0, sizeof(unsigned long long), c->stream));
-    hub_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, c->stream>>>(g->row_ptr, n, best.p);
-    c->launches++;
-    unsigned long long hb = 0;
-    CK_RC(to_host(c, &hb, best.p, 1));
-    const int32_t hub = (int32_t)(0xffffffffu - (uint32_t)(hb & 0xffffffffull));
-    // levels from the hub
-    DBuf<int32_t> level(c, n), src(c, 1);
-    DBuf<uint64_t> lsig(c, n);
-    DBuf<LsItem> item(c, 1);
-    DBuf<int64_t> node_off(c, 2);
-    CK_ALLOC(level); CK_ALLOC(src); CK_ALLOC(lsig); CK_ALLOC(item); CK_ALLOC(node_off);
+    w.ns = ns; w.n = n; w.k = k; w.S = S; w.part = part; w.rp = g->row_ptr;
+    CK_ALLOC(w.best.alloc(c, 1));
+    CK_ALLOC(w.level.alloc(c, n)); CK_ALLOC(w.src.alloc(c, 1)); CK_ALLOC(w.lsig.alloc(c, n));
+    CK_ALLOC(w.item.alloc(c, 1)); CK_ALLOC(w.node_off.alloc(c, 2));
     const LsItem hi{0, 0, 1, 0};
     const int64_t hoff[2] = {0, n};
-    CK_RC(to_dev(c, item.p, &hi, 1));
-    CK_RC(to_dev(c, node_off.p, hoff, 2));
-    CK_RC(to_dev(c, src.p, &hub, 1));
+    CK_RC(to_dev(c, w.item.p, &hi, 1));
+    CK_RC(to_dev(c, w.node_off.p, hoff, 2));
     const int nb = g->w ? (int)wmax + 1 : 2;
-    SlotWs ws;
-    CK_RC(alloc_slots(c, ws, 1, n, nb, false, 0));
-    LsArena A{};
-    A.rp = g->row_ptr; A.col = g->col; A.w = (const int32_t*)g->w;
-    A.irp = irp; A.icol = icol; A.iw = (const int32_t*)iw;
-    A.node_off = node_off.p;
-    LsParams P{};
-    P.mode = LS_SSSP;
-    P.nb = nb;
-    P.srcs = src.p;
-    P.dbg_d = level.p;
-    P.dbg_s = lsig.p;
-    P.dbg_n = n;
-    P.item_counter = ws.counter.p;
-    P.flags = c->flags;
-    ls_launch(false, !g->directed, A, P, ws.W, item.p, 1, 1, c->stream, 1, 4);   // one batch: 4-CTA cluster
+    CK_RC(alloc_slots(c, w.ws, 1, n, nb, false, 0, 1, false));
+    w.A.rp = g->row_ptr; w.A.col = g->col; w.A.w = (const int32_t*)g->w;
+    w.A.irp = irp; w.A.icol = icol; w.A.iw = (const int32_t*)iw;
+    w.A.node_off = w.node_off.p;
+    w.P.mode = LS_SSSP;
+    w.P.nb = nb;
+    w.P.srcs = w.src.p;
+    w.P.dbg_d = w.level.p;
+    w.P.dbg_s = w.lsig.p;
+    w.P.dbg_n = n;
+    w.P.item_counter = w.ws.counter.p;
+    w.P.flags = c->flags;
+    CK_ALLOC(w.keys.alloc(c, ns)); CK_ALLOC(w.kb.alloc(c, ns));
+    CK_ALLOC(w.vals.alloc(c, ns)); CK_ALLOC(w.vb.alloc(c, ns));
+    CK_ALLOC(w.hist.alloc(c, radix_hist_elems(ns)));
+    CK_ALLOC(w.tmp.alloc(c, scan_tmp_elems(radix_hist_elems(ns))));
+    CK_ALLOC(w.out.alloc(c, ns));
+    return BCPP_OK;
+}
+
+int order_emit(bcpp_ctx* c, OrderWs& w, bool directed) {
+    const int32_t n = w.n;
+    const int64_t ns = w.ns;
+    CK_CUDA(cudaMemsetAsync(w.best.p, 0, sizeof(unsigned long long), c->stream));
+    hub_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, c->stream>>>(w.rp, n, w.best.p);
+    hub_src_kernel<<<1, 1, 0, c->stream>>>(w.best.p, w.src.p);
+    c->launches += 2;
+    CK_RC(init_slots(c, w.ws));
+    ls_launch(false, !directed, w.A, w.P, w.ws.W, w.item.p, 1, 1, c->stream, 1, 4);   // one batch: 4-CTA cluster
     c->launches++;
     // stable sorts: by level, then by part
-    DBuf<uint64_t> keys(c, ns), kb(c, ns);
-    DBuf<uint32_t> vals(c, ns), vb(c, ns);
-    DBuf<int64_t> hist(c, radix_hist_elems(ns)), tmp(c, scan_tmp_elems(radix_hist_elems(ns)));
-    CK_ALLOC(keys); CK_ALLOC(kb); CK_ALLOC(vals); CK_ALLOC(vb); CK_ALLOC(hist); CK_ALLOC(tmp);
     const unsigned blocks = (unsigned)std::min<int64_t>((ns + 255) / 256, 8192);
-    level_keys_kernel<<<blocks, 256, 0, c->stream>>>(S, ns, level.p, keys.p, vals.p);
-    radix_sort_pairs(keys.p, vals.p, kb.p, vb.p, ns, 31, hist.p, tmp.p, c->stream, c->launches);
+    level_keys_kernel<<<blocks, 256, 0, c->stream>>>(w.S, ns, w.level.p, w.keys.p, w.vals.p);
+    radix_sort_pairs(w.keys.p, w.vals.p, w.kb.p, w.vb.p, ns, 31, w.hist.p, w.tmp.p, c->stream, c->launches);
     c->launches++;
-    if (part) {
-        part_keys_kernel<<<blocks, 256, 0, c->stream>>>(vals.p, ns, part, keys.p);
-        radix_sort_pairs(keys.p, vals.p, kb.p, vb.p, ns, bits_for((uint64_t)k), hist.p, tmp.p, c->stream, c->launches);
+    if (w.part) {
+        part_keys_kernel<<<blocks, 256, 0, c->stream>>>(w.vals.p, ns, w.part, w.keys.p);
+        radix_sort_pairs(w.keys.p, w.vals.p, w.kb.p, w.vb.p, ns, bits_for((uint64_t)w.k), w.hist.p, w.tmp.p,
+                         c->stream, c->launches);
         c->launches++;
     }
-    CK_ALLOC(out.alloc(c, ns));
-    CK_CUDA(cudaMemcpyAsync(out.p, vals.p, ns * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
+    CK_CUDA(cudaMemcpyAsync(w.out.p, w.vals.p, ns * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
     CK_CUDA(cudaGetLastError());
     return BCPP_OK;
 }
 
+int order_targets(bcpp_ctx* c, const bcpp_graph* g, const int64_t* irp, const int32_t* icol, const uint32_t* iw,
+                  uint64_t wmax, const int32_t* S, int64_t ns, const int32_t* part, int32_t k, OrderWs& w) {
+    CK_RC(order_prepare(c, g, irp, icol, iw, wmax, S, ns, part, k, w));
+    return order_emit(c, w, g->directed != 0);
+}
+
 // --------------------------------------------------------------------------- plain Brandes
-int brandes_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, const bcpp_opts& o, double* bc_out,
-                bcpp_stats* st) {
+// A plain-Brandes evaluation in two parts: plain_prepare takes every host decision (input
+// checks, sizes, batches, workspace) and plain_emit queues the device work only, so that the
+// same sequence runs directly or is captured once into a CUDA graph and replayed.
+struct PlainRun {
+    bcpp_graph g{};
+    const int32_t* S = nullptr;
+    int32_t nS = 0;
+    bcpp_opts o{};
+    double* bc_out = nullptr;
+    uint64_t wmax = 1;
+    int64_t ns = 0;
+    bool trivial = false;          // |S| < 2 or n == 0: all zeros
+    DBuf<uint8_t> in_s;
+    DBuf<uint32_t> cnt;
+    DBuf<unsigned long long> wmaxd;
+    DBuf<int32_t> all;
+    InCsr T;
+    OrderWs ord;
+    bool ordered = false;
+    DBuf<LsItem> items;
+    DBuf<int64_t> node_off;
+    SlotWs ws;
+    int nitems = 0, slots = 0, spl = 1, cl = 1, nb = 2;
+    LsArena A{};
+    LsParams P{};
+};
+
+__global__ void wmax_bound_kernel(const unsigned long long* wmax, unsigned long long bound, uint32_t* flags) {
+    if (wmax[0] > bound) {
+        atomicOr(&flags[FLAG_INVALID], 1u);
+        atomicCAS(&flags[FLAG_INVALID_WHY], 0u, WHY_WEIGHT_RANGE);
+    }
+}
+
+// The input checks as device work only: flags reset, CSR check with the prepared weight bound,
+// targets check (rebuilds the target indicator).  Used before every replay of a captured plan.
+int plain_emit_checks(bcpp_ctx* c, PlainRun& r) {
+    const bcpp_graph* g = &r.g;
+    const int32_t n = g->n;
+    CK_RC(reset_flags(c));
+    CK_CUDA(cudaMemsetAsync(r.wmaxd.p, 0, sizeof(unsigned long long), c->stream));
+    csr_check(n, g->num_arcs, g->row_ptr, g->col, g->w, g->directed, c->flags, r.wmaxd.p, c->stream, nullptr, 0);
+    wmax_bound_kernel<<<1, 1, 0, c->stream>>>(r.wmaxd.p, (unsigned long long)(g->w ? r.wmax : 1), c->flags);
+    c->launches += 2;
+    if (r.nS > 0) {
+        CK_CUDA(cudaMemsetAsync(r.in_s.p, 0, (size_t)std::max(n, 1), c->stream));
+        CK_CUDA(cudaMemsetAsync(r.cnt.p, 0, (size_t)std::max(n, 1) * 4, c->stream));
+        targets_check(r.S, r.nS, n, r.in_s.p, r.cnt.p, c->flags, c->stream);
+        c->launches++;
+    }
+    CK_CUDA(cudaGetLastError());
+    return BCPP_OK;
+}
+
+int plain_prepare(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, const bcpp_opts& o,
+                  double* bc_out, PlainRun& r) {
     CK_RC(check_graph_struct(g));
     if (nS < 0 || (nS > 0 && !S) || (g->n > 0 && !bc_out)) return BCPP_EINVAL;
     const int32_t n = g->n;
     const bool fp32 = o.precision == BCPP_FP32_DELTA;
-    Timer tt(c);
-    tt.start();
+    r.g = *g; r.S = S; r.nS = nS; r.o = o; r.bc_out = bc_out;
     CK_RC(reset_flags(c));
-    uint64_t wmax = 1;
-    CK_RC(validate_csr(c, g, &wmax));
-    DBuf<uint8_t> in_s;
+    CK_RC(validate_csr(c, g, &r.wmax));
+    CK_ALLOC(r.wmaxd.alloc(c, 1));
     if (nS > 0) {
-        CK_ALLOC(in_s.alloc(c, n));
-        DBuf<uint32_t> cnt(c, n);
-        CK_ALLOC(cnt);
-        CK_CUDA(cudaMemsetAsync(in_s.p, 0, (size_t)std::max(n, 1), c->stream));
-        CK_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)std::max(n, 1) * 4, c->stream));
-        targets_check(S, nS, n, in_s.p, cnt.p, c->flags, c->stream);
+        CK_ALLOC(r.in_s.alloc(c, n));
+        CK_ALLOC(r.cnt.alloc(c, n));
+        CK_CUDA(cudaMemsetAsync(r.in_s.p, 0, (size_t)std::max(n, 1), c->stream));
+        CK_CUDA(cudaMemsetAsync(r.cnt.p, 0, (size_t)std::max(n, 1) * 4, c->stream));
+        targets_check(S, nS, n, r.in_s.p, r.cnt.p, c->flags, c->stream);
         c->launches++;
         CK_RC(sync_flags(c));
         if (c->hflags[FLAG_INVALID]) return BCPP_EINVAL;
     }
-    const int64_t ns = nS > 0 ? nS : n;
-    if (ns < 2 || n == 0) {
-        if (n > 0) CK_CUDA(cudaMemsetAsync(bc_out, 0, (size_t)n * sizeof(double), c->stream));
-        CK_CUDA(cudaStreamSynchronize(c->stream));
+    r.ns = nS > 0 ? nS : n;
+    if (r.ns < 2 || n == 0) {
+        r.trivial = true;
         return BCPP_OK;
     }
-    DBuf<int32_t> all;
     const int32_t* srcs = S;
     if (nS == 0) {
-        CK_ALLOC(all.alloc(c, n));
-        iota(all.p, n, c->stream);
-        c->launches++;
-        srcs = all.p;
+        CK_ALLOC(r.all.alloc(c, n));
+        srcs = r.all.p;
     }
-    InCsr T;
-    if (g->directed) CK_RC(build_in_csr(c, g, T));
-    DBuf<int32_t> ordered;
-    if (o.order_sources && ns > 2 * LS_LANES && !g->w) {   // measured to help on unit weights only
-        CK_RC(order_targets(c, g, g->directed ? T.rp.p : g->row_ptr, g->directed ? T.col.p : g->col,
-                            g->directed ? (g->w ? T.w.p : nullptr) : g->w, wmax, srcs, ns, nullptr, 0, ordered));
-        srcs = ordered.p;
+    if (g->directed) CK_RC(in_csr_alloc(c, g, r.T));
+    if (o.order_sources && r.ns > 2 * LS_LANES && !g->w) {   // measured to help on unit weights only
+        CK_RC(order_prepare(c, g, g->directed ? r.T.rp.p : g->row_ptr, g->directed ? r.T.col.p : g->col,
+                            g->directed ? (g->w ? r.T.w.p : nullptr) : g->w, r.wmax, srcs, r.ns, nullptr, 0, r.ord));
+        r.ordered = true;
+        srcs = r.ord.out.p;
     }
     // items: batches of 32 targets (ordered when requested)
     int64_t s0, s1;
-    shard_sources(o, ns, s0, s1);
-    const int spl = choose_spl(c, s1 - s0, o);
-    std::vector<LsItem> hitems = make_items(0, s0, s1, 32 * spl);
-    const int nitems = (int)hitems.size();
-    if (nitems <= 0) {
-        CK_CUDA(cudaMemsetAsync(bc_out, 0, (size_t)n * sizeof(double), c->stream));
-        CK_CUDA(cudaStreamSynchronize(c->stream));
-        return BCPP_OK;
-    }
-    DBuf<LsItem> items(c, nitems);
-    DBuf<int64_t> node_off(c, 2);
-    CK_ALLOC(items); CK_ALLOC(node_off);
-    CK_RC(to_dev(c, items.p, hitems.data(), nitems));
+    shard_sources(o, r.ns, s0, s1);
+    r.spl = choose_spl(c, s1 - s0, o);
+    std::vector<LsItem> hitems = make_items(0, s0, s1, 32 * r.spl);
+    r.nitems = (int)hitems.size();
+    if (r.nitems <= 0) return BCPP_OK;
+    CK_ALLOC(r.items.alloc(c, r.nitems));
+    CK_ALLOC(r.node_off.alloc(c, 2));
+    CK_RC(to_dev(c, r.items.p, hitems.data(), r.nitems));
     const int64_t hoff[2] = {0, n};
-    CK_RC(to_dev(c, node_off.p, hoff, 2));
-    const int nb = g->w ? (int)wmax + 1 : 2;
-    const int cl = spl == 1 ? choose_cluster(c, nitems, o) : 1;
-    const int slots =
-        choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(n, nb, fp32, c->order_factor, spl), (int64_t)n * 16, cl);
-    SlotWs ws;
-    CK_RC(alloc_slots(c, ws, slots, n, nb, fp32, n, spl));
-    LsArena A{};
+    CK_RC(to_dev(c, r.node_off.p, hoff, 2));
+    r.nb = g->w ? (int)r.wmax + 1 : 2;
+    r.cl = r.spl == 1 ? choose_cluster(c, r.nitems, o) : 1;
+    r.slots = choose_slots(c, r.nitems, o.ctas_per_sm, slot_bytes(n, r.nb, fp32, c->order_factor, r.spl),
+                           (int64_t)n * 16, r.cl);
+    CK_RC(alloc_slots(c, r.ws, r.slots, n, r.nb, fp32, n, r.spl, false));
+    LsArena& A = r.A;
     A.rp = g->row_ptr; A.col = g->col; A.w = (const int32_t*)g->w; A.mu = nullptr;
     if (g->directed) {
-        A.irp = T.rp.p; A.icol = T.col.p; A.iw = g->w ? (const int32_t*)T.w.p : nullptr;
+        A.irp = r.T.rp.p; A.icol = r.T.col.p; A.iw = g->w ? (const int32_t*)r.T.w.p : nullptr;
     } else {
         A.irp = g->row_ptr; A.icol = g->col; A.iw = (const int32_t*)g->w;
     }
     A.imu = nullptr;
-    A.node_off = node_off.p;
-    LsParams P{};
+    A.node_off = r.node_off.p;
+    LsParams& P = r.P;
     P.mode = LS_BRANDES;
-    P.nb = nb;
+    P.nb = r.nb;
     P.srcs = srcs;
-    P.in_s = nS > 0 ? in_s.p : nullptr;
+    P.in_s = nS > 0 ? r.in_s.p : nullptr;
     P.items_static = 0;
-    P.item_counter = ws.counter.p;
+    P.item_counter = r.ws.counter.p;
     P.flags = c->flags;
-    Timer tb(c);
-    tb.start();
-    ls_launch(fp32, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream, spl, cl);
+    return BCPP_OK;
+}
+
+// Device work of one evaluation (no host synchronization).  tb (may be null) times the
+// lockstep launch.
+int plain_emit(bcpp_ctx* c, PlainRun& r, Timer* tb) {
+    const bcpp_graph* g = &r.g;
+    const int32_t n = g->n;
+    if (r.trivial || r.nitems <= 0) {
+        if (n > 0) CK_CUDA(cudaMemsetAsync(r.bc_out, 0, (size_t)n * sizeof(double), c->stream));
+        return BCPP_OK;
+    }
+    if (r.nS == 0) {
+        iota(r.all.p, n, c->stream);
+        c->launches++;
+    }
+    if (g->directed) CK_RC(in_csr_emit(c, g, r.T));
+    if (r.ordered) CK_RC(order_emit(c, r.ord, g->directed != 0));
+    CK_RC(init_slots(c, r.ws));
+    if (tb) tb->start();
+    ls_launch(r.o.precision == BCPP_FP32_DELTA, !g->directed, r.A, r.P, r.ws.W, r.items.p, r.nitems, r.slots,
+              c->stream, r.spl, r.cl);
     c->launches++;
-    tb.stop();
+    if (tb) tb->stop();
     CK_CUDA(cudaGetLastError());
-    const bool halve = !g->directed && o.halve_undirected != 0;
-    combine_launch(ws.W.bc_sum, ws.W.bc_cmp, slots, n, n, halve ? 0.5 : 1.0, bc_out, c->stream);
+    const bool halve = !g->directed && r.o.halve_undirected != 0;
+    combine_launch(r.ws.W.bc_sum, r.ws.W.bc_cmp, r.slots, n, n, halve ? 0.5 : 1.0, r.bc_out, c->stream);
     c->launches++;
+    CK_CUDA(cudaGetLastError());
+    return BCPP_OK;
+}
+
+int brandes_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, const bcpp_opts& o, double* bc_out,
+                bcpp_stats* st) {
+    Timer tt(c), tb(c);
+    tt.start();
+    PlainRun r;
+    CK_RC(plain_prepare(c, g, S, nS, o, bc_out, r));
+    CK_RC(plain_emit(c, r, &tb));
     int rc = finish_status(c, st);
     tt.stop();
     if (st) {
@@ -814,6 +936,193 @@ int build_sk(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS_eff,
 }
 
 // --------------------------------------------------------------------------- Brandes++
+// A Brandes++ evaluation in two parts, like plain Brandes: pp_prepare runs Build_SK and takes
+// the host decisions of Brandes_SK and Centrality (targets as skeleton ids, batches, work units,
+// workspace); pp_emit queues the per-source device work (Brandes_SK, Centrality, combine) only,
+// so that it can be captured into a CUDA graph and replayed on the same skeleton.
+struct PpRun {
+    bcpp_graph g{};
+    bcpp_opts o{};
+    double scale = 1.0;
+    double* bc_out = nullptr;
+    const uint8_t* dflag = nullptr;
+    Skeleton K;
+    DBuf<int32_t> tsk, tcnt;
+    OrderWs ord;
+    int32_t nt = 0;
+    SlotWs ws;
+    bool unit = true, mult = false;
+    int nb = 2, spl = 1, nitems = 0, cl = 1, slots = 1;
+    std::vector<CentralityUnit> hunits;
+    DBuf<uint8_t> sk_in_s;
+    DBuf<int64_t> irp, icnt, itmp;
+    DBuf<int32_t> icol, iw;
+    DBuf<uint64_t> imu;
+    DBuf<int64_t> node_off;
+    DBuf<CentralityUnit> units;
+    DBuf<LsItem> items;
+    LsArena A{};
+};
+
+int pp_prepare(bcpp_ctx* c, const bcpp_graph* g, uint64_t wmax, const InCsr* Tin, const int32_t* Ssing,
+               int32_t nsing, const int32_t* Ssrc, int32_t nsrc, const uint8_t* dflag, const int32_t* part, int32_t k,
+               const bcpp_opts& o, double scale, double* bc_out, PpRun& r, Timer* tb) {
+    const int32_t n = g->n;
+    const bool fp32 = o.precision == BCPP_FP32_DELTA;
+    const int64_t ns = nsrc;
+    r.g = *g; r.o = o; r.scale = scale; r.bc_out = bc_out; r.dflag = dflag;
+    // Step 1: Build_SK on P' (every node of Ssing a singleton part)
+    if (tb) tb->start();
+    Skeleton& K = r.K;
+    CK_RC(build_sk(c, g, Ssing, nsing, part, k, wmax, Tin, o, K));
+    if (tb) tb->stop();
+    const int32_t N = K.N;
+    // targets in batch order (grouped by their original part when requested), as skeleton ids
+    CK_ALLOC(r.tsk.alloc(c, ns));
+    CK_ALLOC(r.tcnt.alloc(c, 1));
+    {
+        const int32_t* Suse = Ssrc;
+        if (o.order_sources && ns > 2 * LS_LANES) {
+            CK_RC(order_targets(c, g, g->directed ? Tin->rp.p : g->row_ptr, g->directed ? Tin->col.p : g->col,
+                                g->directed ? (g->w ? Tin->w.p : nullptr) : g->w, wmax, Ssrc, ns, part, k, r.ord));
+            Suse = r.ord.out.p;
+        }
+        sk_target_ids(Suse, (int32_t)ns, K.skid.p, r.tsk.p, r.tcnt.p, c->stream);
+        c->launches++;
+    }
+    CK_RC(to_host(c, &r.nt, r.tcnt.p, 1));
+    r.unit = K.wmax_sk == 1;
+    r.mult = K.mmax_sk > 1;
+    r.nb = (int)K.wmax_sk + 1;
+    int64_t s0, s1;
+    shard_sources(o, r.nt, s0, s1);
+    // Centrality work units: chunks of 64 non-frontier nodes of parts with frontiers
+    for (int32_t i = 0; i < K.kp; i++) {
+        const int32_t sz = K.h_pstart[i + 1] - K.h_pstart[i];
+        if (K.h_nf[i] < 1 || sz <= K.h_nf[i]) continue;
+        for (int32_t v0 = K.h_nf[i]; v0 < sz; v0 += 64) r.hunits.push_back({i, v0, std::min(sz, v0 + 64), 0});
+    }
+    // without non-frontier nodes Brandes_SK runs alone and may use 64-source batches
+    r.spl = r.hunits.empty() ? choose_spl(c, s1 - s0, o) : 1;
+    std::vector<LsItem> hitems = make_items(0, s0, s1, 32 * r.spl);
+    r.nitems = (int)hitems.size();
+    r.cl = (r.nitems > 0 && r.spl == 1) ? choose_cluster(c, r.nitems, o) : 1;
+    r.slots = r.nitems > 0 ? choose_slots(c, r.nitems, o.ctas_per_sm,
+                                          slot_bytes(std::max(N, 1), r.nb, fp32, c->order_factor, r.spl),
+                                          (int64_t)n * 16, r.cl)
+                           : 1;
+    // partial sums live in the lockstep slots; combine at the end
+    CK_RC(alloc_slots(c, r.ws, r.slots, std::max(N, 1), r.nb, fp32, n, r.spl, false));
+    if (r.nitems > 0) {
+        CK_ALLOC(r.sk_in_s.alloc(c, N));
+        if (g->directed) {   // skeleton in-arcs
+            CK_ALLOC(r.icnt.alloc(c, (int64_t)N + 1));
+            CK_ALLOC(r.itmp.alloc(c, scan_tmp_elems((int64_t)N + 1)));
+            CK_ALLOC(r.irp.alloc(c, (int64_t)N + 1));
+            CK_ALLOC(r.icol.alloc(c, K.arcs));
+            CK_ALLOC(r.iw.alloc(c, K.arcs));
+            CK_ALLOC(r.imu.alloc(c, K.arcs));
+        }
+        CK_ALLOC(r.node_off.alloc(c, 2));
+        const int64_t hoff[2] = {0, N};
+        CK_RC(to_dev(c, r.node_off.p, hoff, 2));
+        LsArena& A = r.A;
+        A.rp = K.skrp.p; A.col = K.skcol.p;
+        A.w = r.unit ? nullptr : K.skw.p;
+        A.mu = r.mult ? K.skmu.p : nullptr;
+        if (g->directed) {
+            A.irp = r.irp.p; A.icol = r.icol.p; A.iw = r.unit ? nullptr : r.iw.p; A.imu = r.mult ? r.imu.p : nullptr;
+        } else {
+            A.irp = A.rp; A.icol = A.col; A.iw = A.w; A.imu = A.mu;
+        }
+        A.node_off = r.node_off.p;
+        CK_ALLOC(r.units.alloc(c, (int64_t)r.hunits.size()));
+        CK_RC(to_dev(c, r.units.p, r.hunits.data(), (int64_t)r.hunits.size()));
+        CK_ALLOC(r.items.alloc(c, r.nitems));
+        CK_RC(to_dev(c, r.items.p, hitems.data(), r.nitems));
+    }
+    return BCPP_OK;
+}
+
+// Per-source device work of Brandes++ (no host synchronization); tbr / tce (may be null) time
+// the Brandes_SK and Centrality launches.
+int pp_emit(bcpp_ctx* c, PpRun& r, Timer* tbr, Timer* tce) {
+    const bcpp_graph* g = &r.g;
+    const int32_t n = g->n;
+    const bool fp32 = r.o.precision == BCPP_FP32_DELTA;
+    Skeleton& K = r.K;
+    const int32_t N = K.N;
+    CK_RC(init_slots(c, r.ws));
+    if (r.nitems > 0) {
+        sk_gather_flags(N, K.sknode.p, r.dflag, r.sk_in_s.p, c->stream);
+        c->launches++;
+        if (g->directed) {
+            CK_CUDA(cudaMemsetAsync(r.icnt.p, 0, ((size_t)N + 1) * sizeof(int64_t), c->stream));
+            sk_transpose(N, K.skrp.p, K.skcol.p, K.skw.p, K.skmu.p, r.icnt.p, nullptr, nullptr, nullptr, 0, c->stream);
+            exclusive_scan<int64_t>(r.icnt.p, r.irp.p, (int64_t)N + 1, nullptr, r.itmp.p, c->stream, c->launches);
+            CK_CUDA(cudaMemcpyAsync(r.icnt.p, r.irp.p, ((size_t)N + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                                    c->stream));
+            sk_transpose(N, K.skrp.p, K.skcol.p, K.skw.p, K.skmu.p, r.icnt.p, r.icol.p, r.iw.p, r.imu.p, 1, c->stream);
+            c->launches += 2;
+        }
+        const SkTables T = K.tables();
+        if (r.hunits.empty()) {
+            // no non-frontier nodes: Brandes_SK alone, batches scheduled dynamically
+            LsParams P{};
+            P.mode = LS_BRANDES;
+            P.nb = r.nb;
+            P.srcs = r.tsk.p;
+            P.in_s = r.sk_in_s.p;
+            P.bc_map = K.sknode.p;
+            P.item_counter = r.ws.counter.p;
+            P.flags = c->flags;
+            if (tbr) tbr->start();
+            ls_launch(fp32, !g->directed, r.A, P, r.ws.W, r.items.p, r.nitems, r.slots, c->stream, r.spl, r.cl);
+            c->launches++;
+            if (tbr) tbr->stop();
+            CK_CUDA(cudaGetLastError());
+        }
+        for (int c0 = 0; c0 < r.nitems && !r.hunits.empty(); c0 += r.slots) {
+            const int cn = std::min(r.slots, r.nitems - c0);
+            LsParams P{};
+            P.mode = LS_SKEL;
+            P.nb = r.nb;
+            P.srcs = r.tsk.p;
+            P.in_s = r.sk_in_s.p;
+            P.bc_map = K.sknode.p;
+            P.items_static = 1;
+            P.flags = c->flags;
+            if (tbr) tbr->start();
+            ls_launch(fp32, !g->directed, r.A, P, r.ws.W, r.items.p + c0, cn, cn, c->stream, 1, r.cl);
+            c->launches++;
+            if (tbr) tbr->stop();
+            CK_CUDA(cudaGetLastError());
+            if (tce) tce->start();
+            centrality_launch(fp32, r.units.p, (int)r.hunits.size(), cn, T, K.pnodes.p, K.skbase.p, r.ws.W.d,
+                              r.ws.W.sg, r.ws.W.dl, r.ws.W.cap_n, r.ws.W.bc_sum, r.ws.W.bc_cmp, r.ws.W.cap_bc,
+                              c->flags, c->stream);
+            c->launches++;
+            if (tce) tce->stop();
+            CK_CUDA(cudaGetLastError());
+            ls_reset_launch(r.ws.W, cn, c->stream);
+            c->launches++;
+        }
+    }
+    combine_launch(r.ws.W.bc_sum, r.ws.W.bc_cmp, r.slots, n, n, r.scale, r.bc_out, c->stream);
+    c->launches++;
+    CK_CUDA(cudaGetLastError());
+    return BCPP_OK;
+}
+
+void pp_fill_stats(const PpRun& r, bcpp_stats* st) {
+    if (!st) return;
+    st->skel_nodes = r.K.N;
+    st->skel_edges = r.K.edges;
+    st->k = r.K.k_nonempty;
+    st->lcs = r.K.lcs;
+    st->table_entries = r.K.table_entries;
+}
+
 // Brandes++ core (Alg. 1 steps, and Alg. 3's Brandes_SK(G_sk, S_sc, S_dest) + Centrality):
 // every node of Ssing becomes a singleton part, the sources are Ssrc (a subset of Ssing), and
 // dflag marks the destinations (the indicator of Eq. 7 / Eq. 12 / Eq. 13).  bc_out receives the
@@ -822,204 +1131,81 @@ int brandes_pp_core(bcpp_ctx* c, const bcpp_graph* g, uint64_t wmax, const InCsr
                     int32_t nsing, const int32_t* Ssrc, int32_t nsrc, const uint8_t* dflag, const int32_t* part,
                     int32_t k, const bcpp_opts& o, double scale, double* bc_out, bcpp_stats* st, Timer& tb, Timer& tbr,
                     Timer& tce) {
-    const int32_t n = g->n;
-    const bool fp32 = o.precision == BCPP_FP32_DELTA;
-    const int64_t ns = nsrc;
-    // Step 1: Build_SK on P' (every node of Ssing a singleton part)
-    tb.start();
-    Skeleton K;
-    CK_RC(build_sk(c, g, Ssing, nsing, part, k, wmax, Tin, o, K));
-    tb.stop();
-    // Step 2 + 3: Brandes_SK from every target, Centrality of the non-frontier nodes
-    const int32_t N = K.N;
-    // targets in batch order (grouped by their original part when requested), as skeleton ids
-    DBuf<int32_t> tsk(c, ns), tcnt(c, 1);
-    CK_ALLOC(tsk); CK_ALLOC(tcnt);
-    {
-        DBuf<int32_t> Sord;
-        const int32_t* Suse = Ssrc;
-        if (o.order_sources && ns > 2 * LS_LANES) {
-            CK_RC(order_targets(c, g, g->directed ? Tin->rp.p : g->row_ptr, g->directed ? Tin->col.p : g->col,
-                                g->directed ? (g->w ? Tin->w.p : nullptr) : g->w, wmax, Ssrc, ns, part, k, Sord));
-            Suse = Sord.p;
-        }
-        sk_target_ids(Suse, (int32_t)ns, K.skid.p, tsk.p, tcnt.p, c->stream);
-        c->launches++;
-    }
-    int32_t nt = 0;
-    CK_RC(to_host(c, &nt, tcnt.p, 1));
-    DBuf<double> bsum, bcmp;
-    int slots_used = 0;
-    // partial sums live in the lockstep slots; combine at the end
-    SlotWs ws;
-    const bool unit = K.wmax_sk == 1;
-    const bool mult = K.mmax_sk > 1;
-    const int nb = (int)K.wmax_sk + 1;
-    int64_t s0, s1;
-    shard_sources(o, nt, s0, s1);
-    // Centrality work units: chunks of 64 non-frontier nodes of parts with frontiers
-    std::vector<CentralityUnit> hunits;
-    for (int32_t i = 0; i < K.kp; i++) {
-        const int32_t sz = K.h_pstart[i + 1] - K.h_pstart[i];
-        if (K.h_nf[i] < 1 || sz <= K.h_nf[i]) continue;
-        for (int32_t v0 = K.h_nf[i]; v0 < sz; v0 += 64) hunits.push_back({i, v0, std::min(sz, v0 + 64), 0});
-    }
-    // without non-frontier nodes Brandes_SK runs alone and may use 64-source batches
-    const int spl = hunits.empty() ? choose_spl(c, s1 - s0, o) : 1;
-    std::vector<LsItem> hitems = make_items(0, s0, s1, 32 * spl);
-    const int nitems = (int)hitems.size();
-    const int cl = (nitems > 0 && spl == 1) ? choose_cluster(c, nitems, o) : 1;
-    const int slots = nitems > 0 ? choose_slots(c, nitems, o.ctas_per_sm,
-                                                slot_bytes(std::max(N, 1), nb, fp32, c->order_factor, spl),
-                                                (int64_t)n * 16, cl)
-                                 : 1;
-    CK_RC(alloc_slots(c, ws, slots, std::max(N, 1), nb, fp32, n, spl));
-    slots_used = slots;
-    if (nitems > 0) {
-        DBuf<uint8_t> sk_in_s(c, N);
-        CK_ALLOC(sk_in_s);
-        sk_gather_flags(N, K.sknode.p, dflag, sk_in_s.p, c->stream);
-        c->launches++;
-        // skeleton in-arcs for directed graphs
-        DBuf<int64_t> irp;
-        DBuf<int32_t> icol, iw;
-        DBuf<uint64_t> imu;
-        if (g->directed) {
-            DBuf<int64_t> cnt(c, (int64_t)N + 1), tmp(c, scan_tmp_elems((int64_t)N + 1));
-            CK_ALLOC(cnt); CK_ALLOC(tmp);
-            CK_ALLOC(irp.alloc(c, (int64_t)N + 1));
-            CK_ALLOC(icol.alloc(c, K.arcs));
-            CK_ALLOC(iw.alloc(c, K.arcs));
-            CK_ALLOC(imu.alloc(c, K.arcs));
-            CK_CUDA(cudaMemsetAsync(cnt.p, 0, ((size_t)N + 1) * sizeof(int64_t), c->stream));
-            sk_transpose(N, K.skrp.p, K.skcol.p, K.skw.p, K.skmu.p, cnt.p, nullptr, nullptr, nullptr, 0, c->stream);
-            exclusive_scan<int64_t>(cnt.p, irp.p, (int64_t)N + 1, nullptr, tmp.p, c->stream, c->launches);
-            CK_CUDA(cudaMemcpyAsync(cnt.p, irp.p, ((size_t)N + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice,
-                                    c->stream));
-            sk_transpose(N, K.skrp.p, K.skcol.p, K.skw.p, K.skmu.p, cnt.p, icol.p, iw.p, imu.p, 1, c->stream);
-            c->launches += 2;
-        }
-        DBuf<int64_t> node_off(c, 2);
-        CK_ALLOC(node_off);
-        const int64_t hoff[2] = {0, N};
-        CK_RC(to_dev(c, node_off.p, hoff, 2));
-        LsArena A{};
-        A.rp = K.skrp.p; A.col = K.skcol.p;
-        A.w = unit ? nullptr : K.skw.p;
-        A.mu = mult ? K.skmu.p : nullptr;
-        if (g->directed) {
-            A.irp = irp.p; A.icol = icol.p; A.iw = unit ? nullptr : iw.p; A.imu = mult ? imu.p : nullptr;
-        } else {
-            A.irp = A.rp; A.icol = A.col; A.iw = A.w; A.imu = A.mu;
-        }
-        A.node_off = node_off.p;
-        DBuf<CentralityUnit> units(c, (int64_t)hunits.size());
-        CK_ALLOC(units);
-        CK_RC(to_dev(c, units.p, hunits.data(), (int64_t)hunits.size()));
-        DBuf<LsItem> items(c, nitems);
-        CK_ALLOC(items);
-        CK_RC(to_dev(c, items.p, hitems.data(), nitems));
-        const SkTables T = K.tables();
-        if (hunits.empty()) {
-            // no non-frontier nodes: Brandes_SK alone, batches scheduled dynamically
-            LsParams P{};
-            P.mode = LS_BRANDES;
-            P.nb = nb;
-            P.srcs = tsk.p;
-            P.in_s = sk_in_s.p;
-            P.bc_map = K.sknode.p;
-            P.item_counter = ws.counter.p;
-            P.flags = c->flags;
-            tbr.start();
-            ls_launch(fp32, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream, spl, cl);
-            c->launches++;
-            tbr.stop();
-            CK_CUDA(cudaGetLastError());
-        }
-        for (int c0 = 0; c0 < nitems && !hunits.empty(); c0 += slots) {
-            const int cn = std::min(slots, nitems - c0);
-            LsParams P{};
-            P.mode = LS_SKEL;
-            P.nb = nb;
-            P.srcs = tsk.p;
-            P.in_s = sk_in_s.p;
-            P.bc_map = K.sknode.p;
-            P.items_static = 1;
-            P.flags = c->flags;
-            tbr.start();
-            ls_launch(fp32, !g->directed, A, P, ws.W, items.p + c0, cn, cn, c->stream, 1, cl);
-            c->launches++;
-            tbr.stop();
-            CK_CUDA(cudaGetLastError());
-            if (!hunits.empty()) {
-                tce.start();
-                centrality_launch(fp32, units.p, (int)hunits.size(), cn, T, K.pnodes.p, K.skbase.p, ws.W.d, ws.W.sg,
-                                  ws.W.dl, ws.W.cap_n, ws.W.bc_sum, ws.W.bc_cmp, ws.W.cap_bc, c->flags, c->stream);
-                c->launches++;
-                tce.stop();
-                CK_CUDA(cudaGetLastError());
-            }
-            ls_reset_launch(ws.W, cn, c->stream);
-            c->launches++;
-        }
-    }
-    combine_launch(ws.W.bc_sum, ws.W.bc_cmp, slots_used, n, n, scale, bc_out, c->stream);
-    c->launches++;
-    if (st) {
-        st->skel_nodes = K.N;
-        st->skel_edges = K.edges;
-        st->k = K.k_nonempty;
-        st->lcs = K.lcs;
-        st->table_entries = K.table_entries;
-    }
-    CK_CUDA(cudaGetLastError());
+    PpRun r;
+    CK_RC(pp_prepare(c, g, wmax, Tin, Ssing, nsing, Ssrc, nsrc, dflag, part, k, o, scale, bc_out, r, &tb));
+    CK_RC(pp_emit(c, r, &tbr, &tce));
+    pp_fill_stats(r, st);
     return BCPP_OK;
 }
 
-int brandes_pp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, const int32_t* part, int32_t k,
-                   const bcpp_opts& o, double* bc_out, bcpp_stats* st) {
+// Brandes++ (Alg. 1) for target set S: input checks, the target indicator, Build_SK and the
+// host decisions (pp_top_prepare), then the per-source device work (pp_top_emit).
+struct PpTop {
+    bool trivial = false;
+    int32_t n = 0;
+    double* bc_out = nullptr;
+    DBuf<uint8_t> in_s;
+    DBuf<uint32_t> cnt;
+    DBuf<int32_t> Sall;
+    InCsr Tin;
+    PpRun run;
+};
+
+int pp_top_prepare(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, const int32_t* part, int32_t k,
+                   const bcpp_opts& o, double* bc_out, PpTop& t, Timer* tb) {
     CK_RC(check_graph_struct(g));
     const int32_t n = g->n;
     if (nS < 0 || (nS > 0 && !S) || (n > 0 && (!bc_out || !part)) || k < 0 || (n > 0 && k == 0)) return BCPP_EINVAL;
-    Timer tt(c);
-    tt.start();
+    t.n = n;
+    t.bc_out = bc_out;
     CK_RC(reset_flags(c));
     uint64_t wmax = 1;
     CK_RC(validate_csr(c, g, &wmax));
     const int64_t ns = nS > 0 ? nS : n;
-    DBuf<uint8_t> in_s(c, n);
-    CK_ALLOC(in_s);
-    DBuf<int32_t> Sall;
+    CK_ALLOC(t.in_s.alloc(c, n));
     const int32_t* Sp = S;
     if (nS > 0) {
-        DBuf<uint32_t> cnt(c, n);
-        CK_ALLOC(cnt);
-        CK_CUDA(cudaMemsetAsync(in_s.p, 0, (size_t)std::max(n, 1), c->stream));
-        CK_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)std::max(n, 1) * 4, c->stream));
-        targets_check(S, nS, n, in_s.p, cnt.p, c->flags, c->stream);
+        CK_ALLOC(t.cnt.alloc(c, n));
+        CK_CUDA(cudaMemsetAsync(t.in_s.p, 0, (size_t)std::max(n, 1), c->stream));
+        CK_CUDA(cudaMemsetAsync(t.cnt.p, 0, (size_t)std::max(n, 1) * 4, c->stream));
+        targets_check(S, nS, n, t.in_s.p, t.cnt.p, c->flags, c->stream);
         c->launches++;
     } else {
-        CK_CUDA(cudaMemsetAsync(in_s.p, 1, (size_t)std::max(n, 1), c->stream));
-        CK_ALLOC(Sall.alloc(c, n));
-        iota(Sall.p, n, c->stream);
+        CK_CUDA(cudaMemsetAsync(t.in_s.p, 1, (size_t)std::max(n, 1), c->stream));
+        CK_ALLOC(t.Sall.alloc(c, n));
+        iota(t.Sall.p, n, c->stream);
         c->launches++;
-        Sp = Sall.p;
+        Sp = t.Sall.p;
     }
     CK_RC(sync_flags(c));
     if (c->hflags[FLAG_INVALID]) return BCPP_EINVAL;
     if (ns < 2 || n == 0) {
-        if (n > 0) CK_CUDA(cudaMemsetAsync(bc_out, 0, (size_t)n * sizeof(double), c->stream));
-        CK_CUDA(cudaStreamSynchronize(c->stream));
+        t.trivial = true;
         return BCPP_OK;
     }
-    InCsr Tin;
-    if (g->directed) CK_RC(build_in_csr(c, g, Tin));
-    Timer tb(c), tbr(c), tce(c);
+    if (g->directed) CK_RC(build_in_csr(c, g, t.Tin));
     const bool halve = !g->directed && o.halve_undirected != 0;
-    int rc = brandes_pp_core(c, g, wmax, &Tin, Sp, (int32_t)ns, Sp, (int32_t)ns, in_s.p, part, k, o, halve ? 0.5 : 1.0,
-                             bc_out, st, tb, tbr, tce);
-    if (rc) return rc;
-    rc = finish_status(c, st);
+    return pp_prepare(c, g, wmax, &t.Tin, Sp, (int32_t)ns, Sp, (int32_t)ns, t.in_s.p, part, k, o, halve ? 0.5 : 1.0,
+                      bc_out, t.run, tb);
+}
+
+int pp_top_emit(bcpp_ctx* c, PpTop& t, Timer* tbr, Timer* tce) {
+    if (t.trivial) {
+        if (t.n > 0) CK_CUDA(cudaMemsetAsync(t.bc_out, 0, (size_t)t.n * sizeof(double), c->stream));
+        return BCPP_OK;
+    }
+    return pp_emit(c, t.run, tbr, tce);
+}
+
+int brandes_pp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, const int32_t* part, int32_t k,
+                   const bcpp_opts& o, double* bc_out, bcpp_stats* st) {
+    Timer tt(c), tb(c), tbr(c), tce(c);
+    tt.start();
+    PpTop t;
+    CK_RC(pp_top_prepare(c, g, S, nS, part, k, o, bc_out, t, &tb));
+    CK_RC(pp_top_emit(c, t, &tbr, &tce));
+    if (!t.trivial) pp_fill_stats(t.run, st);
+    int rc = finish_status(c, st);
     tt.stop();
     if (st) {
         st->ms_build_sk = tb.acc;
@@ -1417,6 +1603,130 @@ int stage_graph(bcpp_ctx* c, const bcpp_graph* hg, StagedGraph& sg) {
 
 }  // namespace
 
+// --------------------------------------------------------------------------- captured plans
+// A plan is one evaluation whose host decisions were taken once (plain_prepare / pp_top_prepare)
+// and whose device work was captured into CUDA graphs: `check` (plain Brandes only: the input
+// checks) and `run` (the evaluation).  Replays launch the graphs on the context's stream.
+struct bcpp_plan {
+    bcpp_ctx* c = nullptr;
+    int kind = 0;                        // 1: plain Brandes, 2: Brandes++
+    bcpp_graph g{};
+    const int32_t* S = nullptr;
+    int32_t nS = 0;
+    const int32_t* part = nullptr;
+    int32_t k = 0;
+    bcpp_opts o{};
+    double* bc_out = nullptr;
+    int order_factor = 8;
+    PlainRun* plain = nullptr;
+    PpTop* pp = nullptr;
+    cudaStream_t cs = nullptr;           // capture stream (the context's may be the legacy stream)
+    cudaGraphExec_t check = nullptr, run = nullptr;
+    int64_t run_kernels = 0;
+    bcpp_stats created{};                // skeleton sizes of creation (Brandes++)
+
+    void release() {
+        if (check) cudaGraphExecDestroy(check);
+        if (run) cudaGraphExecDestroy(run);
+        check = run = nullptr;
+        delete plain;
+        delete pp;
+        plain = nullptr;
+        pp = nullptr;
+    }
+};
+
+namespace {
+
+// Record the device work queued by f() on a private stream into an executable graph.
+template <class F>
+int capture_graph(bcpp_ctx* c, cudaStream_t cs, F&& f, cudaGraphExec_t* out, int64_t* nkernels) {
+    CK_CUDA(cudaStreamSynchronize(c->stream));
+    cudaStream_t saved = c->stream;
+    c->stream = cs;
+    const int64_t l0 = c->launches;
+    cudaGraph_t gr = nullptr;
+    int rc = BCPP_OK;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        rc = BCPP_ECUDA;
+    } else {
+        rc = f();
+        const cudaError_t e = cudaStreamEndCapture(cs, &gr);
+        if (rc == BCPP_OK && e != cudaSuccess) rc = BCPP_ECUDA;
+    }
+    c->stream = saved;
+    if (rc == BCPP_OK && cudaGraphInstantiate(out, gr, 0) != cudaSuccess) rc = BCPP_ECUDA;
+    if (gr) cudaGraphDestroy(gr);
+    if (rc != BCPP_OK) cudaGetLastError();
+    if (nkernels) *nkernels = c->launches - l0;
+    return rc;
+}
+
+int plan_build(bcpp_plan* p) {
+    bcpp_ctx* c = p->c;
+    p->release();
+    c->order_factor = p->order_factor;
+    int rc = BCPP_OK;
+    if (p->kind == 1) {
+        p->plain = new (std::nothrow) PlainRun();
+        if (!p->plain) rc = BCPP_ENOMEM;
+        if (!rc) rc = plain_prepare(c, &p->g, p->S, p->nS, p->o, p->bc_out, *p->plain);
+        if (!rc) rc = capture_graph(c, p->cs, [&] { return plain_emit_checks(c, *p->plain); }, &p->check, nullptr);
+        if (!rc) rc = capture_graph(c, p->cs, [&] { return plain_emit(c, *p->plain, nullptr); }, &p->run,
+                                    &p->run_kernels);
+    } else {
+        p->pp = new (std::nothrow) PpTop();
+        if (!p->pp) rc = BCPP_ENOMEM;
+        if (!rc) rc = pp_top_prepare(c, &p->g, p->S, p->nS, p->part, p->k, p->o, p->bc_out, *p->pp, nullptr);
+        if (!rc && !p->pp->trivial) pp_fill_stats(p->pp->run, &p->created);
+        if (!rc) rc = capture_graph(c, p->cs, [&] { return pp_top_emit(c, *p->pp, nullptr, nullptr); }, &p->run,
+                                    &p->run_kernels);
+    }
+    c->order_factor = 8;
+    return rc;
+}
+
+int plan_replay(bcpp_plan* p, bcpp_stats* st) {
+    bcpp_ctx* c = p->c;
+    if (p->check) {
+        CK_CUDA(cudaGraphLaunch(p->check, c->stream));
+        CK_RC(sync_flags(c));
+        if (c->hflags[FLAG_INVALID]) return BCPP_EINVAL;
+    } else {
+        CK_RC(reset_flags(c));
+    }
+    CK_CUDA(cudaGraphLaunch(p->run, c->stream));
+    return finish_status(c, st);
+}
+
+int plan_create(bcpp_ctx* c, int kind, const bcpp_graph* g, const int32_t* S, int32_t nS, const int32_t* part,
+                int32_t k, const bcpp_opts* opts, double* bc_out, bcpp_plan** out) {
+    if (!out) return BCPP_EINVAL;
+    *out = nullptr;
+    if (!c || !g) return BCPP_EINVAL;
+    const bcpp_opts o = opts_or_default(opts);
+    if (o.host_buffers) return BCPP_EINVAL;
+    bcpp_plan* p = new (std::nothrow) bcpp_plan();
+    if (!p) return BCPP_ENOMEM;
+    p->c = c; p->kind = kind; p->g = *g; p->S = S; p->nS = nS; p->part = part; p->k = k; p->o = o; p->bc_out = bc_out;
+    if (cudaStreamCreateWithFlags(&p->cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return BCPP_ECUDA;
+    }
+    const int rc = plan_build(p);
+    if (rc != BCPP_OK) {
+        p->release();
+        cudaStreamDestroy(p->cs);
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return BCPP_OK;
+}
+
+}  // namespace
+
 // A call whose per-batch settle lists outgrew the default capacity is run once more with the
 // worst-case capacity (one entry per node and source of a batch).
 template <class F>
@@ -1692,4 +2002,87 @@ int bcpp_skeleton(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS
     });
 }
 
+int bcpp_plan_brandes(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, const bcpp_opts* opts,
+                      double* bc_out, bcpp_plan** plan) {
+    return plan_create(c, 1, g, S, nS, nullptr, 0, opts, bc_out, plan);
+}
+
+int bcpp_plan_brandes_pp(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, const int32_t* part,
+                         int32_t k, const bcpp_opts* opts, double* bc_out, bcpp_plan** plan) {
+    return plan_create(c, 2, g, S, nS, part, k, opts, bc_out, plan);
+}
+
+int bcpp_plan_launch(bcpp_plan* p, bcpp_stats* stats) {
+    if (!p) return BCPP_EINVAL;
+    bcpp_ctx* c = p->c;
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    Timer tt(c);
+    tt.start();
+    int rc = plan_replay(p, stats);
+    if (rc == BCPP_ECAPACITY && p->order_factor < 64) {
+        // a batch outgrew the settled-entry list: rebuild once with the worst-case capacity
+        p->order_factor = 64;
+        rc = plan_build(p);
+        if (rc == BCPP_OK) rc = plan_replay(p, stats);
+    }
+    tt.stop();
+    if (stats) {
+        const uint32_t ovf = stats->sigma_overflow;
+        *stats = p->created;
+        stats->sigma_overflow = ovf;
+        stats->ms_total = tt.acc;
+        stats->kernel_launches = p->run_kernels;
+    }
+    return rc;
+}
+
+void bcpp_plan_destroy(bcpp_plan* p) {
+    if (!p) return;
+    cudaStreamSynchronize(p->c->stream);
+    p->release();
+    cudaStreamDestroy(p->cs);
+    delete p;
+}
+
+int bcpp_autotune(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS, const bcpp_opts* opts,
+                  bcpp_opts* tuned, float* ms_out) {
+    if (!c || !g || !tuned) return BCPP_EINVAL;
+    const bcpp_opts base = opts_or_default(opts);
+    if (base.host_buffers) return BCPP_EINVAL;
+    int rc = check_graph_struct(g);
+    if (rc) return rc;
+    *tuned = base;
+    const int64_t ns = nS > 0 ? nS : g->n;
+    static const int cand[BCPP_AUTOTUNE_CANDIDATES][2] = {{32, 1}, {32, 2}, {32, 4}, {64, 1}};
+    for (int i = 0; i < BCPP_AUTOTUNE_CANDIDATES; i++)
+        if (ms_out) ms_out[i] = -1.f;
+    if (ns < 2 || g->n == 0) return BCPP_OK;
+    // sample: one shard of the sources holding at least two waves of resident 32-source batches
+    const int64_t nitems = (ns + LS_LANES - 1) / LS_LANES;
+    const int cps = base.ctas_per_sm > 0 ? base.ctas_per_sm : LS_MIN_CTAS;
+    const int64_t wave = (int64_t)cps * c->num_sms;
+    const int64_t shards = std::max<int64_t>(1, nitems / (2 * wave));
+    DBuf<double> scratch(c, g->n);
+    if (!scratch) return BCPP_ENOMEM;
+    float best = -1.f;
+    for (int i = 0; i < BCPP_AUTOTUNE_CANDIDATES; i++) {
+        bcpp_opts o = base;
+        o.batch = cand[i][0];
+        o.cluster = cand[i][1];
+        o.shard_index = 0;
+        o.shard_count = (int32_t)shards;
+        bcpp_stats st{};
+        rc = with_capacity_retry(c, [&] { return brandes_dev(c, g, S, nS, o, scratch.p, &st); });
+        if (rc != BCPP_OK && rc != BCPP_EOVERFLOW_SIGMA) return rc;
+        if (ms_out) ms_out[i] = st.ms_brandes_sk;
+        if (best < 0.f || st.ms_brandes_sk < best) {
+            best = st.ms_brandes_sk;
+            tuned->batch = cand[i][0];
+            tuned->cluster = cand[i][1];
+        }
+    }
+    return BCPP_OK;
+}
+
 }  // extern "C"
+

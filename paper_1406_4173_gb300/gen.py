@@ -324,6 +324,11 @@ def _w_chunglu_1m(seed=0):
     return g, sample_targets(g.n, 4096, seed)
 
 
+def _w_chunglu_10k(seed=0):
+    g = chung_lu_communities(10_000, np.full(10, 1000), 2.3, 10.0, 0.90, seed)
+    return g, np.arange(g.n, dtype=np.int32)
+
+
 def _w_er_batch_4096(seed=0):
     return er_batch(4096, 512, 0.75, 64, 4096, 8.0, seed), None
 
@@ -337,6 +342,8 @@ WORKLOADS = {
                                         "exp 2.3, 90% intra, w~U[1,16], |S|=2,000"),
     "er_batch_4096": (_w_er_batch_4096, "4,096 G(n, 8/(n-1)) graphs, n log-normal median 512 sigma 0.75 "
                                         "clipped [64,4096], full BC each"),
+    "chunglu_10k": (_w_chunglu_10k, "Chung-Lu n=10,000, 10x1,000 communities, degree exp 2.3, mean 10, "
+                                    "90% intra, S=V (the small case of full profiler captures)"),
     "chunglu_1m": (_w_chunglu_1m, "Chung-Lu n=1,000,000, 1,000x1,000 communities, degree exp 2.2, mean 16, "
                                   "85% intra, |S|=4,096"),
 }

@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_binding_covers_exports(lib):
     from paper_1406_4173_gb300 import api
-    assert set(api.EXPORTS) <= set(declared_symbols())
+    assert set(api.EXPORTS) == set(declared_symbols())
 
 
 def test_strerror_and_default_opts_without_gpu(lib):

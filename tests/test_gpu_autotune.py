@@ -1,0 +1,46 @@
+"""GPU: the launch-shape autotuner (bcpp_autotune) returns one of its candidates, times each of
+them, and the tuned options give the oracle's betweenness."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1406_4173_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bc():
+    import torch
+    import paper_1406_4173_gb300 as m
+    from paper_1406_4173_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    return m
+
+
+def rel_err(x, ref):
+    return float(np.max(np.abs(x - ref) / np.maximum(np.abs(ref), 1.0)))
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_autotune_candidates_and_parity(bc, weighted):
+    g = gen.chung_lu_communities(2500, [500] * 5, 2.3, 8.0, 0.9, seed=31, wmax=8 if weighted else None)
+    G = bc.graph_from_edgelist(g)
+    S = gen.sample_targets(g.n, 700, seed=4)
+    tuned, times = bc.autotune(G, S)
+    assert (tuned["batch"], tuned["cluster"]) in bc.api.AUTOTUNE_CANDIDATES
+    assert all(t > 0 for t in times.values()), times
+    assert times[(tuned["batch"], tuned["cluster"])] == min(times.values())
+    ref, _ = oracle.brandes(g, S)
+    x = bc.brandes(G, S, **tuned).cpu().numpy()
+    assert rel_err(x, ref) <= 1e-12
+    xp = bc.brandes_pp(G, S, g.part, **tuned).cpu().numpy()
+    assert rel_err(xp, ref) <= 1e-12
+
+
+def test_autotune_trivial(bc):
+    g = gen.planted_partition(200, 2, 0.05, 0.01, seed=1)
+    G = bc.graph_from_edgelist(g)
+    tuned, times = bc.autotune(G, np.array([3], np.int32))
+    assert all(t == -1.0 for t in times.values())
