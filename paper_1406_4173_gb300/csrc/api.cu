@@ -306,6 +306,15 @@ int64_t order_capacity(int64_t cap_n, int order_factor, int spl) {
     return (int64_t)std::min(order_factor, 32 * spl) * cap_n + 1024;
 }
 
+// Settled entries per node of a batch to provide for.  With unit weights a node is settled
+// at few distinct distances per batch of 32 sources (2 to 3 on the graphs of this project),
+// so the list holds 8 per node and a batch that outgrows it makes the call retry with the
+// worst case (one per node and source).  With integer weights the distances spread (about
+// 15 per node for weights in [1,16]), so weighted runs take the worst case at once.
+int entry_factor(const bcpp_ctx* c, bool weighted, int spl) {
+    return weighted ? 32 * spl : c->order_factor;
+}
+
 int64_t slot_bytes(int64_t cap_n, int nb, bool fp32, int order_factor = 8, int spl = 1) {
     const int64_t cap_order = order_capacity(cap_n, order_factor, spl);
     const int64_t bm_words = (cap_n + 31) / 32;
@@ -357,10 +366,10 @@ int init_slots(bcpp_ctx* c, SlotWs& S) {
     return BCPP_OK;
 }
 
-int alloc_slots(bcpp_ctx* c, SlotWs& S, int slots, int64_t cap_n, int nb, bool fp32, int64_t cap_bc, int spl = 1,
-                bool init = true) {
+int alloc_slots(bcpp_ctx* c, SlotWs& S, int slots, int64_t cap_n, int nb, bool fp32, int64_t cap_bc, int spl,
+                int factor, bool init = true) {
     if (cap_n >= (1 << 25)) return BCPP_EINVAL;   // 32-bit row offsets inside a slot
-    const int64_t cap_order = order_capacity(cap_n, c->order_factor, spl);
+    const int64_t cap_order = order_capacity(cap_n, factor, spl);
     const int64_t rows = cap_n * spl;              // rows of 32 values
     const int32_t cap_steps = (int32_t)std::min<int64_t>(cap_order, 4 * (cap_n + 2) + 4096);
     const int64_t bm_words = (cap_n + 31) / 32;
@@ -496,7 +505,7 @@ int order_prepare(bcpp_ctx* c, const bcpp_graph* g, const int64_t* irp, const in
     CK_RC(to_dev(c, w.item.p, &hi, 1));
     CK_RC(to_dev(c, w.node_off.p, hoff, 2));
     const int nb = g->w ? (int)wmax + 1 : 2;
-    CK_RC(alloc_slots(c, w.ws, 1, n, nb, false, 0, 1, false));
+    CK_RC(alloc_slots(c, w.ws, 1, n, nb, false, 0, 1, entry_factor(c, g->w != nullptr, 1), false));
     w.A.rp = g->row_ptr; w.A.col = g->col; w.A.w = (const int32_t*)g->w;
     w.A.irp = irp; w.A.icol = icol; w.A.iw = (const int32_t*)iw;
     w.A.node_off = w.node_off.p;
@@ -654,9 +663,9 @@ int plain_prepare(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS
     CK_RC(to_dev(c, r.node_off.p, hoff, 2));
     r.nb = g->w ? (int)r.wmax + 1 : 2;
     r.cl = r.spl == 1 ? choose_cluster(c, r.nitems, o) : 1;
-    r.slots = choose_slots(c, r.nitems, o.ctas_per_sm, slot_bytes(n, r.nb, fp32, c->order_factor, r.spl),
-                           (int64_t)n * 16, r.cl);
-    CK_RC(alloc_slots(c, r.ws, r.slots, n, r.nb, fp32, n, r.spl, false));
+    const int ef = entry_factor(c, g->w != nullptr, r.spl);
+    r.slots = choose_slots(c, r.nitems, o.ctas_per_sm, slot_bytes(n, r.nb, fp32, ef, r.spl), (int64_t)n * 16, r.cl);
+    CK_RC(alloc_slots(c, r.ws, r.slots, n, r.nb, fp32, n, r.spl, ef, false));
     LsArena& A = r.A;
     A.rp = g->row_ptr; A.col = g->col; A.w = (const int32_t*)g->w; A.mu = nullptr;
     if (g->directed) {
@@ -876,10 +885,12 @@ int build_sk(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS_eff,
         iota(srcs.p, maxnf, c->stream);
         c->launches++;
         const int nb = g->w ? (int)wmax + 1 : 2;
-        const int slots = choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(maxpart_tab, nb, false, c->order_factor), 0);
+        // parts are small: provide the worst case (one entry per node and frontier source)
+        const int ef = entry_factor(c, true, 1);
+        const int slots = choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(maxpart_tab, nb, false, ef), 0);
         for (int dir = 0; dir < (g->directed ? 2 : 1); dir++) {
             SlotWs ws;
-            CK_RC(alloc_slots(c, ws, slots, maxpart_tab, nb, false, 0));
+            CK_RC(alloc_slots(c, ws, slots, maxpart_tab, nb, false, 0, 1, ef));
             LsArena A{};
             if (dir == 0) {
                 A.rp = lrp.p; A.col = lcol.p; A.w = g->w ? lw.p : nullptr;
@@ -904,7 +915,11 @@ int build_sk(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS_eff,
             ls_launch(false, !g->directed, A, P, ws.W, items.p, nitems, slots, c->stream);
             c->launches++;
             CK_CUDA(cudaGetLastError());
-            CK_CUDA(cudaStreamSynchronize(c->stream));
+            // A batch whose settle list outgrew its bound leaves its table rows unwritten: stop
+            // here, before the skeleton is assembled from them (the caller retries with the
+            // worst-case bound).
+            CK_RC(sync_flags(c));
+            if (c->hflags[FLAG_CAPACITY]) return BCPP_ECAPACITY;
         }
     }
     // skeleton arcs: R with <w,1>, X_i with <d_i, sigma_i>
@@ -1007,12 +1022,12 @@ int pp_prepare(bcpp_ctx* c, const bcpp_graph* g, uint64_t wmax, const InCsr* Tin
     std::vector<LsItem> hitems = make_items(0, s0, s1, 32 * r.spl);
     r.nitems = (int)hitems.size();
     r.cl = (r.nitems > 0 && r.spl == 1) ? choose_cluster(c, r.nitems, o) : 1;
+    const int ef = entry_factor(c, !r.unit, r.spl);
     r.slots = r.nitems > 0 ? choose_slots(c, r.nitems, o.ctas_per_sm,
-                                          slot_bytes(std::max(N, 1), r.nb, fp32, c->order_factor, r.spl),
-                                          (int64_t)n * 16, r.cl)
+                                          slot_bytes(std::max(N, 1), r.nb, fp32, ef, r.spl), (int64_t)n * 16, r.cl)
                            : 1;
     // partial sums live in the lockstep slots; combine at the end
-    CK_RC(alloc_slots(c, r.ws, r.slots, std::max(N, 1), r.nb, fp32, n, r.spl, false));
+    CK_RC(alloc_slots(c, r.ws, r.slots, std::max(N, 1), r.nb, fp32, n, r.spl, ef, false));
     if (r.nitems > 0) {
         CK_ALLOC(r.sk_in_s.alloc(c, N));
         if (g->directed) {   // skeleton in-arcs
@@ -1407,9 +1422,10 @@ int batched_dev(bcpp_ctx* c, int32_t ngraphs, const int64_t* node_ptr_dev, const
     c->launches++;
     const int nb = g->w ? (int)wmax + 1 : 2;
     const int slots =
-        choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(maxn, nb, fp32, c->order_factor, spl), (int64_t)n * 16);
+        choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(maxn, nb, fp32, entry_factor(c, g->w != nullptr, spl), spl),
+                     (int64_t)n * 16);
     SlotWs ws;
-    CK_RC(alloc_slots(c, ws, slots, maxn, nb, fp32, n, spl));
+    CK_RC(alloc_slots(c, ws, slots, maxn, nb, fp32, n, spl, entry_factor(c, g->w != nullptr, spl)));
     LsArena A{};
     A.rp = g->row_ptr; A.col = lcol.p; A.w = (const int32_t*)g->w;
     A.irp = g->row_ptr; A.icol = lcol.p; A.iw = (const int32_t*)g->w;
@@ -1467,9 +1483,10 @@ int sssp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* src, int32_t nsrc,
     // a batch holds each source at most once: split repeated sources across batches is not
     // needed because LS_SSSP lanes are independent rows (a repeat only repeats the row)
     const int nb = g->w ? (int)wmax + 1 : 2;
-    const int slots = choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(n, nb, false, c->order_factor), 0);
+    const int ef = entry_factor(c, g->w != nullptr, 1);
+    const int slots = choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(n, nb, false, ef), 0);
     SlotWs ws;
-    CK_RC(alloc_slots(c, ws, slots, n, nb, false, 0));
+    CK_RC(alloc_slots(c, ws, slots, n, nb, false, 0, 1, ef));
     LsArena A{};
     A.rp = g->row_ptr; A.col = g->col; A.w = (const int32_t*)g->w;
     if (g->directed) {
@@ -1714,7 +1731,11 @@ int plan_create(bcpp_ctx* c, int kind, const bcpp_graph* g, const int32_t* S, in
         delete p;
         return BCPP_ECUDA;
     }
-    const int rc = plan_build(p);
+    int rc = plan_build(p);
+    if (rc == BCPP_ECAPACITY) {   // Build_SK ran at creation and a batch outgrew its list
+        p->order_factor = 64;
+        rc = plan_build(p);
+    }
     if (rc != BCPP_OK) {
         p->release();
         cudaStreamDestroy(p->cs);
