@@ -272,7 +272,7 @@ void bcpp_plan_destroy(bcpp_plan *plan);
  * and unit weights or integer weights <= BCPP_NOALLOC_MAX_WEIGHT; anything else returns
  * BCPP_EINVAL before any work is queued.  Other errors as for bcpp_brandes.
  *
- * Scratch lives in one file-scope static device array of about 46 MB, which every GPU that
+ * Scratch lives in one file-scope static device array of about 40 MB, which every GPU that
  * loads the library holds until the process exits.  The first call on a device looks up
  * that array's device address (cudaGetSymbolAddress) once for the current device; make that
  * first call before any stream capture.  All calls share the array and it keeps the last

@@ -149,23 +149,8 @@ __device__ __forceinline__ int fetch_entry(int* next, int lane) {
 __device__ __forceinline__ LsEnt load_entry(const LsEnt* order, int e, int end) {
     if (e < end) return order[e];
     LsEnt z;
-    z.u = -1; z.deg = 0; z.a0 = 0; z.mask = 0;
+    z.u = -1; z.deg = 0; z.a0 = 0;
     return z;
-}
-
-// Lanes of row u whose distance equals D, as a bit mask over the row's ROW values (read with
-// 16-byte loads by one thread; the row is 16-byte aligned).
-template <int ROW>
-__device__ __forceinline__ uint64_t row_mask(const int32_t* row, int32_t D) {
-    uint64_t m = 0;
-    const int4* r4 = reinterpret_cast<const int4*>(row);
-#pragma unroll
-    for (int q = 0; q < ROW / 4; q++) {
-        const int4 t = r4[q];
-        m |= ((uint64_t)(t.x == D) << (4 * q)) | ((uint64_t)(t.y == D) << (4 * q + 1)) |
-             ((uint64_t)(t.z == D) << (4 * q + 2)) | ((uint64_t)(t.w == D) << (4 * q + 3));
-    }
-    return m;
 }
 
 template <typename DT, int SPL, int CL, bool FUSED, bool WEIGHTED, bool MULT>
@@ -305,16 +290,12 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
             sync();
             if (ctl->err) break;
             const int end = ctl->end;
-            // attach every entry's out-arc range and its settled lanes (independent loads, all
-            // threads; the lanes at D are final: later relaxations only reach D + w > D)
+            // attach every entry's out-arc range (independent loads, all threads)
             for (int e = beg + gtid; e < end; e += GT) {
                 const int32_t u = order[e].u;
                 const int64_t a0 = __ldg(rp + u);
-                const int32_t deg = (int32_t)(__ldg(rp + u + 1) - a0);
-                const uint64_t mk = row_mask<ROW>(d + ((int64_t)u << SH), D);
                 order[e].a0 = a0;
-                order[e].deg = deg;
-                order[e].mask = mk;
+                order[e].deg = (int32_t)(__ldg(rp + u + 1) - a0);
             }
             sync();
             // settle the nodes of step D
@@ -324,13 +305,16 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                 const int e2 = fetch_entry(&ctl->next, lane);
                 const LsEnt nxt = load_entry(order, e2, end);
                 const int u = cur.u;
-                bool act[SPL], pull[SPL];
+                int32_t du[SPL];
+                ld_row<SPL>(dl0 + ((uint32_t)u << SH), du);
+                bool act[SPL], pull[SPL], any = false;
 #pragma unroll
                 for (int s = 0; s < SPL; s++) {
-                    act[s] = (cur.mask >> (lane * SPL + s)) & 1ull;
+                    act[s] = du[s] == D;
                     pull[s] = act[s] && D > 0;
+                    any |= act[s];
                 }
-                if (cur.mask) {
+                if (__ballot_sync(FULL, any)) {
                     bool ovf = false;
                     uint64_t acc[SPL];
 #pragma unroll
@@ -449,14 +433,15 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                     const int e2 = fetch_entry(&ctl->next, lane);
                     const LsEnt nxt = load_entry(order, e2, end);
                     const int u = cur.u;
-                    bool act[SPL];
+                    int32_t du[SPL];
+                    ld_row<SPL>(dl0 + ((uint32_t)u << SH), du);
+                    bool act[SPL], any = false;
 #pragma unroll
-                    for (int s = 0; s < SPL; s++) act[s] = (cur.mask >> (lane * SPL + s)) & 1ull;
-                    if (cur.mask) {
-                        // sigma(s,u) and I_{u in S} do not depend on the arcs: request them first
-                        uint64_t su[SPL];
-                        ld_row<SPL>(sl0 + ((uint32_t)u << SH), su);
-                        const DT is_t = P.in_s ? (DT)P.in_s[base + u] : (DT)1;
+                    for (int s = 0; s < SPL; s++) {
+                        act[s] = du[s] == D;
+                        any |= act[s];
+                    }
+                    if (__ballot_sync(FULL, any)) {
                         DT acc[SPL];
 #pragma unroll
                         for (int s = 0; s < SPL; s++) acc[s] = (DT)0;
@@ -485,6 +470,9 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                                     for (int s = 0; s < SPL; s++) acc[s] += MULT ? (DT)mk[k] * cv[k][s] : cv[k][s];
                             });
                         double contrib = 0.0;
+                        uint64_t su[SPL];
+                        ld_row<SPL>(sl0 + ((uint32_t)u << SH), su);
+                        const DT is_t = P.in_s ? (DT)P.in_s[base + u] : (DT)1;
 #pragma unroll
                         for (int s = 0; s < SPL; s++) {
                             if (act[s]) {

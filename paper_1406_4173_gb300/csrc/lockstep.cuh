@@ -69,14 +69,11 @@ struct LsParams {
     uint32_t* flags;
 };
 
-// One settled (node, step) entry: the node, its out-arc range and the lanes settled at this
-// step (bit lane * SPL + s: source s of lane `lane` has d(u) equal to the step's
-// distance), all filled by one parallel pass before the step's entries are processed.
-struct __align__(8) LsEnt {
-    int64_t a0;
-    uint64_t mask;
+// One settled (node, step) entry: the node and its out-arc range, read with one 16-byte load.
+struct __align__(16) LsEnt {
     int32_t u;
     int32_t deg;
+    int64_t a0;
 };
 
 struct LsSlots {

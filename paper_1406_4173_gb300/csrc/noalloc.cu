@@ -8,7 +8,7 @@
 // their inputs and output.
 //
 // The array is part of the library image: every GPU that loads the library holds it (about
-// 46 MB) until the process exits.  All calls share it and it keeps the last call's contents;
+// 40 MB) until the process exits.  All calls share it and it keeps the last call's contents;
 // each call clears what must start at zero.  Calls whose work overlaps on the GPU (other
 // streams, other host threads) race on the array; serialize them.
 #include <mutex>
