@@ -179,7 +179,7 @@ __global__ void hub_kernel(const int64_t* rp, int32_t n, unsigned long long* bes
     if ((threadIdx.x & 31) == 0) atomicMax(best, b);
 }
 
-// keys[i] = level[S[i]] (or part[S[i]] with part), vals[i] = S[i]
+// keys[i] = key[S[i]] (a per-node sort key), vals[i] = S[i]
 __global__ void level_keys_kernel(const int32_t* S, int64_t ns, const int32_t* level, uint64_t* keys, uint32_t* vals) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += (int64_t)gridDim.x * blockDim.x) {
         keys[i] = (uint64_t)(uint32_t)level[S[i]];
@@ -465,80 +465,163 @@ int build_in_csr(bcpp_ctx* c, const bcpp_graph* g, InCsr& T) {
     return in_csr_emit(c, g, T);
 }
 
-// Order the targets so that every batch holds sources close to each other: stable sort by
-// shortest-path level from the highest-degree node (one single-source run of the lockstep
-// kernel), then, when a partition is given, by part.  Fewer distinct levels per node and batch
-// means fewer settled (node, step) entries.  Only the batching order changes, not the result.
+// Order the targets so that every batch holds sources close to each other: by position in the
+// breadth-first discovery order from the highest-degree node (level by level; within a level
+// by the position of the earliest-placed parent, then by node id), then, when a partition is
+// given, stably by part.  Sources discovered from the same parent are at distance <= 2 from
+// each other, so the nodes of the graph see few distinct distances per batch and a batch
+// settles fewer (node, step) entries.  Only the batching order changes, not the result.
+//
+// The positions depend on the graph only: order_prepare computes them (a single-source run
+// of the lockstep kernel for the levels, then one small sort per level; the level sizes are
+// read by the host), and order_emit sorts S by them (device work only, capturable).
 struct OrderWs {
     int64_t ns = 0;
     int32_t n = 0, k = 0;
     const int32_t* S = nullptr;
     const int32_t* part = nullptr;
-    const int64_t* rp = nullptr;
-    DBuf<unsigned long long> best;
-    DBuf<int32_t> level, src;
-    DBuf<uint64_t> lsig;
-    DBuf<LsItem> item;
-    DBuf<int64_t> node_off;
-    SlotWs ws;
-    LsArena A{};
-    LsParams P{};
+    DBuf<int32_t> pos;        // [n] discovery position of every node
     DBuf<uint64_t> keys, kb;
     DBuf<uint32_t> vals, vb;
     DBuf<int64_t> hist, tmp;
     DBuf<int32_t> out;        // the ordered targets
 };
 
+constexpr int ORDER_MAX_LEVELS = 4096;   // deeper graphs keep plain level order past this level
+
 __global__ void hub_src_kernel(const unsigned long long* best, int32_t* src) {
     src[0] = (int32_t)(0xffffffffu - (uint32_t)(best[0] & 0xffffffffull));
+}
+// level histogram (levels >= cap counted at cap) and the deepest level
+__global__ void level_hist_kernel(const int32_t* level, int32_t n, int32_t cap, int32_t* cnt, int32_t* maxl) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t L = level[v];
+        if (L == DINF) continue;
+        atomicAdd(&cnt[min(L, cap)], 1);
+        atomicMax(maxl, L);
+    }
+}
+// keys = level (unreached last), vals = node
+__global__ void node_level_keys_kernel(const int32_t* level, int32_t n, uint64_t unreached, uint64_t* keys,
+                                       uint32_t* vals) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        keys[v] = level[v] == DINF ? unreached : (uint64_t)level[v];
+        vals[v] = (uint32_t)v;
+    }
+}
+__global__ void scatter_pos_kernel(const uint32_t* vals, int64_t count, int64_t base, int32_t* pos) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        pos[vals[i]] = (int32_t)(base + i);
+}
+// for the nodes of one level (in id order): key = smallest position among their parents (the
+// in-neighbours one level up), val = node
+__global__ void parent_keys_kernel(const uint32_t* nodes, int64_t count, const int64_t* irp, const int32_t* icol,
+                                   const int32_t* level, const int32_t* pos, int32_t L, uint64_t* keys,
+                                   uint32_t* vals) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = nodes[i];
+        int32_t m = INT32_MAX;
+        for (int64_t p = irp[v]; p < irp[v + 1]; p++) {
+            const int32_t u = icol[p];
+            if (level[u] == L - 1) m = min(m, pos[u]);
+        }
+        keys[i] = (uint64_t)(uint32_t)m;
+        vals[i] = v;
+    }
 }
 
 int order_prepare(bcpp_ctx* c, const bcpp_graph* g, const int64_t* irp, const int32_t* icol, const uint32_t* iw,
                   uint64_t wmax, const int32_t* S, int64_t ns, const int32_t* part, int32_t k, OrderWs& w) {
     const int32_t n = g->n;
-    w.ns = ns; w.n = n; w.k = k; w.S = S; w.part = part; w.rp = g->row_ptr;
-    CK_ALLOC(w.best.alloc(c, 1));
-    CK_ALLOC(w.level.alloc(c, n)); CK_ALLOC(w.src.alloc(c, 1)); CK_ALLOC(w.lsig.alloc(c, n));
-    CK_ALLOC(w.item.alloc(c, 1)); CK_ALLOC(w.node_off.alloc(c, 2));
+    w.ns = ns; w.n = n; w.k = k; w.S = S; w.part = part;
+    // levels from the hub: one source, one 4-CTA cluster
+    DBuf<unsigned long long> best(c, 1);
+    DBuf<int32_t> level(c, n), src(c, 1), cnt(c, ORDER_MAX_LEVELS + 1), maxl(c, 1);
+    DBuf<uint64_t> lsig(c, n);
+    DBuf<LsItem> item(c, 1);
+    DBuf<int64_t> node_off(c, 2);
+    CK_ALLOC(best); CK_ALLOC(level); CK_ALLOC(src); CK_ALLOC(cnt); CK_ALLOC(maxl); CK_ALLOC(lsig); CK_ALLOC(item);
+    CK_ALLOC(node_off);
     const LsItem hi{0, 0, 1, 0};
     const int64_t hoff[2] = {0, n};
-    CK_RC(to_dev(c, w.item.p, &hi, 1));
-    CK_RC(to_dev(c, w.node_off.p, hoff, 2));
+    CK_RC(to_dev(c, item.p, &hi, 1));
+    CK_RC(to_dev(c, node_off.p, hoff, 2));
     const int nb = g->w ? (int)wmax + 1 : 2;
-    CK_RC(alloc_slots(c, w.ws, 1, n, nb, false, 0, 1, entry_factor(c, g->w != nullptr, 1), false));
-    w.A.rp = g->row_ptr; w.A.col = g->col; w.A.w = (const int32_t*)g->w;
-    w.A.irp = irp; w.A.icol = icol; w.A.iw = (const int32_t*)iw;
-    w.A.node_off = w.node_off.p;
-    w.P.mode = LS_SSSP;
-    w.P.nb = nb;
-    w.P.srcs = w.src.p;
-    w.P.dbg_d = w.level.p;
-    w.P.dbg_s = w.lsig.p;
-    w.P.dbg_n = n;
-    w.P.item_counter = w.ws.counter.p;
-    w.P.flags = c->flags;
+    SlotWs ws;
+    CK_RC(alloc_slots(c, ws, 1, n, nb, false, 0, 1, entry_factor(c, g->w != nullptr, 1)));
+    LsArena A{};
+    A.rp = g->row_ptr; A.col = g->col; A.w = (const int32_t*)g->w;
+    A.irp = irp; A.icol = icol; A.iw = (const int32_t*)iw;
+    A.node_off = node_off.p;
+    LsParams P{};
+    P.mode = LS_SSSP;
+    P.nb = nb;
+    P.srcs = src.p;
+    P.dbg_d = level.p;
+    P.dbg_s = lsig.p;
+    P.dbg_n = n;
+    P.item_counter = ws.counter.p;
+    P.flags = c->flags;
+    const unsigned nblk = (unsigned)std::min<int64_t>((n + 255) / 256, 8192);
+    CK_CUDA(cudaMemsetAsync(best.p, 0, sizeof(unsigned long long), c->stream));
+    hub_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, c->stream>>>(g->row_ptr, n, best.p);
+    hub_src_kernel<<<1, 1, 0, c->stream>>>(best.p, src.p);
+    c->launches += 2;
+    ls_launch(false, !g->directed, A, P, ws.W, item.p, 1, 1, c->stream, 1, 4);
+    c->launches++;
+    // level sizes
+    CK_CUDA(cudaMemsetAsync(cnt.p, 0, (ORDER_MAX_LEVELS + 1) * sizeof(int32_t), c->stream));
+    CK_CUDA(cudaMemsetAsync(maxl.p, 0, sizeof(int32_t), c->stream));
+    level_hist_kernel<<<nblk, 256, 0, c->stream>>>(level.p, n, ORDER_MAX_LEVELS, cnt.p, maxl.p);
+    c->launches++;
+    int32_t hmax = 0;
+    CK_RC(to_host(c, &hmax, maxl.p, 1));
+    const int32_t lmax = std::min(hmax, ORDER_MAX_LEVELS);
+    std::vector<int32_t> hcnt((size_t)lmax + 1);
+    CK_RC(to_host(c, hcnt.data(), cnt.p, (int64_t)lmax + 1));
+    // all nodes by level (stable: by id within a level), positions = level order
+    DBuf<uint64_t> nk(c, n), nkb(c, n);
+    DBuf<uint32_t> nv(c, n), nvb(c, n);
+    DBuf<int64_t> nhist(c, radix_hist_elems(n)), ntmp(c, scan_tmp_elems(radix_hist_elems(n)));
+    CK_ALLOC(nk); CK_ALLOC(nkb); CK_ALLOC(nv); CK_ALLOC(nvb); CK_ALLOC(nhist); CK_ALLOC(ntmp);
+    CK_ALLOC(w.pos.alloc(c, n));
+    node_level_keys_kernel<<<nblk, 256, 0, c->stream>>>(level.p, n, (uint64_t)hmax + 1, nk.p, nv.p);
+    radix_sort_pairs(nk.p, nv.p, nkb.p, nvb.p, n, bits_for((uint64_t)hmax + 1), nhist.p, ntmp.p, c->stream,
+                     c->launches);
+    scatter_pos_kernel<<<nblk, 256, 0, c->stream>>>(nv.p, n, 0, w.pos.p);
+    c->launches += 2;
+    // levels 1..lmax in discovery order: by the earliest-placed parent (stable: then by id)
+    const int kbits = bits_for((uint64_t)std::max(n, 1));
+    int64_t beg = hcnt.empty() ? 0 : hcnt[0];
+    for (int32_t L = 1; L <= lmax && L < ORDER_MAX_LEVELS; L++) {
+        const int64_t cntL = hcnt[L];
+        if (cntL > 1) {
+            const unsigned b = (unsigned)std::min<int64_t>((cntL + 255) / 256, 8192);
+            parent_keys_kernel<<<b, 256, 0, c->stream>>>(nv.p + beg, cntL, irp, icol, level.p, w.pos.p, L, nk.p,
+                                                         nvb.p);
+            radix_sort_pairs(nk.p, nvb.p, nkb.p, nv.p + beg, cntL, kbits, nhist.p, ntmp.p, c->stream, c->launches);
+            scatter_pos_kernel<<<b, 256, 0, c->stream>>>(nvb.p, cntL, beg, w.pos.p);
+            c->launches += 2;
+        }
+        beg += cntL;
+    }
+    CK_CUDA(cudaGetLastError());
+    // buffers of the per-call sort of S
     CK_ALLOC(w.keys.alloc(c, ns)); CK_ALLOC(w.kb.alloc(c, ns));
     CK_ALLOC(w.vals.alloc(c, ns)); CK_ALLOC(w.vb.alloc(c, ns));
     CK_ALLOC(w.hist.alloc(c, radix_hist_elems(ns)));
     CK_ALLOC(w.tmp.alloc(c, scan_tmp_elems(radix_hist_elems(ns))));
     CK_ALLOC(w.out.alloc(c, ns));
+    CK_CUDA(cudaStreamSynchronize(c->stream));   // the local buffers above go back to the pool
     return BCPP_OK;
 }
 
-int order_emit(bcpp_ctx* c, OrderWs& w, bool directed) {
-    const int32_t n = w.n;
+int order_emit(bcpp_ctx* c, OrderWs& w, bool) {
     const int64_t ns = w.ns;
-    CK_CUDA(cudaMemsetAsync(w.best.p, 0, sizeof(unsigned long long), c->stream));
-    hub_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, c->stream>>>(w.rp, n, w.best.p);
-    hub_src_kernel<<<1, 1, 0, c->stream>>>(w.best.p, w.src.p);
-    c->launches += 2;
-    CK_RC(init_slots(c, w.ws));
-    ls_launch(false, !directed, w.A, w.P, w.ws.W, w.item.p, 1, 1, c->stream, 1, 4);   // one batch: 4-CTA cluster
-    c->launches++;
-    // stable sorts: by level, then by part
     const unsigned blocks = (unsigned)std::min<int64_t>((ns + 255) / 256, 8192);
-    level_keys_kernel<<<blocks, 256, 0, c->stream>>>(w.S, ns, w.level.p, w.keys.p, w.vals.p);
-    radix_sort_pairs(w.keys.p, w.vals.p, w.kb.p, w.vb.p, ns, 31, w.hist.p, w.tmp.p, c->stream, c->launches);
+    level_keys_kernel<<<blocks, 256, 0, c->stream>>>(w.S, ns, w.pos.p, w.keys.p, w.vals.p);
+    radix_sort_pairs(w.keys.p, w.vals.p, w.kb.p, w.vb.p, ns, bits_for((uint64_t)std::max(w.n, 1)), w.hist.p, w.tmp.p,
+                     c->stream, c->launches);
     c->launches++;
     if (w.part) {
         part_keys_kernel<<<blocks, 256, 0, c->stream>>>(w.vals.p, ns, w.part, w.keys.p);
@@ -642,7 +725,11 @@ int plain_prepare(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS
         CK_ALLOC(r.all.alloc(c, n));
         srcs = r.all.p;
     }
-    if (g->directed) CK_RC(in_csr_alloc(c, g, r.T));
+    if (g->directed) {
+        // the source order below reads the in-arcs now; emit rebuilds them for every replay
+        CK_RC(in_csr_alloc(c, g, r.T));
+        CK_RC(in_csr_emit(c, g, r.T));
+    }
     if (o.order_sources && r.ns > 2 * LS_LANES && !g->w) {   // measured to help on unit weights only
         CK_RC(order_prepare(c, g, g->directed ? r.T.rp.p : g->row_ptr, g->directed ? r.T.col.p : g->col,
                             g->directed ? (g->w ? r.T.w.p : nullptr) : g->w, r.wmax, srcs, r.ns, nullptr, 0, r.ord));
