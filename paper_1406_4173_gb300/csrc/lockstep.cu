@@ -442,6 +442,9 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                         any |= act[s];
                     }
                     if (__ballot_sync(FULL, any)) {
+                        // acc(s) = sum over successors v of m(u,v) c(s,v).  On GB300 a warp-wide
+                        // FP64 add costs 16 SM cycles, so the sum skips every arc that is tight on
+                        // no lane of the warp (about half of them), with a warp-uniform branch.
                         DT acc[SPL];
 #pragma unroll
                         for (int s = 0; s < SPL; s++) acc[s] = (DT)0;
@@ -450,6 +453,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                                 const int32_t (*dv)[SPL], int left) {
                                 constexpr int U = decltype(tag)::value;
                                 DT cv[U][SPL];
+                                unsigned used = 0;
 #pragma unroll
                                 for (int k = 0; k < U; k++) {
                                     bool sc[SPL], anys = false;
@@ -463,31 +467,44 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                                     if (anys) ld_row<SPL>(cl0 + ((uint32_t)vv[k] << SH), t);
 #pragma unroll
                                     for (int s = 0; s < SPL; s++) cv[k][s] = sc[s] ? t[s] : (DT)0;
+                                    if (__any_sync(FULL, anys)) used |= 1u << k;
                                 }
 #pragma unroll
                                 for (int k = 0; k < U; k++)
+                                    if (used & (1u << k))
 #pragma unroll
-                                    for (int s = 0; s < SPL; s++) acc[s] += MULT ? (DT)mk[k] * cv[k][s] : cv[k][s];
+                                        for (int s = 0; s < SPL; s++)
+                                            acc[s] += MULT ? (DT)mk[k] * cv[k][s] : cv[k][s];
                             });
-                        double contrib = 0.0;
                         uint64_t su[SPL];
                         ld_row<SPL>(sl0 + ((uint32_t)u << SH), su);
-                        const DT is_t = P.in_s ? (DT)P.in_s[base + u] : (DT)1;
+                        // c(s,u) = (I_{u in S} + delta(s|u)) / sigma(s,u) = acc + I_{u in S} / sigma(s,u)
+                        // with delta(s|u) = sigma(s,u) acc: non-targets need no division
+                        const bool is_t = P.in_s ? P.in_s[base + u] != 0 : true;
+                        const int64_t ix = P.bc_map ? (int64_t)P.bc_map[base + u] : base + u;
+                        // The slot owns its partial sums (no other CTA adds here) and an add needs
+                        // no reply.  FP64 dependencies: each lane adds its own (no FP64 warp
+                        // reduction); FP32 ones are summed over the warp in FP64 first (measured
+                        // faster there: their adds are cheap, the extra atomics are not).
+                        double contrib = 0.0;
 #pragma unroll
                         for (int s = 0; s < SPL; s++) {
                             if (act[s]) {
                                 const DT sd = (DT)su[s];
                                 const DT delta = sd * acc[s];
-                                cl0[((uint32_t)u << SH) + s] = (is_t + delta) / sd;
-                                if (u != my_src[s]) contrib += (double)delta;
+                                cl0[((uint32_t)u << SH) + s] = is_t ? acc[s] + (DT)1 / sd : acc[s];
+                                if (u != my_src[s]) {
+                                    if constexpr (sizeof(DT) == 8) {
+                                        if (bcs && delta != (DT)0) atomicAdd(&bcs[ix], (double)delta);
+                                    } else {
+                                        contrib += (double)delta;
+                                    }
+                                }
                             }
                         }
-                        const double tot = warp_sum(contrib);
-                        if (lane == 0 && bcs && tot != 0.0) {
-                            // the slot owns its partial sums: no other CTA adds here, and the
-                            // add needs no reply, so the warp does not wait for it
-                            const int64_t ix = P.bc_map ? (int64_t)P.bc_map[base + u] : base + u;
-                            atomicAdd(&bcs[ix], tot);
+                        if constexpr (sizeof(DT) != 8) {
+                            const double tot = warp_sum(contrib);
+                            if (lane == 0 && bcs && tot != 0.0) atomicAdd(&bcs[ix], tot);
                         }
                     }
                     e = e2;

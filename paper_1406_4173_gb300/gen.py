@@ -329,6 +329,11 @@ def _w_chunglu_10k(seed=0):
     return g, np.arange(g.n, dtype=np.int32)
 
 
+def _w_planted_200k(seed=0):
+    g = planted_partition(200_000, 100, 0.005, 9e-8, seed)
+    return g, sample_targets(g.n, 200, seed)
+
+
 def _w_er_batch_4096(seed=0):
     return er_batch(4096, 512, 0.75, 64, 4096, 8.0, seed), None
 
@@ -344,6 +349,9 @@ WORKLOADS = {
                                         "clipped [64,4096], full BC each"),
     "chunglu_10k": (_w_chunglu_10k, "Chung-Lu n=10,000, 10x1,000 communities, degree exp 2.3, mean 10, "
                                     "90% intra, S=V (the small case of full profiler captures)"),
+    "planted_200k": (_w_planted_200k, "planted partition n=200,000, 100x2,000, p_in=0.005, p_out=9e-8 "
+                                      "(about 1,800 inter-community edges), |S|=200: a small skeleton "
+                                      "(N/n about 3%, M/m about 16%)"),
     "chunglu_1m": (_w_chunglu_1m, "Chung-Lu n=1,000,000, 1,000x1,000 communities, degree exp 2.2, mean 16, "
                                   "85% intra, |S|=4,096"),
 }

@@ -121,6 +121,23 @@ def test_directed_100k_sampled(bc):
     assert rel_err(pp, plain) < FP64_TOL
 
 
+def test_planted_200k_small_skeleton(bc):
+    """The small-skeleton workload (|S| = 200): plain Brandes and Brandes++ against the oracle
+    over every source, a Brandes++ source shard against the oracle's partial, and the skeleton
+    sizes against the oracle's Build_SK."""
+    g, S = gen.workload("planted_200k")
+    G = bc.graph_from_edgelist(g)
+    ref, _ = oracle.brandes(g, S)
+    assert rel_err(bc.brandes(G, S).cpu().numpy(), ref) < FP64_TOL
+    pp, st = bc.brandes_pp(G, S, g.part, stats=True)
+    assert rel_err(pp.cpu().numpy(), ref) < FP64_TOL
+    nodes, arcs, _ = oracle.skeleton(g, S, g.part)
+    assert st["skel_nodes"] == len(nodes) and st["skel_edges"] == len(arcs[0]) // 2
+    ref20, _ = oracle.brandes(g, S, nsrc=20)
+    got20 = bc.brandes_pp(G, S, g.part, shard=(0, 10), order_sources=False).cpu().numpy()
+    assert rel_err(got20, ref20) < FP64_TOL
+
+
 def test_er_batch_4096_sampled(bc):
     gs, _ = gen.workload("er_batch_4096")
     arena = bc.build_arena(gs)
