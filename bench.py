@@ -503,6 +503,54 @@ def _run_batched(args, bc, graphs, ctx, flush, dev, ws, rank):
     ref64, got32 = (a, b) if prec == "fp64" else (b, a)
     fp32 = {"ms": so["ms_total"] if prec == "fp64" else ms, "fp64_ms": ms if prec == "fp64" else so["ms_total"],
             "max_rel_err_fp32_vs_fp64": _rel(got32, ref64)}
+    # roofline of the batched lockstep launch: per graph, |V_g| sources of the per-source model
+    # bytes, with the tight-arc count D_g from the measured tight fraction of sampled graphs
+    # (their distances from 4 sources each, on the GPU)
+    rng = np.random.default_rng(0)
+    fracs = []
+    for gi in rng.choice(len(graphs), size=min(32, len(graphs)), replace=False):
+        gg = graphs[int(gi)]
+        Gs = bc.graph_from_edgelist(gg, ctx)
+        srcs = np.linspace(0, gg.n - 1, 4).astype(np.int32)
+        dist_s, _ = bc.sssp(Gs, srcs, ctx=ctx, allow_overflow=True)
+        dist_s = dist_s.cpu().numpy().astype(np.int64)
+        rp, col = Gs.row_ptr.cpu().numpy(), Gs.col.cpu().numpy()
+        tails = np.repeat(np.arange(gg.n), np.diff(rp))
+        for i in range(len(srcs)):
+            dd = dist_s[i]
+            ok = (dd[tails] < np.iinfo(np.int32).max) & (dd[col] == dd[tails] + 1)
+            fracs.append(ok.sum() / max(1, len(col)))
+    tight_frac = float(np.mean(fracs))
+    delta_bytes = 4 if prec == "fp32" else 8
+    bytes_launch = float(sum(g.n * model_bytes_per_source(g.n, 2 * g.m, tight_frac * 2 * g.m, 32, delta_bytes)
+                             for g in graphs))
+    peak, peak_kind = measured_peak_hbm()
+    ls_ms = statistics.mean(st["ms_brandes_sk"] for st in logs)
+    achieved = bytes_launch / (ls_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "ls_kernel (batched plain Brandes, forward + backward)",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s", "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": ls_ms,
+                "tight_arc_fraction": tight_frac}
+
+    # end to end: arena CSR and offsets from pinned host memory, result back, inside the timing
+    e2e = None
+    if not args.no_e2e:
+        H = bc.HostCSR.from_device(arena.graph)
+        hout = torch.empty(arena.graph.n, dtype=torch.float64).pin_memory()
+        bc.brandes_batched_host(H, arena.node_ptr_host, precision=prec, ctx=ctx, out=hout)
+        torch.cuda.synchronize()
+        _barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(1)
+            bc.brandes_batched_host(H, arena.node_ptr_host, precision=prec, ctx=ctx, out=hout)
+        torch.cuda.synchronize()
+        te = _max_over_ranks(ws, time.perf_counter() - t0, dev)
+        in_bytes = H.row_ptr.numel() * 8 + H.col.numel() * 4 + 8 * len(arena.node_ptr_host)
+        e2e = {"value": units_per_step * args.steps * ws / te, "unit": UNIT, "h2d_bytes_per_step": int(in_bytes),
+               "d2h_bytes_per_step": int(8 * arena.graph.n)}
+
     cpu, err_oracle = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
@@ -534,9 +582,7 @@ def _run_batched(args, bc, graphs, ctx, flush, dev, ws, rank):
         "plain": {"teps": value / ws, "ms": ms},
         "rel_err_vs_oracle": err_oracle,
         "fp32_delta": fp32,
-        "cuda_graph": graph,
-        "autotune": tune,
-        "wall_s": wall, "gpu_launches": launches, "roofline": None, "cpu_baseline": cpu, "e2e": None,
+        "wall_s": wall, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "clocks": clocks,
     }
 

@@ -255,6 +255,20 @@ int bcpp_plan_launch(bcpp_plan *plan, bcpp_stats *stats);
 /* Free the plan's graphs and return its workspace to the context.  NULL is ignored. */
 void bcpp_plan_destroy(bcpp_plan *plan);
 
+/* A node partition for Brandes++ callers without one (the paper takes its partitions from
+ * external tools, Sec. 6; Brandes++ is exact for every partition, Sec. 4, so only its speed
+ * depends on this choice).  Deterministic label propagation (Raghavan, Albert and Kumara 2007):
+ * labels start as the node ids; half-step t updates the nodes v with v mod 2 == t mod 2 from
+ * the previous half-step's labels: v takes the label carried by most of its neighbours (for a
+ * directed graph in- and out-arcs both count), keeps its own label when that one is among the
+ * most frequent, else takes the smallest most frequent label; nodes without neighbours keep
+ * theirs.  It stops after a round (two half-steps) without a change or after max_rounds >= 1
+ * rounds.  part_out[n] (device; host with opts->host_buffers) receives the labels numbered
+ * 0..k-1 in increasing label order, *k_out (host) the number of parts and *rounds_out (host,
+ * may be NULL) the rounds run.  opts may be NULL.  Errors as for bcpp_csr_validate. */
+int bcpp_partition_lp(bcpp_ctx *ctx, const bcpp_graph *g, int32_t max_rounds, const bcpp_opts *opts,
+                      int32_t *part_out, int32_t *k_out, int32_t *rounds_out);
+
 /* Limits of bcpp_brandes_noalloc (sizes of its static scratch array). */
 #define BCPP_NOALLOC_MAX_NODES 4096
 #define BCPP_NOALLOC_MAX_WEIGHT 15

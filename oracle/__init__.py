@@ -51,8 +51,9 @@ def _load():
             lib.orc_skeleton.argtypes = [i32, i64, P, P, P, i32, P, i32, P, i32, P, P, i64, P, P, P, P, P, P]
             lib.orc_distance_sum.argtypes = [i32, i64, P, P, i32, P, i32, P]
             lib.orc_brandes_st.argtypes = [i32, i64, P, P, P, i32, P, i32, P, i32, i32, P, P]
+            lib.orc_label_propagation.argtypes = [i32, i64, P, P, i32, i32, P, P, P]
             for f in (lib.orc_sssp, lib.orc_brandes, lib.orc_brandes_pp, lib.orc_skeleton, lib.orc_distance_sum,
-                      lib.orc_brandes_st):
+                      lib.orc_brandes_st, lib.orc_label_propagation):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -179,3 +180,16 @@ def brandes_st(g, src, dst, halve: bool | None = None):
     _check(lib.orc_brandes_st(g.n, g.m, _ptr(eu), _ptr(ev), _ptr(ew), int(g.directed), _ptr(a), int(a.shape[0]),
                               _ptr(b), int(b.shape[0]), int(bool(halve)), _ptr(bc), _ptr(ovf)), "brandes_st")
     return bc, bool(ovf[0])
+
+
+def label_propagation(g, max_rounds: int = 20):
+    """Deterministic label-propagation partition (a heuristic defined in bc_oracle.c, not by the
+    paper).  Returns (part int32[n], k, rounds)."""
+    lib = _load()
+    eu, ev, _ = _edges(g)
+    part = np.empty(max(g.n, 1), np.int32)
+    k = np.zeros(1, np.int32)
+    r = np.zeros(1, np.int32)
+    _check(lib.orc_label_propagation(g.n, g.m, _ptr(eu), _ptr(ev), int(g.directed), int(max_rounds), _ptr(part),
+                                     _ptr(k), _ptr(r)), "label_propagation")
+    return part[: g.n], int(k[0]), int(r[0])

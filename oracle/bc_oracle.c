@@ -682,3 +682,80 @@ out:
     graph_free(&g);
     return rc;
 }
+
+/* ------------------------------------------------------------------------- partition */
+/* Label propagation, the partition input of Brandes++ for callers without one (not from the
+ * paper, whose partitions come from external tools; Brandes++ is exact for any partition).
+ * Deterministic rule (Raghavan, Albert and Kumara 2007, made deterministic):
+ *   labels start as the node ids; half-step t updates the nodes v with v mod 2 == t mod 2 from
+ *   the labels of half-step t-1: v takes the label carried by most of its neighbours (each arc
+ *   counts for both of its endpoints, so a directed graph counts in- and out-arcs), keeps its
+ *   own label when that one is among the most frequent, otherwise takes the smallest most
+ *   frequent label; nodes without neighbours keep theirs.  Stop after a round of two
+ *   half-steps without a change, or after max_rounds rounds.  part_out numbers the labels in
+ *   use 0..k-1 in increasing order.  PARITY: this is a heuristic defined here, not by the
+ *   paper; its pins are hand-derived small cases and properties (see the tests). */
+static int cmp_i32(const void *a, const void *b) {
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+int orc_label_propagation(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, int32_t directed,
+                          int32_t max_rounds, int32_t *part_out, int32_t *k_out, int32_t *rounds_out) {
+    (void)directed;   /* both orientations of every arc are neighbours either way */
+    if (n < 0 || m < 0 || max_rounds < 1) return ORC_EINVAL;
+    graph_t g;
+    int rc = graph_build(&g, n, m, eu, ev, NULL, NULL, 1);
+    if (rc) return rc;
+    int32_t *lab = malloc((size_t)(n ? n : 1) * sizeof(int32_t));
+    int32_t *nxt = malloc((size_t)(n ? n : 1) * sizeof(int32_t));
+    int32_t maxdeg = 0;
+    for (int32_t v = 0; v < n; v++)
+        if (g.off[v + 1] - g.off[v] > maxdeg) maxdeg = (int32_t)(g.off[v + 1] - g.off[v]);
+    int32_t *tmp = malloc((size_t)(maxdeg ? maxdeg : 1) * sizeof(int32_t));
+    if (!lab || !nxt || !tmp) { free(lab); free(nxt); free(tmp); graph_free(&g); return ORC_ENOMEM; }
+    for (int32_t v = 0; v < n; v++) lab[v] = v;
+    int32_t rounds = 0;
+    for (int32_t r = 0; r < max_rounds; r++) {
+        int64_t changes = 0;
+        for (int parity = 0; parity < 2; parity++) {
+            memcpy(nxt, lab, (size_t)n * sizeof(int32_t));
+            for (int32_t v = parity; v < n; v += 2) {
+                const int64_t deg = g.off[v + 1] - g.off[v];
+                if (deg == 0) continue;
+                for (int64_t i = 0; i < deg; i++) tmp[i] = lab[g.adj[g.off[v] + i]];
+                qsort(tmp, (size_t)deg, sizeof(int32_t), cmp_i32);
+                int64_t best_cnt = 0, cur_cnt = 0;
+                int32_t best_lab = 0;
+                for (int64_t i = 0; i < deg;) {
+                    int64_t j = i;
+                    while (j < deg && tmp[j] == tmp[i]) j++;
+                    if (j - i > best_cnt) { best_cnt = j - i; best_lab = tmp[i]; }   /* ascending: ties keep the smaller */
+                    if (tmp[i] == lab[v]) cur_cnt = j - i;
+                    i = j;
+                }
+                nxt[v] = cur_cnt == best_cnt ? lab[v] : best_lab;
+                changes += nxt[v] != lab[v];
+            }
+            memcpy(lab, nxt, (size_t)n * sizeof(int32_t));
+        }
+        rounds++;
+        if (changes == 0) break;
+    }
+    /* number the labels in use in increasing order */
+    int32_t *rank = calloc((size_t)(n ? n : 1), sizeof(int32_t));
+    if (!rank) { free(lab); free(nxt); free(tmp); graph_free(&g); return ORC_ENOMEM; }
+    for (int32_t v = 0; v < n; v++) rank[lab[v]] = 1;
+    int32_t k = 0;
+    for (int32_t l = 0; l < n; l++) {
+        const int32_t used = rank[l];
+        rank[l] = k;
+        k += used;
+    }
+    for (int32_t v = 0; v < n; v++) part_out[v] = rank[lab[v]];
+    *k_out = k;
+    if (rounds_out) *rounds_out = rounds;
+    free(rank); free(lab); free(nxt); free(tmp);
+    graph_free(&g);
+    return ORC_OK;
+}

@@ -56,7 +56,8 @@ class c_stats(ctypes.Structure):
 EXPORTS = ["bcpp_default_opts", "bcpp_strerror", "bcpp_create", "bcpp_destroy", "bcpp_workspace_bytes",
            "bcpp_csr_build", "bcpp_csr_validate", "bcpp_brandes", "bcpp_brandes_pp", "bcpp_brandes_batched",
            "bcpp_sssp", "bcpp_skeleton", "bcpp_brandes_noalloc", "bcpp_brandes_pp_st", "bcpp_brandes_pp_all",
-           "bcpp_plan_brandes", "bcpp_plan_brandes_pp", "bcpp_plan_launch", "bcpp_plan_destroy", "bcpp_autotune"]
+           "bcpp_plan_brandes", "bcpp_plan_brandes_pp", "bcpp_plan_launch", "bcpp_plan_destroy", "bcpp_autotune",
+           "bcpp_partition_lp"]
 
 _lib = None
 _lock = threading.Lock()
@@ -97,6 +98,7 @@ def load_library(path: str | None = None):
             "bcpp_plan_launch": (ctypes.c_int, [P, ST]),
             "bcpp_plan_destroy": (None, [P]),
             "bcpp_autotune": (ctypes.c_int, [P, G, P, i32, O, O, ctypes.POINTER(ctypes.c_float)]),
+            "bcpp_partition_lp": (ctypes.c_int, [P, G, i32, O, P, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -359,6 +361,20 @@ def autotune(G: Graph, S=None, precision: str = "fp64", ctx: Context | None = No
     return {"batch": int(t.batch), "cluster": int(t.cluster)}, dict(zip(AUTOTUNE_CANDIDATES, [float(x) for x in ms]))
 
 
+def partition_lp(G: Graph, max_rounds: int = 20, ctx: Context | None = None):
+    """Label-propagation partition (bcpp_partition_lp).  Returns (part int32 device tensor, k,
+    rounds)."""
+    torch = _torch()
+    ctx = ctx or default_context()
+    part = torch.empty(max(G.n, 1), dtype=torch.int32, device=G.row_ptr.device)
+    k, r = ctypes.c_int32(0), ctypes.c_int32(0)
+    cg = G.c()
+    o = _opts()
+    _check(load_library().bcpp_partition_lp(ctx.handle, ctypes.byref(cg), int(max_rounds), ctypes.byref(o),
+                                            part.data_ptr(), ctypes.byref(k), ctypes.byref(r)))
+    return part[: G.n], int(k.value), int(r.value)
+
+
 class Plan:
     """A captured evaluation (bcpp_plan_brandes / bcpp_plan_brandes_pp): ``launch()`` replays its
     CUDA graph and returns the output tensor.  The plan holds references to the tensors it
@@ -459,6 +475,23 @@ def brandes_batched(arena: Arena, precision: str = "fp64", halve: bool = True, c
     o = _opts(precision, halve, ctas_per_sm, batch=batch)
     rc = load_library().bcpp_brandes_batched(ctx.handle, len(arena.node_ptr_host) - 1, arena.node_ptr.data_ptr(),
                                              ctypes.byref(cg), ctypes.byref(o), bc.data_ptr(), ctypes.byref(st))
+    _check(rc, allow_overflow)
+    return (bc, st.as_dict()) if stats else bc
+
+
+def brandes_batched_host(H: "HostCSR", node_ptr_host, precision: str = "fp64", halve: bool = True,
+                         ctx: Context | None = None, out=None, stats: bool = False, allow_overflow: bool = False):
+    """Batched full betweenness with the arena CSR, its node offsets and the result in (pinned)
+    host memory; the library copies in and out."""
+    torch = _torch()
+    ctx = ctx or default_context()
+    off = torch.as_tensor(np.asarray(node_ptr_host, np.int64)).pin_memory()
+    bc = out if out is not None else torch.empty(H.n, dtype=torch.float64).pin_memory()
+    st = c_stats()
+    cg = H.c()
+    o = _opts(precision, halve, host=True)
+    rc = load_library().bcpp_brandes_batched(ctx.handle, int(off.numel()) - 1, off.data_ptr(), ctypes.byref(cg),
+                                             ctypes.byref(o), bc.data_ptr(), ctypes.byref(st))
     _check(rc, allow_overflow)
     return (bc, st.as_dict()) if stats else bc
 

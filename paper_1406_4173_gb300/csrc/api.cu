@@ -10,6 +10,7 @@
 #include "common.cuh"
 #include "csr.cuh"
 #include "lockstep.cuh"
+#include "partition.cuh"
 #include "prims.cuh"
 #include "skeleton.cuh"
 
@@ -1539,6 +1540,51 @@ int batched_dev(bcpp_ctx* c, int32_t ngraphs, const int64_t* node_ptr_dev, const
     return rc;
 }
 
+// --------------------------------------------------------------------------- partition
+int partition_lp_dev(bcpp_ctx* c, const bcpp_graph* g, int32_t max_rounds, int32_t* part_out, int32_t* k_out,
+                     int32_t* rounds_out) {
+    CK_RC(check_graph_struct(g));
+    const int32_t n = g->n;
+    if (max_rounds < 1 || (n > 0 && !part_out) || !k_out) return BCPP_EINVAL;
+    CK_RC(reset_flags(c));
+    uint64_t wmax = 1;
+    CK_RC(validate_csr(c, g, &wmax));
+    *k_out = 0;
+    if (rounds_out) *rounds_out = 0;
+    if (n == 0) return BCPP_OK;
+    InCsr T;
+    if (g->directed) CK_RC(build_in_csr(c, g, T));
+    DBuf<int32_t> l0(c, n), l1(c, n), used(c, n);
+    DBuf<int64_t> rank(c, (int64_t)n + 1), tmp(c, scan_tmp_elems(n));
+    DBuf<unsigned int> changes(c, 1);
+    CK_ALLOC(l0); CK_ALLOC(l1); CK_ALLOC(used); CK_ALLOC(rank); CK_ALLOC(tmp); CK_ALLOC(changes);
+    lp_init(n, l0.p, used.p, c->stream);
+    c->launches++;
+    const int64_t* irp = g->directed ? T.rp.p : nullptr;
+    const int32_t* icol = g->directed ? T.col.p : nullptr;
+    int32_t rounds = 0;
+    for (int32_t r = 0; r < max_rounds; r++) {
+        CK_CUDA(cudaMemsetAsync(changes.p, 0, sizeof(unsigned int), c->stream));
+        lp_step(n, g->row_ptr, g->col, irp, icol, l0.p, l1.p, 0, changes.p, c->stream);
+        lp_step(n, g->row_ptr, g->col, irp, icol, l1.p, l0.p, 1, changes.p, c->stream);
+        c->launches += 2;
+        rounds++;
+        unsigned int hc = 0;
+        CK_RC(to_host(c, &hc, changes.p, 1));
+        if (hc == 0) break;
+    }
+    lp_mark(n, l0.p, used.p, c->stream);
+    exclusive_scan<int32_t>(used.p, rank.p, n, rank.p + n, tmp.p, c->stream, c->launches);
+    lp_number(n, l0.p, rank.p, part_out, c->stream);
+    c->launches += 2;
+    CK_CUDA(cudaGetLastError());
+    int64_t k = 0;
+    CK_RC(to_host(c, &k, rank.p + n, 1));
+    *k_out = (int32_t)k;
+    if (rounds_out) *rounds_out = rounds;
+    return finish_status(c, nullptr);
+}
+
 // --------------------------------------------------------------------------- inspection
 int sssp_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* src, int32_t nsrc, int32_t* dist_out,
              uint64_t* sigma_out, const bcpp_opts& o) {
@@ -2190,6 +2236,20 @@ int bcpp_autotune(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS
         }
     }
     return BCPP_OK;
+}
+
+int bcpp_partition_lp(bcpp_ctx* c, const bcpp_graph* g, int32_t max_rounds, const bcpp_opts* opts,
+                      int32_t* part_out, int32_t* k_out, int32_t* rounds_out) {
+    if (!c || !g) return BCPP_EINVAL;
+    const bcpp_opts o = opts_or_default(opts);
+    if (!o.host_buffers) return partition_lp_dev(c, g, max_rounds, part_out, k_out, rounds_out);
+    StagedGraph sg;
+    DBuf<int32_t> dp;
+    int rc = stage_graph(c, g, sg);
+    if (!rc && !dp.alloc(c, g->n)) rc = BCPP_ENOMEM;
+    if (!rc) rc = partition_lp_dev(c, &sg.g, max_rounds, dp.p, k_out, rounds_out);
+    if (rc == BCPP_OK && g->n > 0 && to_host(c, part_out, dp.p, g->n) != BCPP_OK) rc = BCPP_ECUDA;
+    return rc;
 }
 
 }  // extern "C"

@@ -77,6 +77,20 @@ def test_sigma_uint64_limit_and_overflow(bc):
 
 
 # ----------------------------------------------------------------------------- plain Brandes
+def test_brandes_large_path_counts(bc):
+    """34 x 34 grid: path counts up to C(66,33) ~ 7.2e18 (the uint64 limit's neighbourhood), so
+    the reciprocals 1/sigma of the dependency recursion span 18 decades."""
+    g = gen.grid(34, 34)
+    G = bc.graph_from_edgelist(g)
+    ref, ovf = oracle.brandes(g)
+    assert not ovf
+    assert rel_err(bc.brandes(G).cpu().numpy(), ref) < FP64_TOL
+    assert rel_err(bc.brandes(G, precision="fp32").cpu().numpy(), ref) < FP32_TOL
+    S = gen.sample_targets(g.n, 300, seed=71)
+    ref_s, _ = oracle.brandes(g, S)
+    assert rel_err(bc.brandes(G, S).cpu().numpy(), ref_s) < FP64_TOL
+
+
 @pytest.mark.parametrize("name,g", GRAPHS, ids=IDS)
 def test_brandes_all_targets(bc, name, g):
     G = bc.graph_from_edgelist(g)

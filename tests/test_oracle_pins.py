@@ -335,3 +335,66 @@ def test_pairs_of_parts_sum_to_full_betweenness(seed):
             x, _ = oracle.brandes_st(g, Pi, Pj, halve=False)
             tot += x
     assert rel_err(tot, full) < 1e-12
+
+
+# ----------------------------------------------------------------------------- label-propagation partition
+# The rule is defined in oracle/bc_oracle.c (not by the paper).  Pins: small cases traced by
+# hand from that definition, and properties that any correct implementation of it has.
+def test_label_propagation_hand_traced_cases():
+    # P4 0-1-2-3.  Round 1, even half: 0 <- 1 (only neighbour), 2 <- min(1, 3) = 1;
+    # odd half: 1 keeps 1 (two votes), 3 <- 1.  Round 2 changes nothing: one part, 2 rounds.
+    assert [list(x) if hasattr(x, "__len__") else x for x in oracle.label_propagation(gen.path(4))] == \
+        [[0, 0, 0, 0], 1, 2]
+    # P5 0-1-2-3-4.  Round 1, even: 0 <- 1, 2 <- 1, 4 <- 3 -> [1,1,1,3,3]; odd: 1 keeps 1, 3 keeps 3
+    # (tied with 1, own label kept).  Round 2 changes nothing: parts {0,1,2}, {3,4}.
+    part, k, r = oracle.label_propagation(gen.path(5))
+    assert list(part) == [0, 0, 0, 1, 1] and k == 2 and r == 2
+    # star, centre 0 and leaves 1..8.  Round 1, even: 0 <- 1 (eight ties, smallest), even leaves
+    # <- 0; odd: odd leaves <- 1.  Round 2, even: centre ties 4:4, keeps 1; even leaves <- 1.
+    # Round 3 changes nothing: one part after 3 rounds.
+    part, k, r = oracle.label_propagation(gen.star(9))
+    assert k == 1 and not part.any() and r == 3
+    # directed 3-cycle 0->1->2->0 (in- and out-arcs both count).  Round 1, even: 0 <- min(1,2) = 1,
+    # 2 <- min(0,1) = 0; odd: 1 keeps 1 (tie with 0).  Round 2, even: 0 keeps 1, 2 <- 1 (two votes).
+    # Round 3 changes nothing.
+    cyc = gen.EdgeList(3, np.array([0, 1, 2], np.int32), np.array([1, 2, 0], np.int32), None, True)
+    part, k, r = oracle.label_propagation(cyc)
+    assert k == 1 and not part.any() and r == 3
+
+
+def test_label_propagation_cliques_and_isolated_nodes():
+    # disjoint cliques with scattered ids: one part per clique; isolated nodes keep their own part
+    rng = np.random.default_rng(5)
+    sizes = [5, 7, 4, 9]
+    n = sum(sizes) + 3
+    ids = rng.permutation(n)
+    u, v, groups, o = [], [], [], 0
+    for s in sizes:
+        grp = ids[o:o + s]
+        groups.append(grp)
+        for a in range(s):
+            for b in range(a + 1, s):
+                u.append(grp[a]); v.append(grp[b])
+        o += s
+    g = gen._from_pairs(n, np.array(u), np.array(v), False)
+    part, k, _ = oracle.label_propagation(g)
+    assert k == len(sizes) + 3
+    for grp in groups:
+        assert len(set(part[grp])) == 1
+    assert len({int(part[grp[0]]) for grp in groups}) == len(sizes)
+    for x in ids[o:]:
+        assert np.sum(part == part[x]) == 1
+    # two 6-cliques joined by one edge: two parts
+    u = [a for a in range(6) for b in range(a + 1, 6)] + [6 + a for a in range(6) for b in range(a + 1, 6)] + [5]
+    v = [b for a in range(6) for b in range(a + 1, 6)] + [6 + b for a in range(6) for b in range(a + 1, 6)] + [6]
+    part, k, _ = oracle.label_propagation(gen._from_pairs(12, np.array(u), np.array(v), False))
+    assert k == 2 and len(set(part[:6])) == 1 and len(set(part[6:])) == 1
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_label_propagation_valid_partition(seed):
+    g = gen.chung_lu_communities(600, [150] * 4, 2.3, 6.0, 0.9, seed=seed, directed=bool(seed % 2))
+    part, k, r = oracle.label_propagation(g, max_rounds=30)
+    assert part.min() == 0 and part.max() == k - 1 and len(np.unique(part)) == k and 1 <= r <= 30
+    part2, k2, r2 = oracle.label_propagation(g, max_rounds=30)
+    assert np.array_equal(part, part2) and (k, r) == (k2, r2)
