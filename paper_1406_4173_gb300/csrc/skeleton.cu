@@ -254,110 +254,148 @@ __global__ void target_ids_kernel(const int32_t* S, int32_t nS, const int32_t* s
     if (threadIdx.x == 0) *cnt = base;
 }
 
-// One warp per group of CV non-frontier nodes and one slot; lanes are the slot's sources.
-// Forward: the distance and count through the entry frontiers; backward: the dependency
-// through the exit frontiers that stay on a shortest path (Eq. 13).  A frontier's state row
-// (d, sigma, c of the 32 sources) is read once per group and used for all CV nodes.
-constexpr int CV = 4;
+// Tiled Centrality: one block (16 warps) per unit of up to 64 non-frontier nodes and one slot,
+// each warp CTV nodes, lanes are the slot's sources.  The part's frontier state rows (d with
+// sigma in the forward pass, d with c in the backward pass) are staged in shared memory FT
+// frontiers at a time with coalesced loads, and each warp holds its nodes' table entries of
+// the tile in registers (lane = frontier) and broadcasts them by shuffle, so the inner loop over
+// (frontier, node) reads no global memory.  Forward: the distance and count of each node through
+// its entry frontiers; backward: the dependency through the exit frontiers that stay on a
+// shortest path (Eq. 13 with the tight-frontier tests).
+constexpr int CTV = 4;          // nodes per warp
+constexpr int CT_WARPS = 16;    // warps per block: 64 nodes = one unit
+constexpr int FT = 32;          // frontiers per tile
 
 template <typename DT>
-__global__ void __launch_bounds__(256)
-centrality_kernel(const CentralityUnit* __restrict__ units, SkTables T, const uint32_t* __restrict__ pnodes,
-                  const int32_t* __restrict__ skbase, const int32_t* __restrict__ d_all,
-                  const uint64_t* __restrict__ sg_all, const DT* __restrict__ dl_all, int64_t cap_n,
-                  double* bc_sum, double* bc_cmp, int64_t cap_bc, uint32_t* flags) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const CentralityUnit U = units[blockIdx.x];
-    const int slot = blockIdx.y;
+__global__ void __launch_bounds__(CT_WARPS * 32)
+centrality_tiled_kernel(const CentralityUnit* __restrict__ units, SkTables T, const uint32_t* __restrict__ pnodes,
+                        const int32_t* __restrict__ skbase, const int32_t* __restrict__ d_all,
+                        const uint64_t* __restrict__ sg_all, const DT* __restrict__ dl_all, int64_t cap_n,
+                        double* bc_sum, double* bc_cmp, int64_t cap_bc, uint32_t* flags, int slot_major) {
+    __shared__ int32_t s_d[FT][32];
+    __shared__ uint64_t s_x[FT][32];      // sigma rows (forward) or c rows (backward, as DT bits)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const CentralityUnit U = units[slot_major ? blockIdx.y : blockIdx.x];
+    const int slot = slot_major ? blockIdx.x : blockIdx.y;
     const int32_t i = U.part;
     const int32_t nfi = T.nf[i];
     const int64_t t0 = T.toff[i];
     const int32_t ps = T.pstart[i];
-    const int64_t sb = skbase[i];
-    const int32_t* d = d_all + (int64_t)slot * cap_n * 32 + sb * 32 + lane;
-    const uint64_t* sg = sg_all + (int64_t)slot * cap_n * 32 + sb * 32 + lane;
-    const DT* dl = dl_all + (int64_t)slot * cap_n * 32 + sb * 32 + lane;
+    const int64_t fbase = ((int64_t)slot * cap_n + skbase[i]) * 32;   // row of frontier 0 of part i
+    const int32_t vb = U.v0 + warp * CTV;
+    int nv = U.v1 - vb;
+    nv = nv < 0 ? 0 : (nv > CTV ? CTV : nv);
+    // distances as uint32: two finite distances are below 2^31, so their sum fits; "none" is
+    // 0xffffffff, above every sum
+    uint32_t dv[CTV];
+    uint64_t sv[CTV];
+#pragma unroll
+    for (int j = 0; j < CTV; j++) { dv[j] = 0xffffffffu; sv[j] = 0; }
     bool ovf = false;
-    for (int32_t vb = U.v0 + warp * CV; vb < U.v1; vb += nw * CV) {
-        const int nv = min(CV, U.v1 - vb);
-        const int64_t row0 = t0 + (int64_t)vb * nfi;     // table row of node vb; node vb+j at row0 + j*nfi
-        int64_t dv[CV];
-        uint64_t sv[CV];
+    // ---- forward: d(s,v) = min over entry frontiers, sigma(s,v) = sum over the tight ones
+    for (int32_t f0 = 0; f0 < nfi; f0 += FT) {
+        const int nt = min(FT, nfi - f0);
+        __syncthreads();
+        for (int x = threadIdx.x; x < nt * 32; x += CT_WARPS * 32) {
+            const int64_t o = fbase + (int64_t)(f0 + (x >> 5)) * 32 + (x & 31);
+            s_d[x >> 5][x & 31] = d_all[o];
+            s_x[x >> 5][x & 31] = sg_all[o];
+        }
+        int32_t tdv[CTV];
+        uint64_t tsv[CTV];
 #pragma unroll
-        for (int j = 0; j < CV; j++) { dv[j] = DINF; sv[j] = 0; }
-        for (int32_t f = 0; f < nfi; f++) {
-            int32_t dfv[CV];
-            bool any = false;
-#pragma unroll
-            for (int j = 0; j < CV; j++) {
-                dfv[j] = j < nv ? T.td[row0 + (int64_t)j * nfi + f] : DINF;
-                any |= dfv[j] != DINF;
+        for (int j = 0; j < CTV; j++) {
+            tdv[j] = DINF;
+            tsv[j] = 0;
+            if (j < nv && lane < nt) {
+                const int64_t o = t0 + (int64_t)(vb + j) * nfi + f0 + lane;
+                tdv[j] = T.td[o];
+                if (tdv[j] != DINF) tsv[j] = T.ts[o];
             }
-            if (!any) continue;
-            const int32_t dsf = d[(int64_t)f * 32];
-            if (dsf == DINF) continue;
-            bool tight[CV], need = false;
+        }
+        __syncthreads();
+        for (int f = 0; f < nt; f++) {
+            const int32_t dsf = s_d[f][lane];
 #pragma unroll
-            for (int j = 0; j < CV; j++) {
-                tight[j] = false;
-                if (dfv[j] != DINF) {
-                    const int64_t c = (int64_t)dsf + dfv[j];
+            for (int j = 0; j < CTV; j++) {
+                const int32_t tdj = __shfl_sync(FULL, tdv[j], f);
+                if (tdj == DINF) continue;                     // warp-uniform
+                bool tight = false;
+                if (dsf != DINF) {
+                    const uint32_t c = (uint32_t)dsf + (uint32_t)tdj;
                     if (c < dv[j]) { dv[j] = c; sv[j] = 0; }
-                    tight[j] = c == dv[j];
-                    need |= tight[j];
+                    tight = c == dv[j];
                 }
-            }
-            if (need) {
-                const uint64_t ssf = sg[(int64_t)f * 32];
-#pragma unroll
-                for (int j = 0; j < CV; j++)
-                    if (tight[j]) sv[j] = madd_ck(sv[j], ssf, T.ts[row0 + (int64_t)j * nfi + f], ovf);
-            }
-        }
-        DT acc[CV];
-        bool live = false;
-#pragma unroll
-        for (int j = 0; j < CV; j++) {
-            acc[j] = (DT)0;
-            live |= sv[j] != 0;
-        }
-        if (__any_sync(FULL, live)) {
-            for (int32_t f = 0; f < nfi; f++) {
-                int32_t dvf[CV];
-                bool any = false;
-#pragma unroll
-                for (int j = 0; j < CV; j++) {
-                    dvf[j] = (j < nv && sv[j] != 0) ? T.tdr[row0 + (int64_t)j * nfi + f] : DINF;
-                    any |= dvf[j] != DINF;
-                }
-                if (!any) continue;
-                const int32_t dsf = d[(int64_t)f * 32];
-                if (dsf == DINF) continue;
-                bool on[CV], need = false;
-#pragma unroll
-                for (int j = 0; j < CV; j++) {
-                    on[j] = dvf[j] != DINF && dv[j] + dvf[j] == (int64_t)dsf;
-                    need |= on[j];
-                }
-                if (need) {
-                    const DT cf = dl[(int64_t)f * 32];
-#pragma unroll
-                    for (int j = 0; j < CV; j++)
-                        if (on[j]) acc[j] += (DT)T.tsr[row0 + (int64_t)j * nfi + f] * cf;
+                if (__any_sync(FULL, tight)) {
+                    const uint64_t tsj = shfl_u64(tsv[j], f);
+                    if (tight) sv[j] = madd_ck(sv[j], s_x[f][lane], tsj, ovf);
                 }
             }
         }
+    }
+    // ---- backward: acc = sum over exit frontiers f on a shortest path of sigma_i(v,f) c(s,f)
+    DT acc[CTV];
+    bool live = false;
 #pragma unroll
-        for (int j = 0; j < CV; j++) {
-            const double delta = (double)((DT)sv[j] * acc[j]);
-            const double tot = warp_sum(delta);
-            if (lane == 0 && j < nv && tot != 0.0) {
-                const int64_t ix = (int64_t)slot * cap_bc + pnodes[ps + vb + j];
-                double s0 = bc_sum[ix], c0 = bc_cmp[ix];
-                neumaier_add(s0, c0, tot);
-                bc_sum[ix] = s0;
-                bc_cmp[ix] = c0;
+    for (int j = 0; j < CTV; j++) {
+        acc[j] = (DT)0;
+        live |= sv[j] != 0;
+    }
+    if (__syncthreads_or(live)) {
+        for (int32_t f0 = 0; f0 < nfi; f0 += FT) {
+            const int nt = min(FT, nfi - f0);
+            __syncthreads();
+            for (int x = threadIdx.x; x < nt * 32; x += CT_WARPS * 32) {
+                const int64_t o = fbase + (int64_t)(f0 + (x >> 5)) * 32 + (x & 31);
+                s_d[x >> 5][x & 31] = d_all[o];
+                DT cv = dl_all[o];
+                uint64_t bits = 0;
+                memcpy(&bits, &cv, sizeof(DT));
+                s_x[x >> 5][x & 31] = bits;
             }
+            int32_t tdv[CTV];
+            uint64_t tsv[CTV];
+#pragma unroll
+            for (int j = 0; j < CTV; j++) {
+                tdv[j] = DINF;
+                tsv[j] = 0;
+                if (j < nv && lane < nt) {
+                    const int64_t o = t0 + (int64_t)(vb + j) * nfi + f0 + lane;
+                    tdv[j] = T.tdr[o];
+                    if (tdv[j] != DINF) tsv[j] = T.tsr[o];
+                }
+            }
+            __syncthreads();
+            for (int f = 0; f < nt; f++) {
+                const int32_t dsf = s_d[f][lane];
+#pragma unroll
+                for (int j = 0; j < CTV; j++) {
+                    const int32_t tdj = __shfl_sync(FULL, tdv[j], f);
+                    if (tdj == DINF) continue;                 // warp-uniform
+                    const bool on = sv[j] != 0 && dsf != DINF && dv[j] + (uint32_t)tdj == (uint32_t)dsf;
+                    if (__any_sync(FULL, on)) {
+                        const uint64_t tsj = shfl_u64(tsv[j], f);
+                        if (on) {
+                            DT cf;
+                            const uint64_t bits = s_x[f][lane];
+                            memcpy(&cf, &bits, sizeof(DT));
+                            acc[j] += (DT)tsj * cf;
+                        }
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < CTV; j++) {
+        const double delta = (double)((DT)sv[j] * acc[j]);
+        const double tot = warp_sum(delta);
+        if (lane == 0 && j < nv && tot != 0.0) {
+            const int64_t ix = (int64_t)slot * cap_bc + pnodes[ps + vb + j];
+            double s0 = bc_sum[ix], c0 = bc_cmp[ix];
+            neumaier_add(s0, c0, tot);
+            bc_sum[ix] = s0;
+            bc_cmp[ix] = c0;
         }
     }
     if (__any_sync(FULL, ovf) && lane == 0) atomicOr(&flags[FLAG_SIGMA_OVF], 1u);
@@ -433,13 +471,16 @@ void centrality_launch(bool fp32_delta, const CentralityUnit* units, int nunits,
                        const void* dl, int64_t cap_n, double* bc_sum, double* bc_cmp, int64_t cap_bc,
                        uint32_t* flags, cudaStream_t st) {
     if (nunits <= 0 || nslots <= 0) return;
-    dim3 grid(nunits, nslots);
+    const int slot_major = nunits <= 65535 ? 1 : 0;   // grid.y is limited to 65,535
+    const dim3 grid = slot_major ? dim3(nslots, nunits) : dim3(nunits, nslots);
     if (fp32_delta)
-        centrality_kernel<float><<<grid, 256, 0, st>>>(units, T, pnodes, skbase, d, sg, (const float*)dl, cap_n,
-                                                        bc_sum, bc_cmp, cap_bc, flags);
+        centrality_tiled_kernel<float><<<grid, CT_WARPS * 32, 0, st>>>(units, T, pnodes, skbase, d, sg,
+                                                                      (const float*)dl, cap_n, bc_sum, bc_cmp,
+                                                                      cap_bc, flags, slot_major);
     else
-        centrality_kernel<double><<<grid, 256, 0, st>>>(units, T, pnodes, skbase, d, sg, (const double*)dl, cap_n,
-                                                         bc_sum, bc_cmp, cap_bc, flags);
+        centrality_tiled_kernel<double><<<grid, CT_WARPS * 32, 0, st>>>(units, T, pnodes, skbase, d, sg,
+                                                                       (const double*)dl, cap_n, bc_sum, bc_cmp,
+                                                                       cap_bc, flags, slot_major);
 }
 
 void combine_launch(const double* bc_sum, const double* bc_cmp, int nslots, int64_t cap_bc, int64_t n, double scale,
