@@ -26,10 +26,7 @@ constexpr int LS_LANES = 32;
 #define BCPP_LS_THREADS 512
 #endif
 constexpr int LS_THREADS = BCPP_LS_THREADS;                 // threads per CTA
-#ifndef BCPP_LS_MIN_CTAS
-#define BCPP_LS_MIN_CTAS (1024 / BCPP_LS_THREADS)
-#endif
-constexpr int LS_MIN_CTAS = BCPP_LS_MIN_CTAS;               // resident CTAs per SM (64 registers at 512 x 2)
+constexpr int LS_MIN_CTAS = 1024 / LS_THREADS;              // resident CTAs per SM (64 registers)
 
 enum LsMode : int { LS_BRANDES = 0, LS_SKEL = 1, LS_TABLE = 2, LS_SSSP = 3 };
 
