@@ -110,7 +110,7 @@ def measured_peak_hbm():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("lockstep.cu", "lockstep.cuh", "common.cuh"):
+    for f in ("lockstep.cu", "lockstep.cuh", "lockstep_kernel.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_1406_4173_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -301,7 +301,12 @@ struct SlotWs {
     LsSlots W{};
     int slots = 0, nb = 0;
     int64_t rows = 0;
+    bool narrow = false;        // one-byte distance rows (0xff = unreached)
 };
+
+// One-byte distance rows for unit-weight Brandes passes, except on the worst-case retry (which
+// also serves batches deeper than those rows reach).
+bool use_narrow(const bcpp_ctx* c, bool weighted) { return !weighted && c->order_factor < 64; }
 
 int64_t order_capacity(int64_t cap_n, int order_factor, int spl) {
     return (int64_t)std::min(order_factor, 32 * spl) * cap_n + 1024;
@@ -358,7 +363,7 @@ int init_slots(bcpp_ctx* c, SlotWs& S) {
         CK_CUDA(cudaMemsetAsync(S.bcs.p, 0, (size_t)S.slots * W.cap_bc * sizeof(double), c->stream));
         CK_CUDA(cudaMemsetAsync(S.bcc.p, 0, (size_t)S.slots * W.cap_bc * sizeof(double), c->stream));
     }
-    fill_i32(S.d.p, DINF, (int64_t)S.slots * S.rows * 32, c->stream);
+    fill_i32(S.d.p, S.narrow ? -1 : DINF, (int64_t)S.slots * S.rows * 32, c->stream);
     c->launches++;
     CK_CUDA(cudaMemsetAsync(S.bm.p, 0, (size_t)S.slots * S.nb * W.bm_words * sizeof(uint32_t), c->stream));
     CK_CUDA(cudaMemsetAsync(S.bflag.p, 0, (size_t)S.slots * S.nb, c->stream));
@@ -754,6 +759,7 @@ int plain_prepare(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS
     const int ef = entry_factor(c, g->w != nullptr, r.spl);
     r.slots = choose_slots(c, r.nitems, o.ctas_per_sm, slot_bytes(n, r.nb, fp32, ef, r.spl), (int64_t)n * 16, r.cl);
     CK_RC(alloc_slots(c, r.ws, r.slots, n, r.nb, fp32, n, r.spl, ef, false));
+    r.ws.narrow = use_narrow(c, g->w != nullptr);
     LsArena& A = r.A;
     A.rp = g->row_ptr; A.col = g->col; A.w = (const int32_t*)g->w; A.mu = nullptr;
     if (g->directed) {
@@ -792,7 +798,7 @@ int plain_emit(bcpp_ctx* c, PlainRun& r, Timer* tb) {
     CK_RC(init_slots(c, r.ws));
     if (tb) tb->start();
     ls_launch(r.o.precision == BCPP_FP32_DELTA, !g->directed, r.A, r.P, r.ws.W, r.items.p, r.nitems, r.slots,
-              c->stream, r.spl, r.cl);
+              c->stream, r.spl, r.cl, r.ws.narrow);
     c->launches++;
     if (tb) tb->stop();
     CK_CUDA(cudaGetLastError());
@@ -1116,6 +1122,7 @@ int pp_prepare(bcpp_ctx* c, const bcpp_graph* g, uint64_t wmax, const InCsr* Tin
                            : 1;
     // partial sums live in the lockstep slots; combine at the end
     CK_RC(alloc_slots(c, r.ws, r.slots, std::max(N, 1), r.nb, fp32, n, r.spl, ef, false));
+    r.ws.narrow = r.hunits.empty() && use_narrow(c, !r.unit);   // Centrality reads int32 rows
     if (r.nitems > 0) {
         CK_ALLOC(r.sk_in_s.alloc(c, N));
         if (g->directed) {   // skeleton in-arcs
@@ -1180,7 +1187,8 @@ int pp_emit(bcpp_ctx* c, PpRun& r, Timer* tbr, Timer* tce) {
             P.item_counter = r.ws.counter.p;
             P.flags = c->flags;
             if (tbr) tbr->start();
-            ls_launch(fp32, !g->directed, r.A, P, r.ws.W, r.items.p, r.nitems, r.slots, c->stream, r.spl, r.cl);
+            ls_launch(fp32, !g->directed, r.A, P, r.ws.W, r.items.p, r.nitems, r.slots, c->stream, r.spl, r.cl,
+                      r.ws.narrow);
             c->launches++;
             if (tbr) tbr->stop();
             CK_CUDA(cudaGetLastError());
@@ -1513,7 +1521,9 @@ int batched_dev(bcpp_ctx* c, int32_t ngraphs, const int64_t* node_ptr_dev, const
         choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(maxn, nb, fp32, entry_factor(c, g->w != nullptr, spl), spl),
                      (int64_t)n * 16);
     SlotWs ws;
-    CK_RC(alloc_slots(c, ws, slots, maxn, nb, fp32, n, spl, entry_factor(c, g->w != nullptr, spl)));
+    CK_RC(alloc_slots(c, ws, slots, maxn, nb, fp32, n, spl, entry_factor(c, g->w != nullptr, spl), false));
+    ws.narrow = use_narrow(c, g->w != nullptr);
+    CK_RC(init_slots(c, ws));
     LsArena A{};
     A.rp = g->row_ptr; A.col = lcol.p; A.w = (const int32_t*)g->w;
     A.irp = g->row_ptr; A.icol = lcol.p; A.iw = (const int32_t*)g->w;
@@ -1525,7 +1535,7 @@ int batched_dev(bcpp_ctx* c, int32_t ngraphs, const int64_t* node_ptr_dev, const
     P.item_counter = ws.counter.p;
     P.flags = c->flags;
     tb.start();
-    ls_launch(fp32, true, A, P, ws.W, items.p, nitems, slots, c->stream, spl);
+    ls_launch(fp32, true, A, P, ws.W, items.p, nitems, slots, c->stream, spl, 1, ws.narrow);
     c->launches++;
     CK_CUDA(cudaGetLastError());
     combine_launch(ws.W.bc_sum, ws.W.bc_cmp, slots, n, n, o.halve_undirected ? 0.5 : 1.0, bc_out, c->stream);

@@ -1,0 +1,644 @@
+// The lockstep kernel template and its launchers (see lockstep.cu for the description), included
+// by one translation unit per dependency precision so that the instances compile in parallel.
+#pragma once
+#include <cooperative_groups.h>
+#include <type_traits>
+
+#include "lockstep.cuh"
+
+namespace bcpp {
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+
+// Mark head v in the bucket of distance nd (fire-and-forget: a stale mark only costs a
+// visit that finds no lane at that distance).
+__device__ __forceinline__ void mark_bucket(const LsParams& P, uint32_t* bm, uint8_t* bflag, int64_t bm_words,
+                                            int v, int32_t nd, int* maxpush) {
+    const int bk = nd % P.nb;
+    atomicOr(&bm[(int64_t)bk * bm_words + (v >> 5)], 1u << (v & 31));
+    bflag[bk] = 1;
+    atomicMax(maxpush, nd);
+}
+
+// 1/x for a path count x >= 1.  FP64: a single-precision seed (relative error at most 2^-23
+// after the two roundings) refined by one Newton-Raphson step r' = r + r (1 - x r), which
+// squares the error (about 2^-46, below 1.5e-14 relative) for two FMAs instead of a full
+// double-precision division.  FP32: the ordinary division.
+__device__ __forceinline__ double recip_count(double x) {
+    const double r = (double)__frcp_rn((float)x);
+    return fma(r, fma(-x, r, 1.0), r);
+}
+__device__ __forceinline__ float recip_count(float x) { return 1.0f / x; }
+
+// Distance storage: int32 (DINF = unreached), or one byte per source for unit-weight Brandes
+// passes whose distances stay below 254 (255 = unreached), four times smaller rows.
+template <bool NARROW>
+struct DistT {
+    using T = int32_t;
+    static constexpr int32_t INF = DINF;
+};
+template <>
+struct DistT<true> {
+    using T = uint8_t;
+    static constexpr uint8_t INF = 255;
+};
+constexpr int32_t NARROW_MAX_D = 254;   // a step at this distance would relax to an unstorable 255
+
+// this lane's SPL distances of one node row, as int32 (DINF for unreached)
+template <int SPL>
+__device__ __forceinline__ void ld_dist(const int32_t* p, int32_t (&x)[SPL]) {
+    if constexpr (SPL == 1) {
+        x[0] = *p;
+    } else {
+        const int2 t = *reinterpret_cast<const int2*>(p);
+        x[0] = t.x; x[1] = t.y;
+    }
+}
+template <int SPL>
+__device__ __forceinline__ void ld_dist(const uint8_t* p, int32_t (&x)[SPL]) {
+    if constexpr (SPL == 1) {
+        const uint8_t b = *p;
+        x[0] = b == 255 ? DINF : (int32_t)b;
+    } else {
+        const uchar2 t = *reinterpret_cast<const uchar2*>(p);
+        x[0] = t.x == 255 ? DINF : (int32_t)t.x;
+        x[1] = t.y == 255 ? DINF : (int32_t)t.y;
+    }
+}
+
+// vector access to this lane's SPL consecutive values of one node row
+template <int SPL>
+__device__ __forceinline__ void ld_row(const int32_t* p, int32_t (&x)[SPL]) {
+    if constexpr (SPL == 1) {
+        x[0] = *p;
+    } else {
+        const int2 t = *reinterpret_cast<const int2*>(p);
+        x[0] = t.x; x[1] = t.y;
+    }
+}
+template <int SPL>
+__device__ __forceinline__ void ld_row(const uint64_t* p, uint64_t (&x)[SPL]) {
+    if constexpr (SPL == 1) {
+        x[0] = *p;
+    } else {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2*>(p);
+        x[0] = t.x; x[1] = t.y;
+    }
+}
+template <int SPL>
+__device__ __forceinline__ void ld_row(const double* p, double (&x)[SPL]) {
+    if constexpr (SPL == 1) {
+        x[0] = *p;
+    } else {
+        const double2 t = *reinterpret_cast<const double2*>(p);
+        x[0] = t.x; x[1] = t.y;
+    }
+}
+template <int SPL>
+__device__ __forceinline__ void ld_row(const float* p, float (&x)[SPL]) {
+    if constexpr (SPL == 1) {
+        x[0] = *p;
+    } else {
+        const float2 t = *reinterpret_cast<const float2*>(p);
+        x[0] = t.x; x[1] = t.y;
+    }
+}
+
+// One group of U arcs starting at chunk position j: heads (and weights and multiplicities)
+// are broadcast by shuffle from the chunk's registers, then the distance rows of the whole
+// group are loaded before the group is handed to f (with its size as a compile-time tag), so
+// f can issue its own dependent loads for the whole group at once.
+template <int U, int SPL, bool WEIGHTED, bool MULT, typename DD, class F>
+__device__ __forceinline__ void arc_group(int32_t mv, int32_t mw, uint64_t mm, int j, int cnt, const DD* dl0,
+                                          F&& f) {
+    constexpr int SH = SPL == 1 ? 5 : 6;
+    int32_t vv[U], ww[U], dv[U][SPL];
+    uint64_t mk[U];
+#pragma unroll
+    for (int k = 0; k < U; k++) {
+        vv[k] = __shfl_sync(FULL, mv, (j + k) & 31);
+        ww[k] = WEIGHTED ? __shfl_sync(FULL, mw, (j + k) & 31) : 1;
+        mk[k] = MULT ? shfl_u64(mm, (j + k) & 31) : 1ull;
+    }
+#pragma unroll
+    for (int k = 0; k < U; k++) {
+        if (j + k < cnt) {
+            ld_dist<SPL>(dl0 + ((uint32_t)vv[k] << SH), dv[k]);
+        } else {
+#pragma unroll
+            for (int s = 0; s < SPL; s++) dv[k][s] = DINF;
+        }
+    }
+    f(std::integral_constant<int, U>{}, vv, ww, mk, dv, cnt - j);
+}
+
+// Visit the arcs [a0, a0 + deg) of one row: 32 heads per coalesced load, then groups of
+// UNROLL arcs, or of UNROLL / 2 when at most that many are left (low-degree rows waste less).
+template <int UNROLL, int SPL, bool WEIGHTED, bool MULT, typename DD, class F>
+__device__ __forceinline__ void for_arc_groups(const int32_t* __restrict__ col, const int32_t* __restrict__ w,
+                                               const uint64_t* __restrict__ mu, int64_t a0, int32_t deg,
+                                               const DD* dl0, int lane, F&& f) {
+    for (int32_t c0 = 0; c0 < deg; c0 += 32) {
+        const int cnt = min(32, deg - c0);
+        int32_t mv = 0, mw = 1;
+        uint64_t mm = 1;
+        if (lane < cnt) {
+            mv = __ldg(col + a0 + c0 + lane);
+            if (WEIGHTED) mw = __ldg(w + a0 + c0 + lane);
+            if (MULT) mm = __ldg(mu + a0 + c0 + lane);
+        }
+        for (int j = 0; j < cnt;) {
+            if (cnt - j > UNROLL / 2) {
+                arc_group<UNROLL, SPL, WEIGHTED, MULT>(mv, mw, mm, j, cnt, dl0, f);
+                j += UNROLL;
+            } else {
+                arc_group<UNROLL / 2, SPL, WEIGHTED, MULT>(mv, mw, mm, j, cnt, dl0, f);
+                j += UNROLL / 2;
+            }
+        }
+    }
+}
+
+// Scalar control state of one batch; with a cluster it lives in the leader CTA's shared memory
+// and the other CTAs reach it through distributed shared memory.
+struct LsCtl {
+    int item, pos, next, D, done, maxpush, nsteps, err, end;
+};
+
+// Fetch the next entry index of the current step for this warp (dynamic scheduling).
+__device__ __forceinline__ int fetch_entry(int* next, int lane) {
+    int e = 0;
+    if (lane == 0) e = atomicAdd(next, 1);
+    return __shfl_sync(FULL, e, 0);
+}
+
+__device__ __forceinline__ LsEnt load_entry(const LsEnt* order, int e, int end) {
+    if (e < end) return order[e];
+    LsEnt z;
+    z.u = -1; z.deg = 0; z.a0 = 0;
+    return z;
+}
+
+template <typename DT, int SPL, int CL, bool FUSED, bool WEIGHTED, bool MULT, bool NARROW>
+__global__ void __launch_bounds__(LS_THREADS, LS_MIN_CTAS)
+ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __restrict__ items, int nitems) {
+    // CL CTAs (a thread-block cluster when CL > 1) share one batch and one slot
+    __shared__ LsCtl s_ctl;
+    LsCtl* ctl = &s_ctl;
+    int crank = 0;
+    if constexpr (CL > 1) {
+        cg::cluster_group cluster = cg::this_cluster();
+        crank = (int)cluster.block_rank();
+        ctl = cluster.map_shared_rank(&s_ctl, 0);
+    }
+    auto sync = [&]() {
+        if constexpr (CL == 1) __syncthreads();
+        else cg::this_cluster().sync();
+    };
+    constexpr int GT = CL * LS_THREADS;            // threads sharing the batch
+    const int gtid = crank * LS_THREADS + (int)threadIdx.x;
+    const int gwarp = gtid >> 5;
+    const bool leader = gtid == 0;
+    const int lane = threadIdx.x & 31;
+    const int slot = blockIdx.x / CL;
+    constexpr int ROW = 32 * SPL;                 // sources per node row
+    constexpr int SH = SPL == 1 ? 5 : 6;          // log2(ROW)
+    // arcs handled per group (bounded by the 64 registers of two resident 512-thread CTAs)
+#ifndef BCPP_LS_UNROLL
+#define BCPP_LS_UNROLL 8
+#endif
+    constexpr int UNROLL = SPL == 1 ? ((WEIGHTED && FUSED) ? (MULT ? 4 : 6) : (MULT ? 6 : BCPP_LS_UNROLL))
+                                    : ((WEIGHTED && FUSED) ? (MULT ? 2 : 3) : (MULT ? 3 : 4));
+
+    using DD = typename DistT<NARROW>::T;
+    constexpr DD DD_INF = DistT<NARROW>::INF;
+    DD* d = reinterpret_cast<DD*>(W.d) + (int64_t)slot * W.cap_n * ROW;
+    uint64_t* sg = W.sg + (int64_t)slot * W.cap_n * ROW;
+    DT* dlt = reinterpret_cast<DT*>(W.dl) + (int64_t)slot * W.cap_n * ROW;
+    DD* dl0 = d + lane * SPL;                     // this lane's slice: node v at dl0[v << SH]
+    uint64_t* sl0 = sg + lane * SPL;
+    DT* cl0 = dlt + lane * SPL;
+    LsEnt* order = W.order + (int64_t)slot * W.cap_order;
+    int32_t* step_d = W.step_d + (int64_t)slot * W.cap_steps;
+    int32_t* step_beg = W.step_beg + (int64_t)slot * W.cap_steps;
+    uint32_t* bm = W.bm + (int64_t)slot * P.nb * W.bm_words;
+    uint8_t* bflag = W.bflag + (int64_t)slot * P.nb;
+    double* bcs = W.bc_sum ? W.bc_sum + (int64_t)slot * W.cap_bc : nullptr;
+
+    bool first = true;
+    for (;;) {
+        if (leader) {
+            if (P.items_static) ctl->item = first ? slot : nitems;
+            else ctl->item = atomicAdd(P.item_counter, 1);
+        }
+        first = false;
+        sync();
+        const int it = ctl->item;
+        if (it >= nitems) break;
+        const LsItem I = items[it];
+        const int64_t base = A.node_off[I.g];
+        const int32_t n = (int32_t)(A.node_off[I.g + 1] - base);
+        const int64_t* rp = A.rp + base;
+        const int64_t* irp = A.irp + base;
+        const int32_t nf = P.nfront ? P.nfront[I.g] : 0;
+        int32_t my_src[SPL];
+#pragma unroll
+        for (int s = 0; s < SPL; s++) {
+            const int b = lane * SPL + s;
+            my_src[s] = b < I.nsrc ? P.srcs[I.src_off + b] : -1;
+        }
+
+        // sources: d = 0, sigma = 1, bucket 0
+        if (gtid < 32) {
+#pragma unroll
+            for (int s = 0; s < SPL; s++) {
+                if (my_src[s] >= 0) {
+                    dl0[((uint32_t)my_src[s] << SH) + s] = 0;
+                    sl0[((uint32_t)my_src[s] << SH) + s] = 1;
+                    atomicOr(&bm[my_src[s] >> 5], 1u << (my_src[s] & 31));
+                }
+            }
+        }
+        if (leader) {
+            bflag[0] = 1;
+            ctl->pos = 0; ctl->D = 0; ctl->maxpush = 0; ctl->nsteps = 0; ctl->err = 0;
+        }
+        sync();
+
+        // ------------------------------------------------------------------ forward
+        for (;;) {
+            if (leader) {
+                int D = ctl->D;
+                while (D <= ctl->maxpush && bflag[D % P.nb] == 0) D++;
+                ctl->D = D;
+                ctl->done = (D > ctl->maxpush) || ctl->err;
+                if (!ctl->done) {
+                    bflag[D % P.nb] = 0;
+                    if (NARROW && D >= NARROW_MAX_D) {
+                        // deeper than one-byte distances reach: the call reruns with int32 rows
+                        atomicOr(&P.flags[FLAG_DEPTH], 1u);
+                        ctl->err = 1; ctl->done = 1;
+                    } else if (ctl->nsteps >= W.cap_steps) {
+                        ctl->err = 1; ctl->done = 1;
+                    } else {
+                        step_d[ctl->nsteps] = D;
+                        step_beg[ctl->nsteps] = ctl->pos;
+                        ctl->next = ctl->pos;
+                    }
+                }
+            }
+            sync();
+            if (ctl->done) break;
+            const int32_t D = ctl->D;
+            const int beg = ctl->next;
+            // collect bucket D into the order list
+            {
+                uint32_t* bmD = bm + (int64_t)(D % P.nb) * W.bm_words;
+                const int nwords = (n + 31) >> 5;
+                const int nwr = (nwords + 31) & ~31;
+                for (int wi = gtid; wi < nwr; wi += GT) {
+                    uint32_t x = wi < nwords ? bmD[wi] : 0u;
+                    if (x) bmD[wi] = 0u;
+                    const int c = __popc(x);
+                    const int incl = warp_incl_scan(c, lane);
+                    const int tot = __shfl_sync(FULL, incl, 31);
+                    int bpos = 0;
+                    if (lane == 31 && tot) bpos = atomicAdd(&ctl->pos, tot);
+                    bpos = __shfl_sync(FULL, bpos, 31);
+                    if (tot && bpos + tot > W.cap_order) {
+                        if (lane == 0) atomicExch(&ctl->err, 1);
+                        continue;
+                    }
+                    int p = bpos + incl - c;
+                    while (x) {
+                        const int b = __ffs(x) - 1;
+                        x &= x - 1;
+                        order[p++].u = wi * 32 + b;
+                    }
+                }
+            }
+            sync();
+            if (leader) ctl->end = min(ctl->pos, (int)W.cap_order);
+            sync();
+            if (ctl->err) break;
+            const int end = ctl->end;
+            // attach every entry's out-arc range (independent loads, all threads)
+            for (int e = beg + gtid; e < end; e += GT) {
+                const int32_t u = order[e].u;
+                const int64_t a0 = __ldg(rp + u);
+                order[e].a0 = a0;
+                order[e].deg = (int32_t)(__ldg(rp + u + 1) - a0);
+            }
+            sync();
+            // settle the nodes of step D
+            int e = fetch_entry(&ctl->next, lane);
+            LsEnt cur = load_entry(order, e, end);
+            while (e < end) {
+                const int e2 = fetch_entry(&ctl->next, lane);
+                const LsEnt nxt = load_entry(order, e2, end);
+                const int u = cur.u;
+                int32_t du[SPL];
+                ld_dist<SPL>(dl0 + ((uint32_t)u << SH), du);
+                bool act[SPL], pull[SPL], any = false;
+#pragma unroll
+                for (int s = 0; s < SPL; s++) {
+                    act[s] = du[s] == D;
+                    pull[s] = act[s] && D > 0;
+                    any |= act[s];
+                }
+                if (__ballot_sync(FULL, any)) {
+                    bool ovf = false;
+                    uint64_t acc[SPL];
+#pragma unroll
+                    for (int s = 0; s < SPL; s++) acc[s] = 0;
+                    // sigma(s,u) = sum over parents v (d(v) + w(v,u) = D) of sigma(s,v) * m(v,u)
+                    auto pull_group = [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t* mk,
+                                          const int32_t (*dv)[SPL], int left) {
+                        constexpr int U = decltype(tag)::value;
+                        uint64_t sp[U][SPL];
+#pragma unroll
+                        for (int k = 0; k < U; k++) {
+                            bool par[SPL], anyp = false;
+#pragma unroll
+                            for (int s = 0; s < SPL; s++) {
+                                par[s] = k < left && pull[s] && dv[k][s] < D && dv[k][s] + ww[k] == D &&
+                                         (vv[k] >= nf || dv[k][s] == 0);
+                                anyp |= par[s];
+                            }
+                            uint64_t t[SPL];
+                            if (anyp) ld_row<SPL>(sl0 + ((uint32_t)vv[k] << SH), t);
+#pragma unroll
+                            for (int s = 0; s < SPL; s++) sp[k][s] = par[s] ? t[s] : 0ull;
+                        }
+#pragma unroll
+                        for (int k = 0; k < U; k++)
+#pragma unroll
+                            for (int s = 0; s < SPL; s++)
+                                if (sp[k][s]) acc[s] = madd_ck(acc[s], sp[k][s], MULT ? mk[k] : 1ull, ovf);
+                    };
+                    // relax the out-arcs: lower tentative distances, mark improved heads
+                    auto relax_group = [&](auto tag, const int32_t* vv, const int32_t* ww, const int32_t (*dv)[SPL],
+                                           int left) {
+                        constexpr int U = decltype(tag)::value;
+#pragma unroll
+                        for (int k = 0; k < U; k++) {
+                            if (k >= left) break;
+                            const int64_t nd64 = (int64_t)D + ww[k];
+                            const int32_t nd = nd64 < DINF ? (int32_t)nd64 : DINF;
+                            bool imp[SPL], anyi = false;
+#pragma unroll
+                            for (int s = 0; s < SPL; s++) {
+                                imp[s] = act[s] && nd < dv[k][s];
+                                anyi |= imp[s];
+                            }
+                            const unsigned im = __ballot_sync(FULL, anyi);
+                            if (im) {
+                                DD* pd = dl0 + ((uint32_t)vv[k] << SH);
+#pragma unroll
+                                for (int s = 0; s < SPL; s++) {
+                                    if (imp[s]) {
+                                        if constexpr (WEIGHTED) atomicMin(reinterpret_cast<int32_t*>(pd) + s, nd);
+                                        else pd[s] = (DD)nd;
+                                    }
+                                }
+                                if (lane == __ffs(im) - 1)
+                                    mark_bucket(P, bm, bflag, W.bm_words, vv[k], nd, &ctl->maxpush);
+                            }
+                        }
+                    };
+                    if (FUSED) {
+                        for_arc_groups<UNROLL, SPL, WEIGHTED, MULT>(A.col, A.w, A.mu, cur.a0, cur.deg, dl0, lane,
+                            [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t* mk,
+                                const int32_t (*dv)[SPL], int left) {
+                                pull_group(tag, vv, ww, mk, dv, left);
+                                relax_group(tag, vv, ww, dv, left);
+                            });
+                    } else {
+                        if (D > 0) {
+                            const int64_t i0 = __ldg(irp + u);
+                            const int32_t ideg = (int32_t)(__ldg(irp + u + 1) - i0);
+                            for_arc_groups<UNROLL, SPL, WEIGHTED, MULT>(A.icol, A.iw, A.imu, i0, ideg, dl0, lane,
+                                [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t* mk,
+                                    const int32_t (*dv)[SPL], int left) { pull_group(tag, vv, ww, mk, dv, left); });
+                        }
+                        for_arc_groups<UNROLL, SPL, WEIGHTED, false>(A.col, A.w, nullptr, cur.a0, cur.deg, dl0, lane,
+                            [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t*,
+                                const int32_t (*dv)[SPL], int left) { relax_group(tag, vv, ww, dv, left); });
+                    }
+#pragma unroll
+                    for (int s = 0; s < SPL; s++)
+                        if (pull[s]) sl0[((uint32_t)u << SH) + s] = acc[s];
+                    if (__any_sync(FULL, ovf) && lane == 0) atomicOr(&P.flags[FLAG_SIGMA_OVF], 1u);
+                }
+                e = e2;
+                cur = nxt;
+            }
+            sync();
+            if (leader) { ctl->nsteps++; ctl->D = D + 1; }
+        }
+        sync();
+        const int nsteps = ctl->nsteps;
+        const int olen = min(ctl->pos, (int)W.cap_order);
+        if (ctl->err) {
+            // a list outgrew its bound: report it and leave the slot clean for the next batch
+            if (leader) atomicOr(&P.flags[FLAG_CAPACITY], 1u);
+            for (int64_t i = gtid; i < (int64_t)n * ROW; i += GT) d[i] = DD_INF;
+            for (int64_t i = gtid; i < (int64_t)P.nb * W.bm_words; i += GT) bm[i] = 0u;
+            for (int i = gtid; i < P.nb; i += GT) bflag[i] = 0;
+            if (P.mode == LS_SKEL && leader) {
+                W.hdr[slot * 4 + 0] = 0; W.hdr[slot * 4 + 1] = 0; W.hdr[slot * 4 + 2] = it;
+            }
+            sync();
+            continue;
+        }
+
+        if (P.mode == LS_BRANDES || P.mode == LS_SKEL) {
+            // -------------------------------------------------------------- backward
+            for (int st = nsteps - 1; st >= 0; st--) {
+                if (leader) ctl->next = step_beg[st];
+                sync();
+                const int32_t D = step_d[st];
+                const int end = (st + 1 < nsteps) ? step_beg[st + 1] : olen;
+                int e = fetch_entry(&ctl->next, lane);
+                LsEnt cur = load_entry(order, e, end);
+                while (e < end) {
+                    const int e2 = fetch_entry(&ctl->next, lane);
+                    const LsEnt nxt = load_entry(order, e2, end);
+                    const int u = cur.u;
+                    int32_t du[SPL];
+                    ld_dist<SPL>(dl0 + ((uint32_t)u << SH), du);
+                    bool act[SPL], any = false;
+#pragma unroll
+                    for (int s = 0; s < SPL; s++) {
+                        act[s] = du[s] == D;
+                        any |= act[s];
+                    }
+                    if (__ballot_sync(FULL, any)) {
+                        // acc(s) = sum over successors v of m(u,v) c(s,v).  On GB300 a warp-wide
+                        // FP64 add costs 16 SM cycles, so the sum skips every arc that is tight on
+                        // no lane of the warp (about half of them), with a warp-uniform branch.
+                        DT acc[SPL];
+#pragma unroll
+                        for (int s = 0; s < SPL; s++) acc[s] = (DT)0;
+                        for_arc_groups<UNROLL, SPL, WEIGHTED, MULT>(A.col, A.w, A.mu, cur.a0, cur.deg, dl0, lane,
+                            [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t* mk,
+                                const int32_t (*dv)[SPL], int left) {
+                                constexpr int U = decltype(tag)::value;
+                                DT cv[U][SPL];
+                                unsigned used = 0;
+#pragma unroll
+                                for (int k = 0; k < U; k++) {
+                                    bool sc[SPL], anys = false;
+#pragma unroll
+                                    for (int s = 0; s < SPL; s++) {
+                                        sc[s] = k < left && act[s] && dv[k][s] != DINF &&
+                                                (int64_t)dv[k][s] == (int64_t)D + ww[k];
+                                        anys |= sc[s];
+                                    }
+                                    DT t[SPL];
+                                    if (anys) ld_row<SPL>(cl0 + ((uint32_t)vv[k] << SH), t);
+#pragma unroll
+                                    for (int s = 0; s < SPL; s++) cv[k][s] = sc[s] ? t[s] : (DT)0;
+                                    if (__any_sync(FULL, anys)) used |= 1u << k;
+                                }
+#pragma unroll
+                                for (int k = 0; k < U; k++)
+                                    if (used & (1u << k))
+#pragma unroll
+                                        for (int s = 0; s < SPL; s++)
+                                            acc[s] += MULT ? (DT)mk[k] * cv[k][s] : cv[k][s];
+                            });
+                        uint64_t su[SPL];
+                        ld_row<SPL>(sl0 + ((uint32_t)u << SH), su);
+                        // c(s,u) = (I_{u in S} + delta(s|u)) / sigma(s,u) = acc + I_{u in S} / sigma(s,u)
+                        // with delta(s|u) = sigma(s,u) acc: non-targets need no division
+                        const bool is_t = P.in_s ? P.in_s[base + u] != 0 : true;
+                        const int64_t ix = P.bc_map ? (int64_t)P.bc_map[base + u] : base + u;
+                        // The slot owns its partial sums (no other CTA adds here) and an add needs
+                        // no reply.  FP64 dependencies: each lane adds its own (no FP64 warp
+                        // reduction); FP32 ones are summed over the warp in FP64 first (measured
+                        // faster there: their adds are cheap, the extra atomics are not).
+                        double contrib = 0.0;
+#pragma unroll
+                        for (int s = 0; s < SPL; s++) {
+                            if (act[s]) {
+                                const DT sd = (DT)su[s];
+                                const DT delta = sd * acc[s];
+                                cl0[((uint32_t)u << SH) + s] = is_t ? acc[s] + recip_count(sd) : acc[s];
+                                if (u != my_src[s]) {
+                                    if constexpr (sizeof(DT) == 8) {
+                                        if (bcs && delta != (DT)0) atomicAdd(&bcs[ix], (double)delta);
+                                    } else {
+                                        contrib += (double)delta;
+                                    }
+                                }
+                            }
+                        }
+                        if constexpr (sizeof(DT) != 8) {
+                            const double tot = warp_sum(contrib);
+                            if (lane == 0 && bcs && tot != 0.0) atomicAdd(&bcs[ix], tot);
+                        }
+                    }
+                    e = e2;
+                    cur = nxt;
+                }
+                sync();
+            }
+        } else if constexpr (SPL == 1 && !NARROW) {
+            if (P.mode == LS_TABLE) {
+                // ---------------------------------------------------------- tables d_i[v][f], sigma_i[v][f]
+                const int64_t t0 = P.toff[I.g];
+                for (int v = gwarp; v < n; v += GT / 32) {
+                    if (lane < I.nsrc) {
+                        const int32_t dv = dl0[(uint32_t)v << SH];
+                        const int64_t o = t0 + (int64_t)v * nf + I.aux + lane;
+                        P.td[o] = dv;
+                        P.ts[o] = dv == DINF ? 0ull : sl0[(uint32_t)v << SH];
+                    }
+                }
+                sync();
+            } else if (P.mode == LS_SSSP) {
+                for (int v = gwarp; v < n; v += GT / 32) {
+                    if (lane < I.nsrc) {
+                        const int32_t dv = dl0[(uint32_t)v << SH];
+                        const int64_t o = (int64_t)(I.src_off + lane) * P.dbg_n + v;
+                        P.dbg_d[o] = dv;
+                        P.dbg_s[o] = dv == DINF ? 0ull : sl0[(uint32_t)v << SH];
+                    }
+                }
+                sync();
+            }
+        }
+
+        if (P.mode == LS_SKEL) {
+            if (leader) {
+                W.hdr[slot * 4 + 0] = olen;
+                W.hdr[slot * 4 + 1] = nsteps;
+                W.hdr[slot * 4 + 2] = it;
+            }
+        } else {
+            // restore "unreached" on every touched row
+            for (int e = gwarp; e < olen; e += GT / 32) {
+                DD* pd = dl0 + ((uint32_t)order[e].u << SH);
+#pragma unroll
+                for (int s = 0; s < SPL; s++) pd[s] = DD_INF;
+            }
+        }
+        sync();
+    }
+    // with a cluster, the leader's shared memory must outlive the other CTAs' last reads
+    sync();
+}
+
+template <typename DT, int SPL, int CL, bool F, bool WT, bool M, bool NW>
+void ls_go(const LsArena& A, const LsParams& P, const LsSlots& W, const LsItem* items, int nitems, int slots,
+           cudaStream_t st) {
+    if constexpr (CL == 1) {
+        ls_kernel<DT, SPL, 1, F, WT, M, NW><<<slots, LS_THREADS, 0, st>>>(A, P, W, items, nitems);
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(slots * CL));
+        cfg.blockDim = dim3(LS_THREADS);
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, ls_kernel<DT, SPL, CL, F, WT, M, NW>, A, P, W, items, nitems);
+    }
+}
+
+template <typename DT, int SPL, int CL>
+void ls_launch_t(bool fused, bool weighted, bool mult, bool narrow, const LsArena& A, const LsParams& P,
+                 const LsSlots& W, const LsItem* items, int nitems, int slots, cudaStream_t st) {
+    if (fused) {
+        if (!weighted && narrow) ls_go<DT, SPL, CL, true, false, false, true>(A, P, W, items, nitems, slots, st);
+        else if (!weighted) ls_go<DT, SPL, CL, true, false, false, false>(A, P, W, items, nitems, slots, st);
+        else if (!mult) ls_go<DT, SPL, CL, true, true, false, false>(A, P, W, items, nitems, slots, st);
+        else ls_go<DT, SPL, CL, true, true, true, false>(A, P, W, items, nitems, slots, st);
+    } else {
+        if (!weighted && narrow) ls_go<DT, SPL, CL, false, false, false, true>(A, P, W, items, nitems, slots, st);
+        else if (!weighted) ls_go<DT, SPL, CL, false, false, false, false>(A, P, W, items, nitems, slots, st);
+        else if (!mult) ls_go<DT, SPL, CL, false, true, false, false>(A, P, W, items, nitems, slots, st);
+        else ls_go<DT, SPL, CL, false, true, true, false>(A, P, W, items, nitems, slots, st);
+    }
+}
+
+template <typename DT>
+void ls_launch_dt(int spl, int cl, bool fused, bool weighted, bool mult, bool narrow, const LsArena& A,
+                  const LsParams& P, const LsSlots& W, const LsItem* items, int nitems, int slots, cudaStream_t st) {
+    if (spl == 2) ls_launch_t<DT, 2, 1>(fused, weighted, mult, narrow, A, P, W, items, nitems, slots, st);
+    else if (cl == 4) ls_launch_t<DT, 1, 4>(fused, weighted, mult, narrow, A, P, W, items, nitems, slots, st);
+    else if (cl == 2) ls_launch_t<DT, 1, 2>(fused, weighted, mult, narrow, A, P, W, items, nitems, slots, st);
+    else ls_launch_t<DT, 1, 1>(fused, weighted, mult, narrow, A, P, W, items, nitems, slots, st);
+}
+
+}  // namespace
+
+}  // namespace bcpp

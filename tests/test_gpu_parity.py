@@ -325,6 +325,23 @@ def test_deep_unit_graphs(bc):
 
 
 
+def test_one_byte_distance_boundary(bc):
+    """Unit-weight Brandes keeps distances in one byte per source while they stay below 254: a
+    path of 254 nodes (longest distance 253) runs in one-byte rows, one of 255 nodes (254) makes
+    the batch reaching it abort and the call rerun with int32 rows; both give the closed form,
+    plain and batched."""
+    for n in (254, 255):
+        i = np.arange(n)
+        G = bc.graph_from_edgelist(gen.path(n))
+        assert rel_err(bc.brandes(G).cpu().numpy(), i * (n - 1 - i)) < FP64_TOL, n
+        assert rel_err(bc.brandes(G, precision="fp32").cpu().numpy(), i * (n - 1 - i)) < FP32_TOL, n
+    arena = bc.build_arena([gen.path(254), gen.path(255), gen.cycle(600)])
+    got = bc.brandes_batched(arena).cpu().numpy()
+    assert rel_err(got[:254], np.arange(254) * (253 - np.arange(254))) < FP64_TOL
+    assert rel_err(got[254:509], np.arange(255) * (254 - np.arange(255))) < FP64_TOL
+    assert rel_err(got[509:], np.full(600, (300 - 1) ** 2 / 2)) < FP64_TOL
+
+
 # ----------------------------------------------------------------------------- CTA clusters per batch
 def test_two_cta_clusters(bc):
     """Between 77 and 152 batches the library runs 2-CTA clusters per batch (4 with fewer,
