@@ -17,7 +17,7 @@ enum : int {
     FLAG_CAPACITY = 1,      // a per-batch list outgrew its buffer
     FLAG_INVALID = 2,       // input validation failed
     FLAG_INVALID_WHY = 3,   // first reason code of an invalid input
-    FLAG_DEPTH = 4,         // one-byte distances would overflow (the call reruns with int32 rows)
+    FLAG_DEPTH = 4,         // a one-byte distance or 32-bit path count would overflow (rerun with wide rows)
     FLAG_COUNT = 8
 };
 

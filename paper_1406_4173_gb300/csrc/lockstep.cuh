@@ -99,9 +99,10 @@ struct LsSlots {
 // per lane (1: 32-source batches, rows of 32; 2: 64-source batches, rows of 64, LS_BRANDES
 // only).  cl = CTAs per batch (1, 2 or 4; with 2 or 4 they form a thread-block cluster that
 // shares the batch's control state through distributed shared memory; spl = 1 only).
-// narrow: one-byte distance rows (unit weights, LS_BRANDES only; ignored otherwise), for slots
-// initialised to 0xff bytes; a batch deeper than 253 levels aborts with FLAG_DEPTH and
-// FLAG_CAPACITY, and the call reruns with int32 rows.
+// narrow: one-byte distance rows and 32-bit path-count rows (unit weights, LS_BRANDES only;
+// ignored otherwise), for slots whose distance rows start as 0xff bytes; a batch deeper than
+// 253 levels or with a count of 2^32 or more aborts with FLAG_DEPTH and FLAG_CAPACITY, and the
+// call reruns with int32 / uint64 rows.
 void ls_launch(bool fp32_delta, bool fused, const LsArena& A, const LsParams& P, const LsSlots& W,
                const LsItem* items, int nitems, int slots, cudaStream_t st, int spl = 1, int cl = 1,
                bool narrow = false);

@@ -33,16 +33,19 @@ __device__ __forceinline__ double recip_count(double x) {
 }
 __device__ __forceinline__ float recip_count(float x) { return 1.0f / x; }
 
-// Distance storage: int32 (DINF = unreached), or one byte per source for unit-weight Brandes
-// passes whose distances stay below 254 (255 = unreached), four times smaller rows.
+// Row storage: distances int32 (DINF = unreached) and path counts uint64, or, for unit-weight
+// Brandes passes whose distances stay below 254 and path counts below 2^32, one byte per
+// distance (255 = unreached) and 32 bits per count: rows four and two times smaller.
 template <bool NARROW>
 struct DistT {
     using T = int32_t;
+    using S = uint64_t;
     static constexpr int32_t INF = DINF;
 };
 template <>
 struct DistT<true> {
     using T = uint8_t;
+    using S = uint32_t;
     static constexpr uint8_t INF = 255;
 };
 constexpr int32_t NARROW_MAX_D = 254;   // a step at this distance would relax to an unstorable 255
@@ -85,6 +88,15 @@ __device__ __forceinline__ void ld_row(const uint64_t* p, uint64_t (&x)[SPL]) {
         x[0] = *p;
     } else {
         const ulonglong2 t = *reinterpret_cast<const ulonglong2*>(p);
+        x[0] = t.x; x[1] = t.y;
+    }
+}
+template <int SPL>
+__device__ __forceinline__ void ld_row(const uint32_t* p, uint64_t (&x)[SPL]) {
+    if constexpr (SPL == 1) {
+        x[0] = *p;
+    } else {
+        const uint2 t = *reinterpret_cast<const uint2*>(p);
         x[0] = t.x; x[1] = t.y;
     }
 }
@@ -216,10 +228,11 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
     using DD = typename DistT<NARROW>::T;
     constexpr DD DD_INF = DistT<NARROW>::INF;
     DD* d = reinterpret_cast<DD*>(W.d) + (int64_t)slot * W.cap_n * ROW;
-    uint64_t* sg = W.sg + (int64_t)slot * W.cap_n * ROW;
+    using SG = typename DistT<NARROW>::S;
+    SG* sg = reinterpret_cast<SG*>(W.sg) + (int64_t)slot * W.cap_n * ROW;
     DT* dlt = reinterpret_cast<DT*>(W.dl) + (int64_t)slot * W.cap_n * ROW;
     DD* dl0 = d + lane * SPL;                     // this lane's slice: node v at dl0[v << SH]
-    uint64_t* sl0 = sg + lane * SPL;
+    SG* sl0 = sg + lane * SPL;
     DT* cl0 = dlt + lane * SPL;
     LsEnt* order = W.order + (int64_t)slot * W.cap_order;
     int32_t* step_d = W.step_d + (int64_t)slot * W.cap_steps;
@@ -428,10 +441,20 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                             [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t*,
                                 const int32_t (*dv)[SPL], int left) { relax_group(tag, vv, ww, dv, left); });
                     }
+                    bool wide = false;
 #pragma unroll
-                    for (int s = 0; s < SPL; s++)
-                        if (pull[s]) sl0[((uint32_t)u << SH) + s] = acc[s];
+                    for (int s = 0; s < SPL; s++) {
+                        if (pull[s]) sl0[((uint32_t)u << SH) + s] = (SG)acc[s];
+                        if constexpr (NARROW) wide |= pull[s] && (acc[s] >> 32) != 0;
+                    }
                     if (__any_sync(FULL, ovf) && lane == 0) atomicOr(&P.flags[FLAG_SIGMA_OVF], 1u);
+                    if constexpr (NARROW) {
+                        // a count past 32 bits: abort the batch, the call reruns with 64-bit rows
+                        if (__any_sync(FULL, wide) && lane == 0) {
+                            atomicOr(&P.flags[FLAG_DEPTH], 1u);
+                            atomicExch(&ctl->err, 1);
+                        }
+                    }
                 }
                 e = e2;
                 cur = nxt;
