@@ -1120,6 +1120,12 @@ int pp_prepare(bcpp_ctx* c, const bcpp_graph* g, uint64_t wmax, const InCsr* Tin
     r.slots = r.nitems > 0 ? choose_slots(c, r.nitems, o.ctas_per_sm,
                                           slot_bytes(std::max(N, 1), r.nb, fp32, ef, r.spl), (int64_t)n * 16, r.cl)
                            : 1;
+    if (!r.hunits.empty() && r.nitems > 0) {
+        // with Centrality the batches run in static chunks of `slots`: make the chunks equal
+        // (128 batches on 76 slots run as 64 + 64 instead of 76 + 52)
+        const int chunks = div_up(r.nitems, r.slots);
+        r.slots = div_up(r.nitems, chunks);
+    }
     // partial sums live in the lockstep slots; combine at the end
     CK_RC(alloc_slots(c, r.ws, r.slots, std::max(N, 1), r.nb, fp32, n, r.spl, ef, false));
     r.ws.narrow = r.hunits.empty() && use_narrow(c, !r.unit);   // Centrality reads int32 rows
