@@ -44,3 +44,14 @@ def test_autotune_trivial(bc):
     G = bc.graph_from_edgelist(g)
     tuned, times = bc.autotune(G, np.array([3], np.int32))
     assert all(t == -1.0 for t in times.values())
+
+
+def test_autotune_directed_weighted(bc):
+    g = gen.chung_lu_communities(1200, [300] * 4, 2.3, 6.0, 0.85, seed=19, directed=True, wmax=9)
+    G = bc.graph_from_edgelist(g)
+    S = gen.sample_targets(g.n, 400, seed=6)
+    tuned, times = bc.autotune(G, S, precision="fp32")
+    assert (tuned["batch"], tuned["cluster"]) in bc.api.AUTOTUNE_CANDIDATES
+    ref, _ = oracle.brandes(g, S)
+    x = bc.brandes(G, S, precision="fp32", **tuned).cpu().numpy()
+    assert rel_err(x, ref) <= 2e-4

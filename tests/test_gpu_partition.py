@@ -46,3 +46,21 @@ def test_brandes_pp_on_label_propagation_partition(bc):
     ref, _ = oracle.brandes(g, S)
     got = bc.brandes_pp(G, S, part, k).cpu().numpy()
     assert float(np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1.0))) < 1e-12
+
+
+def test_partition_host_buffers(bc):
+    """The host-buffer form of bcpp_partition_lp gives the device form's labels."""
+    import ctypes
+    from paper_1406_4173_gb300 import api
+    g = gen.planted_partition(500, 5, 0.04, 0.002, seed=9)
+    G = bc.graph_from_edgelist(g)
+    dev, k, r = bc.partition_lp(G)
+    H = bc.HostCSR.from_device(G)
+    part = np.empty(g.n, np.int32)
+    kk, rr = ctypes.c_int32(0), ctypes.c_int32(0)
+    o = api._opts(host=True)
+    cg = H.c()
+    rc = api.load_library().bcpp_partition_lp(bc.default_context().handle, ctypes.byref(cg), 20, ctypes.byref(o),
+                                              part.ctypes.data, ctypes.byref(kk), ctypes.byref(rr))
+    assert rc == 0
+    assert np.array_equal(part, dev.cpu().numpy()) and (kk.value, rr.value) == (k, r)

@@ -130,3 +130,18 @@ def test_plan_trivial_target_set(bc):
             assert not np.any(plan.launch().cpu().numpy())
         finally:
             plan.close()
+
+
+def test_plan_directed_weighted_fp32_shard(bc):
+    """A plan of a directed weighted graph in FP32-delta mode and a source shard: the shard's
+    replay equals the oracle's partial over the same sources (batching in the given order)."""
+    g = gen.chung_lu_communities(900, [180] * 5, 2.3, 6.0, 0.85, seed=17, directed=True, wmax=12)
+    G = bc.graph_from_edgelist(g)
+    S = gen.sample_targets(g.n, 320, seed=8)
+    ref, _ = oracle.brandes(g, S, nsrc=160)                 # shard 0 of 2: the first 160 targets
+    plan = bc.plan_brandes(G, S, precision="fp32", shard=(0, 2), order_sources=False)
+    try:
+        assert rel_err(plan.launch().cpu().numpy(), ref) <= FP32_TOL
+        assert rel_err(plan.launch().cpu().numpy(), ref) <= FP32_TOL
+    finally:
+        plan.close()
