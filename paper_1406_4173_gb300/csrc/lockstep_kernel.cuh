@@ -224,6 +224,10 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
 #endif
     constexpr int UNROLL = SPL == 1 ? ((WEIGHTED && FUSED) ? (MULT ? 4 : 6) : (MULT ? 6 : BCPP_LS_UNROLL))
                                     : ((WEIGHTED && FUSED) ? (MULT ? 2 : 3) : (MULT ? 3 : 4));
+    // Leaf entries (no successor on any active lane) skip the backward arc scan.  Measured: 1.5%
+    // to 5% faster with one CTA per batch and on weighted graphs, slower in the clustered
+    // unit-weight instances (one more live register there costs more than the skip saves).
+    constexpr bool LEAVES = CL == 1 || WEIGHTED;
 
     using DD = typename DistT<NARROW>::T;
     constexpr DD DD_INF = DistT<NARROW>::INF;
@@ -364,6 +368,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                 }
                 if (__ballot_sync(FULL, any)) {
                     bool ovf = false;
+                    bool cand = false;   // some arc relaxed to <= its head's distance: a possible successor
                     uint64_t acc[SPL];
 #pragma unroll
                     for (int s = 0; s < SPL; s++) acc[s] = 0;
@@ -405,6 +410,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
 #pragma unroll
                             for (int s = 0; s < SPL; s++) {
                                 imp[s] = act[s] && nd < dv[k][s];
+                                if constexpr (LEAVES) cand |= act[s] && nd <= dv[k][s];
                                 anyi |= imp[s];
                             }
                             const unsigned im = __ballot_sync(FULL, anyi);
@@ -440,6 +446,13 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                         for_arc_groups<UNROLL, SPL, WEIGHTED, false>(A.col, A.w, nullptr, cur.a0, cur.deg, dl0, lane,
                             [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t*,
                                 const int32_t (*dv)[SPL], int left) { relax_group(tag, vv, ww, dv, left); });
+                    }
+                    // Every shortest-path successor of u was relaxed to at most its distance here,
+                    // so an entry without such an arc on any active lane is a leaf of all its
+                    // lanes' DAGs: the backward pass skips its arcs (sign bit of its degree).
+                    if constexpr (LEAVES) {
+                        if ((P.mode == LS_BRANDES || P.mode == LS_SKEL) && !__any_sync(FULL, cand) && lane == 0)
+                            order[e].deg = cur.deg | INT32_MIN;
                     }
                     bool wide = false;
 #pragma unroll
@@ -506,6 +519,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                         DT acc[SPL];
 #pragma unroll
                         for (int s = 0; s < SPL; s++) acc[s] = (DT)0;
+                        if (cur.deg >= 0)   // not a leaf (see the forward pass)
                         for_arc_groups<UNROLL, SPL, WEIGHTED, MULT>(A.col, A.w, A.mu, cur.a0, cur.deg, dl0, lane,
                             [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t* mk,
                                 const int32_t (*dv)[SPL], int left) {
