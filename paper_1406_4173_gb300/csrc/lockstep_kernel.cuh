@@ -451,8 +451,16 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                     // so an entry without such an arc on any active lane is a leaf of all its
                     // lanes' DAGs: the backward pass skips its arcs (sign bit of its degree).
                     if constexpr (LEAVES) {
-                        if ((P.mode == LS_BRANDES || P.mode == LS_SKEL) && !__any_sync(FULL, cand) && lane == 0)
-                            order[e].deg = cur.deg | INT32_MIN;
+                        if ((P.mode == LS_BRANDES || P.mode == LS_SKEL) && !__any_sync(FULL, cand)) {
+                            // a leaf is finished here: delta(s|u) = 0 and c(s,u) = I_{u in S} / sigma(s,u);
+                            // the backward pass skips the entry
+                            const bool tgt = P.in_s ? P.in_s[base + u] != 0 : true;
+#pragma unroll
+                            for (int s = 0; s < SPL; s++)
+                                if (act[s])
+                                    cl0[((uint32_t)u << SH) + s] = tgt ? recip_count((DT)(pull[s] ? acc[s] : 1ull)) : (DT)0;
+                            if (lane == 0) order[e].deg = cur.deg | INT32_MIN;
+                        }
                     }
                     bool wide = false;
 #pragma unroll
@@ -503,6 +511,11 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                 while (e < end) {
                     const int e2 = fetch_entry(&ctl->next, lane);
                     const LsEnt nxt = load_entry(order, e2, end);
+                    if (LEAVES && cur.deg < 0) {   // a leaf, finished by the forward pass
+                        e = e2;
+                        cur = nxt;
+                        continue;
+                    }
                     const int u = cur.u;
                     int32_t du[SPL];
                     ld_dist<SPL>(dl0 + ((uint32_t)u << SH), du);
@@ -519,7 +532,6 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                         DT acc[SPL];
 #pragma unroll
                         for (int s = 0; s < SPL; s++) acc[s] = (DT)0;
-                        if (cur.deg >= 0)   // not a leaf (see the forward pass)
                         for_arc_groups<UNROLL, SPL, WEIGHTED, MULT>(A.col, A.w, A.mu, cur.a0, cur.deg, dl0, lane,
                             [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t* mk,
                                 const int32_t (*dv)[SPL], int left) {
