@@ -567,29 +567,18 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                         const bool is_t = P.in_s ? P.in_s[base + u] != 0 : true;
                         const int64_t ix = P.bc_map ? (int64_t)P.bc_map[base + u] : base + u;
                         // The slot owns its partial sums (no other CTA adds here) and an add needs
-                        // no reply.  FP64 dependencies: each lane adds its own (no FP64 warp
-                        // reduction); FP32 ones are summed over the warp in FP64 first (measured
-                        // faster there: their adds are cheap, the extra atomics are not).
-                        double contrib = 0.0;
+                        // no reply: each lane adds its own dependency (in FP64), so no FP64 warp
+                        // reduction is needed.
 #pragma unroll
                         for (int s = 0; s < SPL; s++) {
                             if (act[s]) {
                                 const DT sd = (DT)su[s];
                                 const DT delta = sd * acc[s];
                                 cl0[((uint32_t)u << SH) + s] = is_t ? acc[s] + recip_count(sd) : acc[s];
-                                if (u != my_src[s]) {
-                                    if constexpr (sizeof(DT) == 8) {
-                                        if (bcs && delta != (DT)0) atomicAdd(&bcs[ix], (double)delta);
-                                    } else {
-                                        contrib += (double)delta;
-                                    }
-                                }
+                                if (u != my_src[s] && bcs && delta != (DT)0) atomicAdd(&bcs[ix], (double)delta);
                             }
                         }
-                        if constexpr (sizeof(DT) != 8) {
-                            const double tot = warp_sum(contrib);
-                            if (lane == 0 && bcs && tot != 0.0) atomicAdd(&bcs[ix], tot);
-                        }
+
                     }
                     e = e2;
                     cur = nxt;
