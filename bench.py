@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="skip the captured-plan (CUDA graph) measurement")
     ap.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--pp-all", action="store_true",
+                    help="also time Brandes++All (Alg. 3, all pairs of parts; S = V workloads only) once")
     return ap.parse_args()
 
 
@@ -366,6 +368,16 @@ def _run_single(args, bc, gen, g, S, ctx, flush, dev, ws, rank):
             "max_rel_err_fp32_vs_fp64": _rel(got32, ref64)}
     fp32["speedup_fp32_over_fp64_plain"] = fp32["plain_fp64_ms"] / fp32["plain_ms"]
 
+    # Brandes++All (Alg. 3): the k^2 ordered pairs of parts, once, outside the timed region
+    pp_all = None
+    if args.pp_all and nS == n:
+        flush.fill_(1)
+        x3, s3 = bc.brandes_pp_all(G, part, precision=prec, stats=True, ctx=ctx)
+        pp_all = {"teps": nS * m / (s3["ms_total"] / 1e3), "ms": s3["ms_total"], "pairs": s3["skel_edges"],
+                  "k": s3["k"], "ms_build_sk": s3["ms_build_sk"], "ms_brandes_sk": s3["ms_brandes_sk"],
+                  "ms_centrality": s3["ms_centrality"], "max_rel_err_vs_plain": _rel(x3.cpu().numpy(), a),
+                  "kernel_launches": s3["kernel_launches"]}
+
     # captured plans (CUDA graphs): plain Brandes replays the whole evaluation; the Brandes++
     # plan replays Brandes_SK + Centrality + combine on the skeleton built at plan creation
     graph = None
@@ -472,6 +484,7 @@ def _run_single(args, bc, gen, g, S, ctx, flush, dev, ws, rank):
         "max_rel_err_pp_vs_plain": pp_vs_plain,
         "rel_err_vs_oracle": err_oracle,
         "fp32_delta": fp32,
+        "brandes_pp_all": pp_all,
         "cuda_graph": graph,
         "autotune": tune,
         "wall_s": wall,
