@@ -13,15 +13,9 @@ namespace cg = cooperative_groups;
 namespace {
 
 
-// Mark head v in the bucket of distance nd (fire-and-forget: a stale mark only costs a
-// visit that finds no lane at that distance).
-__device__ __forceinline__ void mark_bucket(const LsParams& P, uint32_t* bm, uint8_t* bflag, int64_t bm_words,
-                                            int v, int32_t nd, int* maxpush) {
-    const int bk = nd % P.nb;
-    atomicOr(&bm[(int64_t)bk * bm_words + (v >> 5)], 1u << (v & 31));
-    bflag[bk] = 1;
-    atomicMax(maxpush, nd);
-}
+// Mark head v in a bucket's bitmap (fire-and-forget: a stale mark only costs a visit that
+// finds no lane at that distance).
+__device__ __forceinline__ void mark_head(uint32_t* bmk, int v) { atomicOr(&bmk[v >> 5], 1u << (v & 31)); }
 
 // 1/x for a path count x >= 1.  FP64: a single-precision seed (relative error at most 2^-23
 // after the two roundings) refined by one Newton-Raphson step r' = r + r (1 - x r), which
@@ -288,17 +282,17 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
         // ------------------------------------------------------------------ forward
         for (;;) {
             if (leader) {
+                // Integer weights: the next non-empty bucket up to the largest tentative distance.
+                // Unit weights: the levels are consecutive, and the step after the last level
+                // finds its bucket empty and leaves maxpush below D.
                 int D = ctl->D;
-                while (D <= ctl->maxpush && bflag[D % P.nb] == 0) D++;
+                if constexpr (WEIGHTED)
+                    while (D <= ctl->maxpush && bflag[D % P.nb] == 0) D++;
                 ctl->D = D;
                 ctl->done = (D > ctl->maxpush) || ctl->err;
                 if (!ctl->done) {
-                    bflag[D % P.nb] = 0;
-                    if (NARROW && D >= NARROW_MAX_D) {
-                        // deeper than one-byte distances reach: the call reruns with int32 rows
-                        atomicOr(&P.flags[FLAG_DEPTH], 1u);
-                        ctl->err = 1; ctl->done = 1;
-                    } else if (ctl->nsteps >= W.cap_steps) {
+                    if constexpr (WEIGHTED) bflag[D % P.nb] = 0;
+                    if (ctl->nsteps >= W.cap_steps) {
                         ctl->err = 1; ctl->done = 1;
                     } else {
                         step_d[ctl->nsteps] = D;
@@ -311,9 +305,12 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
             if (ctl->done) break;
             const int32_t D = ctl->D;
             const int beg = ctl->next;
+            // heads relaxed to D + w go to bucket (D + w) mod nb; w < nb, so one subtraction
+            // replaces the modulo
+            const int dmod = D % P.nb;
             // collect bucket D into the order list
             {
-                uint32_t* bmD = bm + (int64_t)(D % P.nb) * W.bm_words;
+                uint32_t* bmD = bm + (int64_t)dmod * W.bm_words;
                 const int nwords = (n + 31) >> 5;
                 const int nwr = (nwords + 31) & ~31;
                 for (int wi = gtid; wi < nwr; wi += GT) {
@@ -338,7 +335,14 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                 }
             }
             sync();
-            if (leader) ctl->end = min(ctl->pos, (int)W.cap_order);
+            if (leader) {
+                ctl->end = min(ctl->pos, (int)W.cap_order);
+                if (NARROW && D >= NARROW_MAX_D && ctl->end > beg) {
+                    // nodes deeper than one-byte distances reach: the call reruns with int32 rows
+                    atomicOr(&P.flags[FLAG_DEPTH], 1u);
+                    ctl->err = 1;
+                }
+            }
             sync();
             if (ctl->err) break;
             const int end = ctl->end;
@@ -423,8 +427,15 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                                         else pd[s] = (DD)nd;
                                     }
                                 }
-                                if (lane == __ffs(im) - 1)
-                                    mark_bucket(P, bm, bflag, W.bm_words, vv[k], nd, &ctl->maxpush);
+                                if (lane == __ffs(im) - 1) {
+                                    int bk = dmod + ww[k];
+                                    if (bk >= P.nb) bk -= P.nb;
+                                    mark_head(bm + (int64_t)bk * W.bm_words, vv[k]);
+                                    if constexpr (WEIGHTED) {
+                                        bflag[bk] = 1;
+                                        atomicMax(&ctl->maxpush, nd);
+                                    }
+                                }
                             }
                         }
                     };
@@ -481,7 +492,11 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                 cur = nxt;
             }
             sync();
-            if (leader) { ctl->nsteps++; ctl->D = D + 1; }
+            if (leader) {
+                ctl->D = D + 1;
+                if (WEIGHTED || end > beg) ctl->nsteps++;
+                if (!WEIGHTED && end > beg) ctl->maxpush = D + 1;   // try the next level
+            }
         }
         sync();
         const int nsteps = ctl->nsteps;
