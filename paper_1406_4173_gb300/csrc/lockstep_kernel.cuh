@@ -386,7 +386,8 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                             bool par[SPL], anyp = false;
 #pragma unroll
                             for (int s = 0; s < SPL; s++) {
-                                par[s] = k < left && pull[s] && dv[k][s] < D && dv[k][s] + ww[k] == D &&
+                                const bool tight = WEIGHTED ? dv[k][s] < D && dv[k][s] + ww[k] == D : dv[k][s] == D - 1;
+                                par[s] = k < left && pull[s] && tight &&
                                          (vv[k] >= nf || dv[k][s] == 0);
                                 anyp |= par[s];
                             }
@@ -399,7 +400,10 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                         for (int k = 0; k < U; k++)
 #pragma unroll
                             for (int s = 0; s < SPL; s++)
-                                if (sp[k][s]) acc[s] = madd_ck(acc[s], sp[k][s], MULT ? mk[k] : 1ull, ovf);
+                                if constexpr (NARROW)
+                                    acc[s] += sp[k][s];   // parents' counts < 2^32, fewer than 2^31 parents
+                                else if (sp[k][s])
+                                    acc[s] = madd_ck(acc[s], sp[k][s], MULT ? mk[k] : 1ull, ovf);
                     };
                     // relax the out-arcs: lower tentative distances, mark improved heads
                     auto relax_group = [&](auto tag, const int32_t* vv, const int32_t* ww, const int32_t (*dv)[SPL],
@@ -409,7 +413,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                         for (int k = 0; k < U; k++) {
                             if (k >= left) break;
                             const int64_t nd64 = (int64_t)D + ww[k];
-                            const int32_t nd = nd64 < DINF ? (int32_t)nd64 : DINF;
+                            const int32_t nd = !WEIGHTED ? D + 1 : nd64 < DINF ? (int32_t)nd64 : DINF;
                             bool imp[SPL], anyi = false;
 #pragma unroll
                             for (int s = 0; s < SPL; s++) {
@@ -558,8 +562,9 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                                     bool sc[SPL], anys = false;
 #pragma unroll
                                     for (int s = 0; s < SPL; s++) {
-                                        sc[s] = k < left && act[s] && dv[k][s] != DINF &&
-                                                (int64_t)dv[k][s] == (int64_t)D + ww[k];
+                                        sc[s] = k < left && act[s] &&
+                                                (WEIGHTED ? dv[k][s] != DINF && (int64_t)dv[k][s] == (int64_t)D + ww[k]
+                                                          : dv[k][s] == D + 1);
                                         anys |= sc[s];
                                     }
                                     DT t[SPL];
