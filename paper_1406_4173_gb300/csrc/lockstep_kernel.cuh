@@ -44,7 +44,9 @@ struct DistT<true> {
 };
 constexpr int32_t NARROW_MAX_D = 254;   // a step at this distance would relax to an unstorable 255
 
-// this lane's SPL distances of one node row, as int32 (DINF for unreached)
+// this lane's SPL distances of one node row, as int32: DINF for unreached in int32 rows; one-byte
+// rows keep their 255, which every comparison of a unit-weight pass (distances D - 1, D, D + 1
+// with D <= 253) treats like an unreached node
 template <int SPL>
 __device__ __forceinline__ void ld_dist(const int32_t* p, int32_t (&x)[SPL]) {
     if constexpr (SPL == 1) {
@@ -57,12 +59,11 @@ __device__ __forceinline__ void ld_dist(const int32_t* p, int32_t (&x)[SPL]) {
 template <int SPL>
 __device__ __forceinline__ void ld_dist(const uint8_t* p, int32_t (&x)[SPL]) {
     if constexpr (SPL == 1) {
-        const uint8_t b = *p;
-        x[0] = b == 255 ? DINF : (int32_t)b;
+        x[0] = *p;
     } else {
         const uchar2 t = *reinterpret_cast<const uchar2*>(p);
-        x[0] = t.x == 255 ? DINF : (int32_t)t.x;
-        x[1] = t.y == 255 ? DINF : (int32_t)t.y;
+        x[0] = t.x;
+        x[1] = t.y;
     }
 }
 
@@ -116,7 +117,8 @@ __device__ __forceinline__ void ld_row(const float* p, float (&x)[SPL]) {
 // One group of U arcs starting at chunk position j: heads (and weights and multiplicities)
 // are broadcast by shuffle from the chunk's registers, then the distance rows of the whole
 // group are loaded before the group is handed to f (with its size as a compile-time tag), so
-// f can issue its own dependent loads for the whole group at once.
+// f can issue its own dependent loads for the whole group at once.  Positions past the row's
+// end get distance DINF, which is never a parent's or a successor's distance.
 template <int U, int SPL, bool WEIGHTED, bool MULT, typename DD, class F>
 __device__ __forceinline__ void arc_group(int32_t mv, int32_t mw, uint64_t mm, int j, int cnt, const DD* dl0,
                                           F&& f) {
@@ -378,7 +380,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                     for (int s = 0; s < SPL; s++) acc[s] = 0;
                     // sigma(s,u) = sum over parents v (d(v) + w(v,u) = D) of sigma(s,v) * m(v,u)
                     auto pull_group = [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t* mk,
-                                          const int32_t (*dv)[SPL], int left) {
+                                          const int32_t (*dv)[SPL]) {
                         constexpr int U = decltype(tag)::value;
                         uint64_t sp[U][SPL];
 #pragma unroll
@@ -387,7 +389,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
 #pragma unroll
                             for (int s = 0; s < SPL; s++) {
                                 const bool tight = WEIGHTED ? dv[k][s] < D && dv[k][s] + ww[k] == D : dv[k][s] == D - 1;
-                                par[s] = k < left && pull[s] && tight &&
+                                par[s] = pull[s] && tight &&
                                          (vv[k] >= nf || dv[k][s] == 0);
                                 anyp |= par[s];
                             }
@@ -447,7 +449,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                         for_arc_groups<UNROLL, SPL, WEIGHTED, MULT>(A.col, A.w, A.mu, cur.a0, cur.deg, dl0, lane,
                             [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t* mk,
                                 const int32_t (*dv)[SPL], int left) {
-                                pull_group(tag, vv, ww, mk, dv, left);
+                                pull_group(tag, vv, ww, mk, dv);
                                 relax_group(tag, vv, ww, dv, left);
                             });
                     } else {
@@ -456,7 +458,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                             const int32_t ideg = (int32_t)(__ldg(irp + u + 1) - i0);
                             for_arc_groups<UNROLL, SPL, WEIGHTED, MULT>(A.icol, A.iw, A.imu, i0, ideg, dl0, lane,
                                 [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t* mk,
-                                    const int32_t (*dv)[SPL], int left) { pull_group(tag, vv, ww, mk, dv, left); });
+                                    const int32_t (*dv)[SPL], int) { pull_group(tag, vv, ww, mk, dv); });
                         }
                         for_arc_groups<UNROLL, SPL, WEIGHTED, false>(A.col, A.w, nullptr, cur.a0, cur.deg, dl0, lane,
                             [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t*,
@@ -553,7 +555,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                         for (int s = 0; s < SPL; s++) acc[s] = (DT)0;
                         for_arc_groups<UNROLL, SPL, WEIGHTED, MULT>(A.col, A.w, A.mu, cur.a0, cur.deg, dl0, lane,
                             [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t* mk,
-                                const int32_t (*dv)[SPL], int left) {
+                                const int32_t (*dv)[SPL], int) {
                                 constexpr int U = decltype(tag)::value;
                                 DT cv[U][SPL];
                                 unsigned used = 0;
@@ -562,7 +564,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                                     bool sc[SPL], anys = false;
 #pragma unroll
                                     for (int s = 0; s < SPL; s++) {
-                                        sc[s] = k < left && act[s] &&
+                                        sc[s] = act[s] &&
                                                 (WEIGHTED ? dv[k][s] != DINF && (int64_t)dv[k][s] == (int64_t)D + ww[k]
                                                           : dv[k][s] == D + 1);
                                         anys |= sc[s];
@@ -571,11 +573,13 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                                     if (anys) ld_row<SPL>(cl0 + ((uint32_t)vv[k] << SH), t);
 #pragma unroll
                                     for (int s = 0; s < SPL; s++) cv[k][s] = sc[s] ? t[s] : (DT)0;
-                                    if (__any_sync(FULL, anys)) used |= 1u << k;
+                                    if constexpr (std::is_same<DT, double>::value)
+                                        if (__any_sync(FULL, anys)) used |= 1u << k;
                                 }
+                                // FP32 adds are cheap: no vote, non-tight arcs add zero
 #pragma unroll
                                 for (int k = 0; k < U; k++)
-                                    if (used & (1u << k))
+                                    if (!std::is_same<DT, double>::value || (used & (1u << k)))
 #pragma unroll
                                         for (int s = 0; s < SPL; s++)
                                             acc[s] += MULT ? (DT)mk[k] * cv[k][s] : cv[k][s];
