@@ -169,7 +169,10 @@ int bcpp_brandes_pp_st(bcpp_ctx *ctx, const bcpp_graph *g, const int32_t *Ssrc, 
 /* Brandes++All (Sec. 5, Alg. 3): full betweenness (all ordered pairs, halved for undirected
  * graphs by default) as the sum over every ordered pair of parts (i, j) of the step above with
  * S_sc = P_i and S_dest = P_j (k^2 skeleton passes).  Exact: equals bcpp_brandes with S = V.
- * stats->skel_edges receives the number of (i, j) passes run. */
+ * The skeleton of P is built once; the pairs run four at a time on streams and workspace of the
+ * call's own (created and destroyed inside it, after the ctx stream's earlier work), and the
+ * call returns when they are done.  stats->skel_edges receives the number of (i, j) passes run;
+ * the phase times are summed over the pairs. */
 int bcpp_brandes_pp_all(bcpp_ctx *ctx, const bcpp_graph *g, const int32_t *part, int32_t k,
                         const bcpp_opts *opts, double *bc_out, bcpp_stats *stats);
 

@@ -4,6 +4,7 @@
 // calls of the same size do not allocate.
 #include <algorithm>
 #include <cstring>
+#include <memory>
 #include <numeric>
 #include <vector>
 
@@ -408,25 +409,60 @@ int alloc_slots(bcpp_ctx* c, SlotWs& S, int slots, int64_t cap_n, int nb, bool f
     return init ? init_slots(c, S) : BCPP_OK;
 }
 
+// Accumulated device time of [start, stop) intervals on the context's stream.  A lazy timer
+// does not wait at stop: it keeps each interval's events and adds them up in resolve(), so the
+// host can go on queueing work.
 struct Timer {
     bcpp_ctx* c;
     cudaEvent_t a, b;
     float acc = 0.f;
-    explicit Timer(bcpp_ctx* ctx) : c(ctx) {
+    bool lazy = false;
+    cudaEvent_t la = nullptr;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> iv;
+    explicit Timer(bcpp_ctx* ctx, bool lazy_ = false) : c(ctx), lazy(lazy_) {
         cudaEventCreate(&a);
         cudaEventCreate(&b);
     }
     ~Timer() {
+        resolve();
+        if (la) cudaEventDestroy(la);
         cudaEventDestroy(a);
         cudaEventDestroy(b);
     }
-    void start() { cudaEventRecord(a, c->stream); }
+    void start() {
+        if (lazy) {
+            if (!la) cudaEventCreate(&la);
+            cudaEventRecord(la, c->stream);
+            return;
+        }
+        cudaEventRecord(a, c->stream);
+    }
     void stop() {
+        if (lazy) {
+            cudaEvent_t e = nullptr;
+            if (!la || cudaEventCreate(&e) != cudaSuccess) return;
+            cudaEventRecord(e, c->stream);
+            iv.push_back({la, e});
+            la = nullptr;
+            return;
+        }
         cudaEventRecord(b, c->stream);
         cudaEventSynchronize(b);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, a, b);
         acc += ms;
+    }
+    float resolve() {
+        for (auto& x : iv) {
+            float ms = 0.f;
+            if (cudaEventSynchronize(x.second) == cudaSuccess && cudaEventElapsedTime(&ms, x.first, x.second) == cudaSuccess)
+                acc += ms;
+            cudaEventDestroy(x.first);
+            cudaEventDestroy(x.second);
+        }
+        iv.clear();
+        cudaGetLastError();
+        return acc;
     }
 };
 
@@ -498,6 +534,39 @@ constexpr int ORDER_MAX_LEVELS = 4096;   // deeper graphs keep plain level order
 __global__ void hub_src_kernel(const unsigned long long* best, int32_t* src) {
     src[0] = (int32_t)(0xffffffffu - (uint32_t)(best[0] & 0xffffffffull));
 }
+// Breadth-first levels from one source over unit-weight arcs, as the lockstep kernel's LS_SSSP
+// mode would give them (DINF = unreached), but with the whole GPU on each level: warp w looks
+// at nodes [32w, 32w + 32) and scans the arcs of those at level L with all its lanes;
+// unreached heads get L + 1 (concurrent writers all write L + 1).  more[L] = some head was
+// reached; a level whose predecessor reached nothing returns at once.
+__global__ void bfs_seed_kernel(int32_t* level, const int32_t* src, int32_t* more, int32_t nmore) {
+    level[src[0]] = 0;
+    for (int i = 0; i < nmore; i++) more[i] = 0;
+}
+__global__ void bfs_level_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col, int32_t n,
+                                 int32_t* level, int32_t L, int32_t* more) {
+    if (L > 0 && more[L - 1] == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    bool found = false;
+    for (int64_t b0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; b0 < n; b0 += nw * 32) {
+        const int64_t v = b0 + lane;
+        unsigned m = __ballot_sync(FULL, v < n && level[v] == L);
+        while (m) {
+            const int64_t u = b0 + (__ffs(m) - 1);
+            m &= m - 1;
+            const int64_t a1 = rp[u + 1];
+            for (int64_t a = rp[u] + lane; a < a1; a += 32) {
+                const int32_t w = col[a];
+                if (level[w] == DINF) {
+                    level[w] = L + 1;
+                    found = true;
+                }
+            }
+        }
+    }
+    if (__any_sync(FULL, found) && lane == 0) more[L] = 1;
+}
 // level histogram (levels >= cap counted at cap) and the deepest level
 __global__ void level_hist_kernel(const int32_t* level, int32_t n, int32_t cap, int32_t* cnt, int32_t* maxl) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
@@ -540,7 +609,7 @@ int order_prepare(bcpp_ctx* c, const bcpp_graph* g, const int64_t* irp, const in
                   uint64_t wmax, const int32_t* S, int64_t ns, const int32_t* part, int32_t k, OrderWs& w) {
     const int32_t n = g->n;
     w.ns = ns; w.n = n; w.k = k; w.S = S; w.part = part;
-    // levels from the hub: one source, one 4-CTA cluster
+    // levels from the hub (the node of largest degree)
     DBuf<unsigned long long> best(c, 1);
     DBuf<int32_t> level(c, n), src(c, 1), cnt(c, ORDER_MAX_LEVELS + 1), maxl(c, 1);
     DBuf<uint64_t> lsig(c, n);
@@ -552,29 +621,53 @@ int order_prepare(bcpp_ctx* c, const bcpp_graph* g, const int64_t* irp, const in
     const int64_t hoff[2] = {0, n};
     CK_RC(to_dev(c, item.p, &hi, 1));
     CK_RC(to_dev(c, node_off.p, hoff, 2));
-    const int nb = g->w ? (int)wmax + 1 : 2;
-    SlotWs ws;
-    CK_RC(alloc_slots(c, ws, 1, n, nb, false, 0, 1, entry_factor(c, g->w != nullptr, 1)));
-    LsArena A{};
-    A.rp = g->row_ptr; A.col = g->col; A.w = (const int32_t*)g->w;
-    A.irp = irp; A.icol = icol; A.iw = (const int32_t*)iw;
-    A.node_off = node_off.p;
-    LsParams P{};
-    P.mode = LS_SSSP;
-    P.nb = nb;
-    P.srcs = src.p;
-    P.dbg_d = level.p;
-    P.dbg_s = lsig.p;
-    P.dbg_n = n;
-    P.item_counter = ws.counter.p;
-    P.flags = c->flags;
     const unsigned nblk = (unsigned)std::min<int64_t>((n + 255) / 256, 8192);
     CK_CUDA(cudaMemsetAsync(best.p, 0, sizeof(unsigned long long), c->stream));
     hub_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, c->stream>>>(g->row_ptr, n, best.p);
     hub_src_kernel<<<1, 1, 0, c->stream>>>(best.p, src.p);
     c->launches += 2;
-    ls_launch(false, !g->directed, A, P, ws.W, item.p, 1, 1, c->stream, 1, 4);
-    c->launches++;
+    // Unit weights: level-synchronous breadth-first search over the whole GPU, 8 levels per
+    // host check; a graph deeper than BFS_LEVELS levels falls back to the lockstep kernel.
+    constexpr int32_t BFS_LEVELS = 256;
+    bool have_levels = false;
+    if (!g->w) {
+        DBuf<int32_t> more(c, BFS_LEVELS);
+        CK_ALLOC(more);
+        fill_i32(level.p, DINF, n, c->stream);
+        bfs_seed_kernel<<<1, 1, 0, c->stream>>>(level.p, src.p, more.p, BFS_LEVELS);
+        c->launches += 2;
+        const unsigned bblk = (unsigned)std::min<int64_t>(((int64_t)n + 255) / 256, (int64_t)c->num_sms * 8);
+        for (int32_t L0 = 0; L0 < BFS_LEVELS && !have_levels; L0 += 8) {
+            for (int32_t L = L0; L < L0 + 8; L++) {
+                bfs_level_kernel<<<bblk, 256, 0, c->stream>>>(g->row_ptr, g->col, n, level.p, L, more.p);
+                c->launches++;
+            }
+            int32_t last = 1;
+            CK_RC(to_host(c, &last, more.p + L0 + 7, 1));
+            have_levels = last == 0;
+        }
+    }
+    if (!have_levels) {
+        // levels (or weighted distances) from the lockstep kernel: one source, one 4-CTA cluster
+        const int nb = g->w ? (int)wmax + 1 : 2;
+        SlotWs ws;
+        CK_RC(alloc_slots(c, ws, 1, n, nb, false, 0, 1, entry_factor(c, g->w != nullptr, 1)));
+        LsArena A{};
+        A.rp = g->row_ptr; A.col = g->col; A.w = (const int32_t*)g->w;
+        A.irp = irp; A.icol = icol; A.iw = (const int32_t*)iw;
+        A.node_off = node_off.p;
+        LsParams P{};
+        P.mode = LS_SSSP;
+        P.nb = nb;
+        P.srcs = src.p;
+        P.dbg_d = level.p;
+        P.dbg_s = lsig.p;
+        P.dbg_n = n;
+        P.item_counter = ws.counter.p;
+        P.flags = c->flags;
+        ls_launch(false, !g->directed, A, P, ws.W, item.p, 1, 1, c->stream, 1, 4);
+        c->launches++;
+    }
     // level sizes
     CK_CUDA(cudaMemsetAsync(cnt.p, 0, (ORDER_MAX_LEVELS + 1) * sizeof(int32_t), c->stream));
     CK_CUDA(cudaMemsetAsync(maxl.p, 0, sizeof(int32_t), c->stream));
@@ -842,12 +935,14 @@ struct Skeleton {
     DBuf<uint64_t> skmu;
     std::vector<int32_t> h_pstart, h_nf, h_skbase;
     std::vector<int64_t> h_toff;
+    const Skeleton* shared = nullptr;   // tables owned by another skeleton (same parts, same order)
     SkTables tables() const {
+        const Skeleton& o = shared ? *shared : *this;
         SkTables T;
         T.pstart = pstart.p; T.nf = nf.p; T.toff = toff.p;
-        T.td = td.p; T.ts = ts.p;
-        T.tdr = tdr.p ? tdr.p : td.p;
-        T.tsr = tsr.p ? tsr.p : ts.p;
+        T.td = o.td.p; T.ts = o.ts.p;
+        T.tdr = o.tdr.p ? o.tdr.p : o.td.p;
+        T.tsr = o.tsr.p ? o.tsr.p : o.ts.p;
         return T;
     }
 };
@@ -872,8 +967,12 @@ int build_local_csr(bcpp_ctx* c, const Skeleton& K, const int64_t* rp, const int
     return BCPP_OK;
 }
 
+// reuse (may be null): a skeleton of the same graph built for `part` without singletons.  Every
+// part that keeps its nodes under P' keeps its frontiers, its local order and so its Dijkstra_SK
+// tables, so they are read from `reuse` instead of being recomputed (Alg. 3 builds the
+// skeleton once and only expands P_i and P_j per pair).
 int build_sk(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS_eff, const int32_t* part, int32_t k,
-             uint64_t wmax, const InCsr* Tin, const bcpp_opts& o, Skeleton& K) {
+             uint64_t wmax, const InCsr* Tin, const bcpp_opts& o, Skeleton& K, const Skeleton* reuse = nullptr) {
     const int32_t n = g->n;
     const bool fp32 = o.precision == BCPP_FP32_DELTA;
     (void)fp32;
@@ -911,10 +1010,20 @@ int build_sk(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS_eff,
     CK_RC(to_host(c, K.h_nf.data(), K.nf.p, kp));
     CK_RC(sync_flags(c));
     if (c->hflags[FLAG_INVALID]) return BCPP_EINVAL;
+    // tables of the parts that keep their nodes can come from `reuse` if nothing else differs
+    if (reuse && reuse->kp == k && reuse->n == n) {
+        for (int32_t i = 0; i < k && reuse; i++) {
+            const int32_t sz = K.h_pstart[i + 1] - K.h_pstart[i];
+            const int32_t sz0 = reuse->h_pstart[i + 1] - reuse->h_pstart[i];
+            if (sz > 0 && (sz != sz0 || K.h_nf[i] != reuse->h_nf[i])) reuse = nullptr;
+        }
+    } else {
+        reuse = nullptr;
+    }
     // host: skeleton ids, table offsets, statistics
     K.h_skbase.resize(kp);
     K.h_toff.resize((size_t)kp + 1);
-    int64_t N = 0, tofs = 0;
+    int64_t N = 0, tofs = 0, entries = 0;
     int32_t maxpart_tab = 0;
     K.lcs = 0;
     K.k_nonempty = 0;
@@ -922,9 +1031,10 @@ int build_sk(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS_eff,
         const int32_t sz = K.h_pstart[i + 1] - K.h_pstart[i];
         K.h_skbase[i] = (int32_t)N;
         N += K.h_nf[i];
-        K.h_toff[i] = tofs;
+        K.h_toff[i] = reuse ? (i < k ? reuse->h_toff[i] : 0) : tofs;
         if (sz >= 2 && K.h_nf[i] >= 1) {
-            tofs += (int64_t)sz * K.h_nf[i];
+            if (!reuse) tofs += (int64_t)sz * K.h_nf[i];
+            entries += (int64_t)sz * K.h_nf[i];
             maxpart_tab = std::max(maxpart_tab, sz);
         }
         K.lcs = std::max(K.lcs, sz);
@@ -932,7 +1042,8 @@ int build_sk(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS_eff,
     }
     K.h_toff[kp] = tofs;
     K.N = (int32_t)N;
-    K.table_entries = tofs;
+    K.table_entries = entries;
+    K.shared = reuse;
     CK_ALLOC(K.skbase.alloc(c, kp));
     CK_ALLOC(K.toff.alloc(c, (int64_t)kp + 1));
     CK_ALLOC(K.sknode.alloc(c, std::max<int64_t>(N, 1)));
@@ -940,11 +1051,13 @@ int build_sk(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS_eff,
     CK_RC(to_dev(c, K.toff.p, K.h_toff.data(), (int64_t)kp + 1));
     sk_local_ids(n, K.pnodes.p, K.partp.p, K.pstart.p, K.nf.p, K.skbase.p, K.loc.p, K.skid.p, K.sknode.p, c->stream);
     c->launches++;
-    CK_ALLOC(K.td.alloc(c, std::max<int64_t>(tofs, 1)));
-    CK_ALLOC(K.ts.alloc(c, std::max<int64_t>(tofs, 1)));
-    if (g->directed) {
-        CK_ALLOC(K.tdr.alloc(c, std::max<int64_t>(tofs, 1)));
-        CK_ALLOC(K.tsr.alloc(c, std::max<int64_t>(tofs, 1)));
+    if (!reuse) {
+        CK_ALLOC(K.td.alloc(c, std::max<int64_t>(tofs, 1)));
+        CK_ALLOC(K.ts.alloc(c, std::max<int64_t>(tofs, 1)));
+        if (g->directed) {
+            CK_ALLOC(K.tdr.alloc(c, std::max<int64_t>(tofs, 1)));
+            CK_ALLOC(K.tsr.alloc(c, std::max<int64_t>(tofs, 1)));
+        }
     }
     CK_ALLOC(K.pstart64.alloc(c, (int64_t)kp + 1));
     i64_from_i32_kernel<<<(unsigned)std::min<int64_t>(((int64_t)kp + 256) / 256, 8192), 256, 0, c->stream>>>(
@@ -1075,7 +1188,8 @@ struct PpRun {
 
 int pp_prepare(bcpp_ctx* c, const bcpp_graph* g, uint64_t wmax, const InCsr* Tin, const int32_t* Ssing,
                int32_t nsing, const int32_t* Ssrc, int32_t nsrc, const uint8_t* dflag, const int32_t* part, int32_t k,
-               const bcpp_opts& o, double scale, double* bc_out, PpRun& r, Timer* tb) {
+               const bcpp_opts& o, double scale, double* bc_out, PpRun& r, Timer* tb,
+               const Skeleton* reuse = nullptr) {
     const int32_t n = g->n;
     const bool fp32 = o.precision == BCPP_FP32_DELTA;
     const int64_t ns = nsrc;
@@ -1083,7 +1197,7 @@ int pp_prepare(bcpp_ctx* c, const bcpp_graph* g, uint64_t wmax, const InCsr* Tin
     // Step 1: Build_SK on P' (every node of Ssing a singleton part)
     if (tb) tb->start();
     Skeleton& K = r.K;
-    CK_RC(build_sk(c, g, Ssing, nsing, part, k, wmax, Tin, o, K));
+    CK_RC(build_sk(c, g, Ssing, nsing, part, k, wmax, Tin, o, K, reuse));
     if (tb) tb->stop();
     const int32_t N = K.N;
     // targets in batch order (grouped by their original part when requested), as skeleton ids
@@ -1247,9 +1361,9 @@ void pp_fill_stats(const PpRun& r, bcpp_stats* st) {
 int brandes_pp_core(bcpp_ctx* c, const bcpp_graph* g, uint64_t wmax, const InCsr* Tin, const int32_t* Ssing,
                     int32_t nsing, const int32_t* Ssrc, int32_t nsrc, const uint8_t* dflag, const int32_t* part,
                     int32_t k, const bcpp_opts& o, double scale, double* bc_out, bcpp_stats* st, Timer& tb, Timer& tbr,
-                    Timer& tce) {
+                    Timer& tce, const Skeleton* reuse = nullptr) {
     PpRun r;
-    CK_RC(pp_prepare(c, g, wmax, Tin, Ssing, nsing, Ssrc, nsrc, dflag, part, k, o, scale, bc_out, r, &tb));
+    CK_RC(pp_prepare(c, g, wmax, Tin, Ssing, nsing, Ssrc, nsrc, dflag, part, k, o, scale, bc_out, r, &tb, reuse));
     CK_RC(pp_emit(c, r, &tbr, &tce));
     pp_fill_stats(r, st);
     return BCPP_OK;
@@ -1397,6 +1511,47 @@ int brandes_pp_st_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* Ssrc, int
 // Brandes++All (Alg. 3): for every ordered pair of parts (i, j), Brandes_SK with S_sc = P_i
 // and S_dest = P_j on the skeleton where both parts are expanded into singletons, then
 // Centrality; C(v) is the sum of the k^2 partial results (Sec. 5).
+// A context of its own (stream, workspace pool, status flags) for one lane of concurrent work.
+struct SubCtx {
+    bcpp_ctx* c = nullptr;
+    cudaStream_t st = nullptr;
+    SubCtx() = default;
+    SubCtx(const SubCtx&) = delete;
+    SubCtx& operator=(const SubCtx&) = delete;
+    ~SubCtx() {
+        if (c) bcpp_destroy(c);   // waits for the stream
+        if (st) cudaStreamDestroy(st);
+    }
+    int open(const bcpp_ctx* parent) {
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            st = nullptr;
+            cudaGetLastError();
+            return BCPP_ECUDA;
+        }
+        CK_RC(bcpp_create(&c, st));
+        c->order_factor = parent->order_factor;
+        return reset_flags(c);
+    }
+};
+
+// One lane of Alg. 3's pair loop: its context, its pair buffers and its running sums.
+struct PairLane {
+    SubCtx sc;                      // destroyed last: the buffers below return to its pool first
+    DBuf<int32_t> pair;
+    DBuf<uint8_t> dflag;
+    DBuf<double> tmp, sum, comp;
+    std::unique_ptr<Timer> tb, tbr, tce;
+    int64_t calls = 0;
+};
+
+// Brandes++All (Alg. 3): Build_SK once on P, then for every ordered pair (i, j) of non-empty
+// parts Brandes_SK with S_sc = P_i and S_dest = P_j (both expanded into singletons) and
+// Centrality, summed into C(v).  The pairs are independent: they run round-robin on
+// ALL_LANES contexts of their own (streams, workspace), so that one pair's small Brandes_SK
+// launch overlaps other pairs' work; each lane keeps a compensated running sum and the lanes
+// are added in a fixed order, so the result does not depend on timing.
+constexpr int ALL_LANES = 4;
+
 int brandes_pp_all_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* part, int32_t k, const bcpp_opts& o,
                        double* bc_out, bcpp_stats* st) {
     CK_RC(check_graph_struct(g));
@@ -1418,40 +1573,92 @@ int brandes_pp_all_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* part, in
     for (int32_t i = 0; i < k; i++) off[i + 1] += off[i];
     std::vector<int32_t> byp(n), fill(off.begin(), off.end() - 1);
     for (int32_t v = 0; v < n; v++) byp[fill[hp[v]]++] = v;
-    DBuf<int32_t> dbyp(c, n), pair(c, n);
-    DBuf<uint8_t> dflag(c, n);
-    DBuf<double> tmp(c, n), sum(c, n), comp(c, n);
-    CK_ALLOC(dbyp); CK_ALLOC(pair); CK_ALLOC(dflag); CK_ALLOC(tmp); CK_ALLOC(sum); CK_ALLOC(comp);
+    DBuf<int32_t> dbyp(c, n);
+    DBuf<double> sum(c, n), comp(c, n);
+    CK_ALLOC(dbyp); CK_ALLOC(sum); CK_ALLOC(comp);
     CK_RC(to_dev(c, dbyp.p, byp.data(), n));
     CK_CUDA(cudaMemsetAsync(sum.p, 0, (size_t)n * sizeof(double), c->stream));
     CK_CUDA(cudaMemsetAsync(comp.p, 0, (size_t)n * sizeof(double), c->stream));
     InCsr Tin;
     if (g->directed) CK_RC(build_in_csr(c, g, Tin));
-    Timer tb(c), tbr(c), tce(c);
+    Timer tb(c);
     const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 8192);
-    int64_t calls = 0;
+    // Build_SK once on P: every pair reads the tables of the parts it keeps from it
+    Skeleton K0;
+    tb.start();
+    CK_RC(build_sk(c, g, nullptr, 0, part, k, wmax, &Tin, o, K0));
+    tb.stop();
+    // the lanes start after everything above
+    struct Ev {
+        cudaEvent_t e = nullptr;
+        ~Ev() { if (e) cudaEventDestroy(e); }
+    } ready;
+    CK_CUDA(cudaEventCreateWithFlags(&ready.e, cudaEventDisableTiming));
+    CK_CUDA(cudaEventRecord(ready.e, c->stream));
+    PairLane lanes[ALL_LANES];
+    struct JoinMain {   // destroyed before the lanes: nothing queued here reads their buffers after
+        cudaStream_t s;
+        ~JoinMain() { cudaStreamSynchronize(s); }
+    } join_main{c->stream};
+    for (PairLane& L : lanes) {
+        CK_RC(L.sc.open(c));
+        bcpp_ctx* lc = L.sc.c;
+        CK_CUDA(cudaStreamWaitEvent(lc->stream, ready.e, 0));
+        CK_ALLOC(L.pair.alloc(lc, n)); CK_ALLOC(L.dflag.alloc(lc, n));
+        CK_ALLOC(L.tmp.alloc(lc, n)); CK_ALLOC(L.sum.alloc(lc, n)); CK_ALLOC(L.comp.alloc(lc, n));
+        CK_CUDA(cudaMemsetAsync(L.sum.p, 0, (size_t)n * sizeof(double), lc->stream));
+        CK_CUDA(cudaMemsetAsync(L.comp.p, 0, (size_t)n * sizeof(double), lc->stream));
+        L.tb.reset(new Timer(lc, true));
+        L.tbr.reset(new Timer(lc, true));
+        L.tce.reset(new Timer(lc, true));
+    }
+    int64_t p = 0;
     for (int32_t j = 0; j < k; j++) {
         const int32_t nj = (int32_t)(off[j + 1] - off[j]);
         if (nj == 0) continue;
-        part_flag_kernel<<<blocks, 256, 0, c->stream>>>(part, n, j, dflag.p);
-        c->launches++;
         for (int32_t i = 0; i < k; i++) {
             const int32_t ni = (int32_t)(off[i + 1] - off[i]);
             if (ni == 0 || (i == j && ni < 2)) continue;
+            PairLane& L = lanes[p++ % ALL_LANES];
+            bcpp_ctx* lc = L.sc.c;
+            part_flag_kernel<<<blocks, 256, 0, lc->stream>>>(part, n, j, L.dflag.p);
+            lc->launches++;
             // singletons: P_i followed by P_j (P_i alone when i == j)
-            CK_CUDA(cudaMemcpyAsync(pair.p, dbyp.p + off[i], (size_t)ni * 4, cudaMemcpyDeviceToDevice, c->stream));
+            CK_CUDA(cudaMemcpyAsync(L.pair.p, dbyp.p + off[i], (size_t)ni * 4, cudaMemcpyDeviceToDevice, lc->stream));
             int32_t nsing = ni;
             if (i != j) {
-                CK_CUDA(cudaMemcpyAsync(pair.p + ni, dbyp.p + off[j], (size_t)nj * 4, cudaMemcpyDeviceToDevice,
-                                        c->stream));
+                CK_CUDA(cudaMemcpyAsync(L.pair.p + ni, dbyp.p + off[j], (size_t)nj * 4, cudaMemcpyDeviceToDevice,
+                                        lc->stream));
                 nsing += nj;
             }
-            CK_RC(brandes_pp_core(c, g, wmax, &Tin, pair.p, nsing, pair.p, ni, dflag.p, part, k, o, 1.0, tmp.p,
-                                  nullptr, tb, tbr, tce));
-            accumulate_kernel<<<blocks, 256, 0, c->stream>>>(tmp.p, n, sum.p, comp.p);
-            c->launches++;
-            calls++;
+            CK_RC(brandes_pp_core(lc, g, wmax, &Tin, L.pair.p, nsing, L.pair.p, ni, L.dflag.p, part, k, o, 1.0,
+                                  L.tmp.p, nullptr, *L.tb, *L.tbr, *L.tce, &K0));
+            accumulate_kernel<<<blocks, 256, 0, lc->stream>>>(L.tmp.p, n, L.sum.p, L.comp.p);
+            lc->launches++;
+            L.calls++;
         }
+    }
+    // join: the lanes' sums (and compensations) in lane order, and their status flags
+    uint32_t merged[FLAG_COUNT] = {};
+    float ms_b = tb.acc, ms_br = 0.f, ms_ce = 0.f;
+    int64_t calls = 0;
+    for (PairLane& L : lanes) {
+        bcpp_ctx* lc = L.sc.c;
+        CK_RC(sync_flags(lc));   // waits for the lane's stream
+        for (int f = 0; f < FLAG_COUNT; f++) merged[f] |= lc->hflags[f];
+        accumulate_kernel<<<blocks, 256, 0, c->stream>>>(L.sum.p, n, sum.p, comp.p);
+        accumulate_kernel<<<blocks, 256, 0, c->stream>>>(L.comp.p, n, sum.p, comp.p);
+        c->launches += 2 + lc->launches;
+        ms_b += L.tb->resolve();
+        ms_br += L.tbr->resolve();
+        ms_ce += L.tce->resolve();
+        calls += L.calls;
+    }
+    if (merged[FLAG_INVALID] | merged[FLAG_CAPACITY] | merged[FLAG_SIGMA_OVF] | merged[FLAG_DEPTH]) {
+        CK_RC(sync_flags(c));
+        for (int f = 0; f < FLAG_COUNT; f++) merged[f] |= c->hflags[f];
+        CK_CUDA(cudaMemcpyAsync(c->flags, merged, sizeof(merged), cudaMemcpyHostToDevice, c->stream));
+        CK_CUDA(cudaStreamSynchronize(c->stream));
     }
     const bool halve = !g->directed && o.halve_undirected != 0;
     finish_kernel<<<blocks, 256, 0, c->stream>>>(sum.p, comp.p, n, halve ? 0.5 : 1.0, bc_out);
@@ -1460,9 +1667,9 @@ int brandes_pp_all_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* part, in
     tt.stop();
     if (st) {
         st->k = k;
-        st->ms_build_sk = tb.acc;
-        st->ms_brandes_sk = tbr.acc;
-        st->ms_centrality = tce.acc;
+        st->ms_build_sk = ms_b;
+        st->ms_brandes_sk = ms_br;
+        st->ms_centrality = ms_ce;
         st->ms_total = tt.acc;
         st->skel_edges = calls;   // number of (i, j) Brandes_SK runs
     }
