@@ -1548,8 +1548,9 @@ struct PairLane {
 // parts Brandes_SK with S_sc = P_i and S_dest = P_j (both expanded into singletons) and
 // Centrality, summed into C(v).  The pairs are independent: they run round-robin on
 // ALL_LANES contexts of their own (streams, workspace), so that one pair's small Brandes_SK
-// launch overlaps other pairs' work; each lane keeps a compensated running sum and the lanes
-// are added in a fixed order, so the result does not depend on timing.
+// launch overlaps other pairs' work; each pair goes to a fixed lane, each lane keeps a
+// compensated running sum and the lanes are added in a fixed order, so the combination does
+// not depend on which pair finishes first.
 constexpr int ALL_LANES = 4;
 
 int brandes_pp_all_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* part, int32_t k, const bcpp_opts& o,
