@@ -380,3 +380,21 @@ def test_brandes_pp_all_equals_brandes(bc, directed, wmax):
     assert rel_err(got.cpu().numpy(), ref) < FP64_TOL
     k = int(g.part.max()) + 1
     assert st["skel_edges"] == k * k
+
+
+def test_brandes_pp_all_uneven_parts(bc):
+    """Alg. 3 with an empty part and a one-node part, in both precisions: the pairs that run
+    (every ordered pair of non-empty parts except a one-node part with itself) are counted, and
+    the sum equals plain Brandes."""
+    g = gen.planted_partition(300, 6, 0.06, 0.004, seed=65)
+    part = np.asarray(g.part, np.int32).copy()
+    part[part == 5] = 7          # part 5 left empty
+    part[10] = 6                 # part 6 holds one node
+    G = bc.graph_from_edgelist(g)
+    ref, _ = oracle.brandes(g)
+    got, st = bc.brandes_pp_all(G, part, k=8, stats=True)
+    assert rel_err(got.cpu().numpy(), ref) < FP64_TOL
+    nonempty = len(np.unique(part))
+    assert st["skel_edges"] == nonempty * nonempty - 1
+    got32 = bc.brandes_pp_all(G, part, k=8, precision="fp32").cpu().numpy()
+    assert rel_err(got32, ref) < FP32_TOL
