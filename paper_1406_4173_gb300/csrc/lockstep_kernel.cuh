@@ -214,11 +214,15 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
     const int slot = blockIdx.x / CL;
     constexpr int ROW = 32 * SPL;                 // sources per node row
     constexpr int SH = SPL == 1 ? 5 : 6;          // log2(ROW)
-    // arcs handled per group (bounded by the 64 registers of two resident 512-thread CTAs)
+    // arcs handled per group (bounded by the 64 registers of two resident 512-thread CTAs).
+    // Unit weights: groups of 4 in FP64 and with one CTA per batch, 8 in clustered FP32-delta
+    // instances (same-box A/B on the unit-weight workloads; integer weights keep 8).
 #ifndef BCPP_LS_UNROLL
 #define BCPP_LS_UNROLL 8
 #endif
-    constexpr int UNROLL = SPL == 1 ? ((WEIGHTED && FUSED) ? (MULT ? 4 : 6) : (MULT ? 6 : BCPP_LS_UNROLL))
+    constexpr int UNIT_UNROLL = (std::is_same<DT, double>::value || CL == 1) ? 4 : BCPP_LS_UNROLL;
+    constexpr int UNROLL = SPL == 1 ? ((WEIGHTED && FUSED) ? (MULT ? 4 : 6)
+                                                           : (MULT ? 6 : (WEIGHTED ? BCPP_LS_UNROLL : UNIT_UNROLL)))
                                     : ((WEIGHTED && FUSED) ? (MULT ? 2 : 3) : (MULT ? 3 : 4));
     // Leaf entries (no successor on any active lane) skip the backward arc scan.  Measured: 1.5%
     // to 5% faster with one CTA per batch and on weighted graphs, slower in the clustered
