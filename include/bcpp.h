@@ -108,6 +108,14 @@ typedef struct {
 /* Fill opts with the defaults listed above. */
 void bcpp_default_opts(bcpp_opts *opts);
 
+/* The source positions [*s0, *s1) of shard `index` of `count` over `num_sources` sources in
+ * batch order: [num_sources * index / count, num_sources * (index + 1) / count), the rule that
+ * opts.shard_index / shard_count apply (Alg. 1 sums over the sources s in S independently, so
+ * the shards' partial sums add up to the full result).  count <= 1 gives [0, num_sources).
+ * Host-only (no device work, no context).  BCPP_EINVAL for num_sources < 0, count > 1 with
+ * index outside [0, count), or a NULL output pointer. */
+int bcpp_shard_bounds(int64_t num_sources, int32_t index, int32_t count, int64_t *s0, int64_t *s1);
+
 /* Message for a status code (static string). */
 const char *bcpp_strerror(int status);
 
@@ -216,6 +224,18 @@ int bcpp_skeleton(bcpp_ctx *ctx, const bcpp_graph *g, const int32_t *S, int32_t 
 int bcpp_autotune(bcpp_ctx *ctx, const bcpp_graph *g, const int32_t *S, int32_t nS,
                   const bcpp_opts *opts, bcpp_opts *tuned, float *ms_out);
 
+/* Autotuner for bcpp_brandes_batched (many independent graphs in one launch): runs the batched
+ * evaluation of the whole arena once per candidate -- source batches of 32 or 64 (`batch`) with
+ * two or one resident batches per SM (`ctas_per_sm`), in the order (32, 2), (64, 2), (32, 1),
+ * (64, 1) -- and writes into *tuned a copy of *opts (NULL: defaults) with the fastest candidate's
+ * `batch` and `ctas_per_sm`.  A batched graph's batches are small and numerous, so every batch
+ * runs on one CTA (no cluster candidates).  ms_out (host, may be NULL) receives the candidates'
+ * kernel times in milliseconds [BCPP_AUTOTUNE_BATCHED_CANDIDATES] (-1 for an empty arena).
+ * Arguments and errors as for bcpp_brandes_batched; opts->host_buffers must be 0. */
+#define BCPP_AUTOTUNE_BATCHED_CANDIDATES 4
+int bcpp_autotune_batched(bcpp_ctx *ctx, int32_t num_graphs, const int64_t *graph_node_ptr,
+                          const bcpp_graph *arena, const bcpp_opts *opts, bcpp_opts *tuned, float *ms_out);
+
 /* ---------------------------------------------------------------------------------------
  * Captured plans (CUDA graphs).  The paper has no counterpart: this is the repeated-evaluation
  * form of bcpp_brandes and bcpp_brandes_pp for a service that evaluates the same graph many
@@ -283,20 +303,29 @@ int bcpp_partition_lp(bcpp_ctx *ctx, const bcpp_graph *g, int32_t max_rounds, co
  * where an allocation, which can synchronize the device, is not acceptable.  No context is
  * needed: the call takes only inputs, the output and a stream.
  *
- * Computes exactly what bcpp_brandes computes with BCPP_FP64 (same kernels): bc_out[n] (device)
- * receives C^S(v) for the targets S[nS] (device; nS == 0 means S = V), halved when `halve`
- * is non-zero.  The graph (device CSR) must be undirected with n <= BCPP_NOALLOC_MAX_NODES
- * and unit weights or integer weights <= BCPP_NOALLOC_MAX_WEIGHT; anything else returns
- * BCPP_EINVAL before any work is queued.  Other errors as for bcpp_brandes.
+ * bc_out[n] (device, caller-owned) receives C^S(v) for the targets S[nS] (device; nS == 0
+ * means S = V), halved when `halve` is non-zero, in FP64.  It runs the kernels of bcpp_brandes
+ * with a fixed launch shape (eight batches of 32 sources in flight, sources in the given order),
+ * so the FP64 sums are added in another order: results agree with bcpp_brandes to a relative
+ * 1e-12, not bit for bit.  The graph (device CSR) must be undirected with
+ * n <= BCPP_NOALLOC_MAX_NODES and unit weights or integer weights <= BCPP_NOALLOC_MAX_WEIGHT.
  *
- * Scratch lives in one file-scope static device array of about 40 MB, which every GPU that
- * loads the library holds until the process exits.  The first call on a device looks up
- * that array's device address (cudaGetSymbolAddress) once for the current device; make that
- * first call before any stream capture.  All calls share the array and it keeps the last
- * call's contents (each call clears what must start at zero), so calls whose GPU work
- * overlaps -- on different streams or from different host threads -- race on it: serialize
- * them.  The call synchronizes `cuda_stream` (NULL = legacy default stream) before it
- * returns. */
+ * Checks.  On the host, before any GPU work: null pointers, n above the limit, a directed
+ * graph and nS outside [0, n] return BCPP_EINVAL.  On the device, before the betweenness
+ * kernels run: an invalid CSR (as bcpp_csr_validate), a weight above the limit and repeated or
+ * out-of-range targets return BCPP_EINVAL; such a refused call has already overwritten the
+ * shared scratch array (never the output).  Other errors as for bcpp_brandes.
+ *
+ * Scratch lives in one file-scope static device array of about 43 MB.  Every GPU on which the
+ * library's device code is loaded holds it until the process exits.  CUDA loads that code
+ * lazily by default: the array is placed on a device by the first call there, which looks up
+ * its device address (cudaGetSymbolAddress; every call looks it up again, which allocates
+ * nothing); make that first call before a host allocator reserves the free device memory and
+ * before any stream capture, or run the process with CUDA_MODULE_LOADING=EAGER.  All calls
+ * share the array and it keeps the last call's contents (each call clears what must start at
+ * zero), so calls whose GPU work overlaps -- on different streams or from different host
+ * threads -- race on it: serialize them.  The call synchronizes `cuda_stream` (NULL = legacy
+ * default stream) before it returns. */
 int bcpp_brandes_noalloc(const bcpp_graph *g, const int32_t *S, int32_t nS, int32_t halve,
                          double *bc_out, void *cuda_stream);
 

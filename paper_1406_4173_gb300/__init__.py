@@ -7,13 +7,14 @@ library has not been built (there is no CPU fallback).
 """
 from .api import (  # noqa: F401
     Arena, BcppError, Context, Graph, HostCSR, SigmaOverflow, brandes, brandes_batched, brandes_batched_host, brandes_host, brandes_pp,
-    brandes_pp_host, brandes_noalloc, brandes_pp_st, brandes_pp_all, build_arena, Plan, autotune, partition_lp, plan_brandes, plan_brandes_pp, csr_build, csr_validate, default_context, graph_from_edgelist, load_library,
-    skeleton, sssp,
+    brandes_pp_host, brandes_noalloc, brandes_pp_st, brandes_pp_all, build_arena, Plan, autotune, autotune_batched, partition_lp, plan_brandes, plan_brandes_pp, csr_build, csr_validate, default_context, graph_from_edgelist, load_library,
+    shard_bounds, skeleton, sssp,
 )
+from . import sharded  # noqa: F401
 
 __all__ = [
     "Arena", "BcppError", "Context", "Graph", "HostCSR", "SigmaOverflow", "brandes", "brandes_batched",
     "brandes_batched_host",
     "brandes_host", "brandes_noalloc", "brandes_pp", "brandes_pp_st", "brandes_pp_all", "brandes_pp_host", "build_arena", "csr_build", "csr_validate", "default_context",
-    "graph_from_edgelist", "load_library", "Plan", "autotune", "partition_lp", "plan_brandes", "plan_brandes_pp", "skeleton", "sssp",
+    "graph_from_edgelist", "load_library", "Plan", "autotune", "autotune_batched", "partition_lp", "plan_brandes", "plan_brandes_pp", "shard_bounds", "sharded", "skeleton", "sssp",
 ]

@@ -57,7 +57,7 @@ EXPORTS = ["bcpp_default_opts", "bcpp_strerror", "bcpp_create", "bcpp_destroy", 
            "bcpp_csr_build", "bcpp_csr_validate", "bcpp_brandes", "bcpp_brandes_pp", "bcpp_brandes_batched",
            "bcpp_sssp", "bcpp_skeleton", "bcpp_brandes_noalloc", "bcpp_brandes_pp_st", "bcpp_brandes_pp_all",
            "bcpp_plan_brandes", "bcpp_plan_brandes_pp", "bcpp_plan_launch", "bcpp_plan_destroy", "bcpp_autotune",
-           "bcpp_partition_lp"]
+           "bcpp_partition_lp", "bcpp_shard_bounds", "bcpp_autotune_batched"]
 
 _lib = None
 _lock = threading.Lock()
@@ -99,6 +99,8 @@ def load_library(path: str | None = None):
             "bcpp_plan_destroy": (None, [P]),
             "bcpp_autotune": (ctypes.c_int, [P, G, P, i32, O, O, ctypes.POINTER(ctypes.c_float)]),
             "bcpp_partition_lp": (ctypes.c_int, [P, G, i32, O, P, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+            "bcpp_shard_bounds": (ctypes.c_int, [i64, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+            "bcpp_autotune_batched": (ctypes.c_int, [P, i32, P, G, O, O, ctypes.POINTER(ctypes.c_float)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -208,6 +210,15 @@ def _dev_i32(x, device):
     if isinstance(x, torch.Tensor):
         return x.to(device=device, dtype=torch.int32).contiguous()
     return torch.as_tensor(np.ascontiguousarray(x, dtype=np.int32), device=device)
+
+
+def shard_bounds(num_sources: int, index: int, count: int) -> tuple[int, int]:
+    """Source positions [s0, s1) of shard `index` of `count` (bcpp_shard_bounds; host only):
+    the rule behind the `shard=(index, count)` option of the betweenness calls."""
+    s0, s1 = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load_library().bcpp_shard_bounds(int(num_sources), int(index), int(count), ctypes.byref(s0),
+                                            ctypes.byref(s1)))
+    return int(s0.value), int(s1.value)
 
 
 # ----------------------------------------------------------------------------- CSR
@@ -359,6 +370,25 @@ def autotune(G: Graph, S=None, precision: str = "fp64", ctx: Context | None = No
                                       ctypes.byref(o), ctypes.byref(t), ms)
     _check(rc, allow_overflow=True)
     return {"batch": int(t.batch), "cluster": int(t.cluster)}, dict(zip(AUTOTUNE_CANDIDATES, [float(x) for x in ms]))
+
+
+AUTOTUNE_BATCHED_CANDIDATES = [(32, 2), (64, 2), (32, 1), (64, 1)]   # (batch, ctas_per_sm)
+
+
+def autotune_batched(arena: "Arena", precision: str = "fp64", ctx: Context | None = None):
+    """Time the batched launch-shape candidates on the whole arena (bcpp_autotune_batched).
+    Returns ({"batch": b, "ctas_per_sm": c}, {(batch, ctas_per_sm): ms}) -- pass the first as
+    keyword arguments to brandes_batched."""
+    ctx = ctx or default_context()
+    o = _opts(precision, True)
+    t = c_opts()
+    ms = (ctypes.c_float * len(AUTOTUNE_BATCHED_CANDIDATES))()
+    cg = arena.graph.c()
+    rc = load_library().bcpp_autotune_batched(ctx.handle, len(arena.node_ptr_host) - 1, arena.node_ptr.data_ptr(),
+                                              ctypes.byref(cg), ctypes.byref(o), ctypes.byref(t), ms)
+    _check(rc, allow_overflow=True)
+    return ({"batch": int(t.batch), "ctas_per_sm": int(t.ctas_per_sm)},
+            dict(zip(AUTOTUNE_BATCHED_CANDIDATES, [float(x) for x in ms])))
 
 
 def partition_lp(G: Graph, max_rounds: int = 20, ctx: Context | None = None):
@@ -576,7 +606,7 @@ class HostCSR:
 
 
 def brandes_host(H: HostCSR, S=None, precision="fp64", halve=True, ctx: Context | None = None, out=None,
-                 stats: bool = False, allow_overflow: bool = False):
+                 stats: bool = False, allow_overflow: bool = False, shard=None):
     """Plain Brandes with every array in (pinned) host memory; the library copies in and out."""
     torch = _torch()
     ctx = ctx or default_context()
@@ -585,7 +615,7 @@ def brandes_host(H: HostCSR, S=None, precision="fp64", halve=True, ctx: Context 
     bc = out if out is not None else torch.empty(H.n, dtype=torch.float64).pin_memory()
     st = c_stats()
     cg = H.c()
-    o = _opts(precision, halve, host=True)
+    o = _opts(precision, halve, host=True, shard=shard)
     rc = load_library().bcpp_brandes(ctx.handle, ctypes.byref(cg), None if nS == 0 else St.data_ptr(), nS,
                                      ctypes.byref(o), bc.data_ptr(), ctypes.byref(st))
     _check(rc, allow_overflow)
@@ -593,7 +623,7 @@ def brandes_host(H: HostCSR, S=None, precision="fp64", halve=True, ctx: Context 
 
 
 def brandes_pp_host(H: HostCSR, S, part, k=None, precision="fp64", halve=True, ctx: Context | None = None, out=None,
-                    stats: bool = False, allow_overflow: bool = False):
+                    stats: bool = False, allow_overflow: bool = False, shard=None):
     """Brandes++ with every array in (pinned) host memory; the library copies in and out."""
     torch = _torch()
     ctx = ctx or default_context()
@@ -605,7 +635,7 @@ def brandes_pp_host(H: HostCSR, S, part, k=None, precision="fp64", halve=True, c
     bc = out if out is not None else torch.empty(H.n, dtype=torch.float64).pin_memory()
     st = c_stats()
     cg = H.c()
-    o = _opts(precision, halve, host=True)
+    o = _opts(precision, halve, host=True, shard=shard)
     rc = load_library().bcpp_brandes_pp(ctx.handle, ctypes.byref(cg), None if nS == 0 else St.data_ptr(), nS,
                                         pt.data_ptr(), int(k), ctypes.byref(o), bc.data_ptr(), ctypes.byref(st))
     _check(rc, allow_overflow)
@@ -620,6 +650,10 @@ def brandes_noalloc(G: Graph, S=None, halve: bool = True, out=None, stream=None,
     dev = G.row_ptr.device
     St = _dev_i32(S, dev)
     nS = 0 if St is None else int(St.numel())
+    if out is not None and (out.dtype != torch.float64 or out.numel() < G.n or not out.is_contiguous()
+                            or out.device != dev):
+        raise BcppError(BCPP_EINVAL, "out must be a contiguous float64 tensor of at least n elements "
+                                     "on the graph's device")
     bc = out if out is not None else torch.empty(G.n, dtype=torch.float64, device=dev)
     st = stream if stream is not None else torch.cuda.current_stream()
     cg = G.c()

@@ -224,15 +224,20 @@ __global__ void i64_from_i32_kernel(const int32_t* in, int64_t* out, int64_t n) 
         out[i] = in[i];
 }
 
-// sources [s0, s1) of this shard: shard r of R takes sources [ns*r/R, ns*(r+1)/R)
-void shard_sources(const bcpp_opts& o, int64_t ns, int64_t& s0, int64_t& s1) {
+// sources [s0, s1) of shard r of R: [ns*r/R, ns*(r+1)/R) (bcpp_shard_bounds)
+void shard_range(int64_t ns, int64_t r, int64_t R, int64_t& s0, int64_t& s1) {
     s0 = 0;
     s1 = ns;
-    if (o.shard_count > 1) {
-        const int64_t r = std::max(0, std::min(o.shard_index, o.shard_count - 1));
-        s0 = ns * r / o.shard_count;
-        s1 = ns * (r + 1) / o.shard_count;
+    if (R > 1) {
+        s0 = ns * r / R;
+        s1 = ns * (r + 1) / R;
     }
+}
+
+// sources [s0, s1) of this call's shard (an out-of-range shard index is clamped)
+void shard_sources(const bcpp_opts& o, int64_t ns, int64_t& s0, int64_t& s1) {
+    const int64_t r = std::max(0, std::min(o.shard_index, o.shard_count - 1));
+    shard_range(ns, r, o.shard_count, s0, s1);
 }
 
 // batches of `lanes` consecutive sources of [s0, s1) of graph g
@@ -297,7 +302,7 @@ struct SlotWs {
     DBuf<int32_t> step_d, step_beg, hdr;
     DBuf<uint32_t> bm;
     DBuf<uint8_t> bflag;
-    DBuf<double> bcs, bcc;
+    DBuf<double> bcs, bcc, bcb;
     DBuf<int> counter;
     LsSlots W{};
     int slots = 0, nb = 0;
@@ -322,11 +327,20 @@ int entry_factor(const bcpp_ctx* c, bool weighted, int spl) {
     return weighted ? 32 * spl : c->order_factor;
 }
 
+// Non-empty steps a batch can record.  Every recorded step holds at least one settled entry
+// (a bucket is flagged only when a head is marked in it, and with weights below nb the window
+// of tentative distances maps each bucket to a single distance), so the order capacity bounds
+// them; so does the number of distinct distances, 0 .. (nb - 1)(n - 1).
+int32_t step_capacity(int64_t cap_n, int nb, int64_t cap_order) {
+    const int64_t dist_bound = (int64_t)(nb - 1) * std::max<int64_t>(cap_n - 1, 0) + 2;
+    return (int32_t)std::min<int64_t>(cap_order, dist_bound);
+}
+
 int64_t slot_bytes(int64_t cap_n, int nb, bool fp32, int order_factor = 8, int spl = 1) {
     const int64_t cap_order = order_capacity(cap_n, order_factor, spl);
     const int64_t bm_words = (cap_n + 31) / 32;
     return cap_n * 32 * spl * (4 + 8 + (fp32 ? 4 : 8)) + cap_order * (int64_t)sizeof(LsEnt) +
-           2 * (cap_n + 4098) * 4 + (int64_t)nb * bm_words * 4 + nb;
+           2 * (int64_t)step_capacity(cap_n, nb, cap_order) * 4 + (int64_t)nb * bm_words * 4 + nb;
 }
 
 // CTAs per batch: with fewer batches than resident CTAs (two per SM), 2 or 4 CTAs of a
@@ -363,6 +377,7 @@ int init_slots(bcpp_ctx* c, SlotWs& S) {
     if (W.cap_bc > 0) {
         CK_CUDA(cudaMemsetAsync(S.bcs.p, 0, (size_t)S.slots * W.cap_bc * sizeof(double), c->stream));
         CK_CUDA(cudaMemsetAsync(S.bcc.p, 0, (size_t)S.slots * W.cap_bc * sizeof(double), c->stream));
+        CK_CUDA(cudaMemsetAsync(S.bcb.p, 0, (size_t)S.slots * W.cap_bc * sizeof(double), c->stream));
     }
     fill_i32(S.d.p, S.narrow ? -1 : DINF, (int64_t)S.slots * S.rows * 32, c->stream);
     c->launches++;
@@ -378,7 +393,7 @@ int alloc_slots(bcpp_ctx* c, SlotWs& S, int slots, int64_t cap_n, int nb, bool f
     if (cap_n >= (1 << 25)) return BCPP_EINVAL;   // 32-bit row offsets inside a slot
     const int64_t cap_order = order_capacity(cap_n, factor, spl);
     const int64_t rows = cap_n * spl;              // rows of 32 values
-    const int32_t cap_steps = (int32_t)std::min<int64_t>(cap_order, 4 * (cap_n + 2) + 4096);
+    const int32_t cap_steps = step_capacity(cap_n, nb, cap_order);
     const int64_t bm_words = (cap_n + 31) / 32;
     CK_ALLOC(S.d.alloc(c, (int64_t)slots * rows * 32));
     CK_ALLOC(S.sg.alloc(c, (int64_t)slots * rows * 32));
@@ -393,6 +408,7 @@ int alloc_slots(bcpp_ctx* c, SlotWs& S, int slots, int64_t cap_n, int nb, bool f
     if (cap_bc > 0) {
         CK_ALLOC(S.bcs.alloc(c, (int64_t)slots * cap_bc));
         CK_ALLOC(S.bcc.alloc(c, (int64_t)slots * cap_bc));
+        CK_ALLOC(S.bcb.alloc(c, (int64_t)slots * cap_bc));
     }
     S.slots = slots;
     S.nb = nb;
@@ -404,6 +420,7 @@ int alloc_slots(bcpp_ctx* c, SlotWs& S, int slots, int64_t cap_n, int nb, bool f
     W.bm = S.bm.p; W.bm_words = bm_words; W.bflag = S.bflag.p;
     W.bc_sum = cap_bc > 0 ? S.bcs.p : nullptr;
     W.bc_cmp = cap_bc > 0 ? S.bcc.p : nullptr;
+    W.bc_bat = cap_bc > 0 ? S.bcb.p : nullptr;
     W.cap_bc = cap_bc;
     W.hdr = S.hdr.p;
     return init ? init_slots(c, S) : BCPP_OK;
@@ -850,7 +867,7 @@ int plain_prepare(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS
     r.nb = g->w ? (int)r.wmax + 1 : 2;
     r.cl = r.spl == 1 ? choose_cluster(c, r.nitems, o) : 1;
     const int ef = entry_factor(c, g->w != nullptr, r.spl);
-    r.slots = choose_slots(c, r.nitems, o.ctas_per_sm, slot_bytes(n, r.nb, fp32, ef, r.spl), (int64_t)n * 16, r.cl);
+    r.slots = choose_slots(c, r.nitems, o.ctas_per_sm, slot_bytes(n, r.nb, fp32, ef, r.spl), (int64_t)n * 24, r.cl);
     CK_RC(alloc_slots(c, r.ws, r.slots, n, r.nb, fp32, n, r.spl, ef, false));
     r.ws.narrow = use_narrow(c, g->w != nullptr);
     LsArena& A = r.A;
@@ -1169,7 +1186,7 @@ struct PpRun {
     double* bc_out = nullptr;
     const uint8_t* dflag = nullptr;
     Skeleton K;
-    DBuf<int32_t> tsk, tcnt;
+    DBuf<int32_t> tsk;
     OrderWs ord;
     int32_t nt = 0;
     SlotWs ws;
@@ -1202,7 +1219,6 @@ int pp_prepare(bcpp_ctx* c, const bcpp_graph* g, uint64_t wmax, const InCsr* Tin
     const int32_t N = K.N;
     // targets in batch order (grouped by their original part when requested), as skeleton ids
     CK_ALLOC(r.tsk.alloc(c, ns));
-    CK_ALLOC(r.tcnt.alloc(c, 1));
     {
         const int32_t* Suse = Ssrc;
         if (o.order_sources && ns > 2 * LS_LANES) {
@@ -1210,10 +1226,10 @@ int pp_prepare(bcpp_ctx* c, const bcpp_graph* g, uint64_t wmax, const InCsr* Tin
                                 g->directed ? (g->w ? Tin->w.p : nullptr) : g->w, wmax, Ssrc, ns, part, k, r.ord));
             Suse = r.ord.out.p;
         }
-        sk_target_ids(Suse, (int32_t)ns, K.skid.p, r.tsk.p, r.tcnt.p, c->stream);
+        sk_target_ids(Suse, (int32_t)ns, K.skid.p, r.tsk.p, c->stream);
         c->launches++;
     }
-    CK_RC(to_host(c, &r.nt, r.tcnt.p, 1));
+    r.nt = (int32_t)ns;
     r.unit = K.wmax_sk == 1;
     r.mult = K.mmax_sk > 1;
     r.nb = (int)K.wmax_sk + 1;
@@ -1232,7 +1248,7 @@ int pp_prepare(bcpp_ctx* c, const bcpp_graph* g, uint64_t wmax, const InCsr* Tin
     r.cl = (r.nitems > 0 && r.spl == 1) ? choose_cluster(c, r.nitems, o) : 1;
     const int ef = entry_factor(c, !r.unit, r.spl);
     r.slots = r.nitems > 0 ? choose_slots(c, r.nitems, o.ctas_per_sm,
-                                          slot_bytes(std::max(N, 1), r.nb, fp32, ef, r.spl), (int64_t)n * 16, r.cl)
+                                          slot_bytes(std::max(N, 1), r.nb, fp32, ef, r.spl), (int64_t)n * 24, r.cl)
                            : 1;
     if (!r.hunits.empty() && r.nitems > 0) {
         // with Centrality the batches run in static chunks of `slots`: make the chunks equal
@@ -1733,7 +1749,7 @@ int batched_dev(bcpp_ctx* c, int32_t ngraphs, const int64_t* node_ptr_dev, const
     const int nb = g->w ? (int)wmax + 1 : 2;
     const int slots =
         choose_slots(c, nitems, o.ctas_per_sm, slot_bytes(maxn, nb, fp32, entry_factor(c, g->w != nullptr, spl), spl),
-                     (int64_t)n * 16);
+                     (int64_t)n * 24);
     SlotWs ws;
     CK_RC(alloc_slots(c, ws, slots, maxn, nb, fp32, n, spl, entry_factor(c, g->w != nullptr, spl), false));
     ws.narrow = use_narrow(c, g->w != nullptr);
@@ -2137,6 +2153,13 @@ void bcpp_default_opts(bcpp_opts* o) {
     o->shard_count = 0;
 }
 
+int bcpp_shard_bounds(int64_t num_sources, int32_t index, int32_t count, int64_t* s0, int64_t* s1) {
+    if (num_sources < 0 || !s0 || !s1) return BCPP_EINVAL;
+    if (count > 1 && (index < 0 || index >= count)) return BCPP_EINVAL;
+    shard_range(num_sources, index, count, *s0, *s1);
+    return BCPP_OK;
+}
+
 const char* bcpp_strerror(int s) {
     switch (s) {
         case BCPP_OK: return "ok";
@@ -2457,6 +2480,42 @@ int bcpp_autotune(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS
             best = st.ms_brandes_sk;
             tuned->batch = cand[i][0];
             tuned->cluster = cand[i][1];
+        }
+    }
+    return BCPP_OK;
+}
+
+int bcpp_autotune_batched(bcpp_ctx* c, int32_t num_graphs, const int64_t* graph_node_ptr, const bcpp_graph* arena,
+                          const bcpp_opts* opts, bcpp_opts* tuned, float* ms_out) {
+    if (!c || !arena || !graph_node_ptr || num_graphs < 0 || !tuned) return BCPP_EINVAL;
+    const bcpp_opts base = opts_or_default(opts);
+    if (base.host_buffers) return BCPP_EINVAL;
+    int rc = check_graph_struct(arena);
+    if (rc) return rc;
+    *tuned = base;
+    static const int cand[BCPP_AUTOTUNE_BATCHED_CANDIDATES][2] = {{32, 2}, {64, 2}, {32, 1}, {64, 1}};
+    for (int i = 0; i < BCPP_AUTOTUNE_BATCHED_CANDIDATES; i++)
+        if (ms_out) ms_out[i] = -1.f;
+    if (arena->n == 0) return BCPP_OK;
+    std::vector<int64_t> hptr((size_t)num_graphs + 1);
+    rc = to_host(c, hptr.data(), graph_node_ptr, (int64_t)num_graphs + 1);
+    if (rc) return rc;
+    DBuf<double> scratch(c, arena->n);
+    if (!scratch) return BCPP_ENOMEM;
+    float best = -1.f;
+    for (int i = 0; i < BCPP_AUTOTUNE_BATCHED_CANDIDATES; i++) {
+        bcpp_opts o = base;
+        o.batch = cand[i][0];
+        o.ctas_per_sm = cand[i][1];
+        bcpp_stats st{};
+        rc = with_capacity_retry(c, [&] { return batched_dev(c, num_graphs, graph_node_ptr, hptr.data(), arena, o,
+                                                             scratch.p, &st); });
+        if (rc != BCPP_OK && rc != BCPP_EOVERFLOW_SIGMA) return rc;
+        if (ms_out) ms_out[i] = st.ms_brandes_sk;
+        if (best < 0.f || st.ms_brandes_sk < best) {
+            best = st.ms_brandes_sk;
+            tuned->batch = cand[i][0];
+            tuned->ctas_per_sm = cand[i][1];
         }
     }
     return BCPP_OK;

@@ -89,8 +89,9 @@ struct LsSlots {
     uint32_t* bm;                // [slot][nb][bm_words] bucket bitmaps
     int64_t bm_words;
     uint8_t* bflag;              // [slot][nb] bucket non-empty flags
-    double* bc_sum;              // [slot][cap_bc] partial betweenness (sum)
-    double* bc_cmp;              // [slot][cap_bc] compensation (Neumaier, where a kernel keeps one)
+    double* bc_sum;              // [slot][cap_bc] partial betweenness (Neumaier sum over the slot's batches)
+    double* bc_cmp;              // [slot][cap_bc] its compensation
+    double* bc_bat;              // [slot][cap_bc] the current batch's sums (zero between batches)
     int64_t cap_bc;
     int32_t* hdr;                // [slot][4]: order length, steps, item, -
 };

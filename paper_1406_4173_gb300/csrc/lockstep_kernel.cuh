@@ -170,6 +170,21 @@ __device__ __forceinline__ void for_arc_groups(const int32_t* __restrict__ col, 
     }
 }
 
+// Whether some value of one node's distance row (ROW int32 values, 16-byte aligned) equals D.
+template <int ROW>
+__device__ __forceinline__ bool row_has(const int32_t* row, int32_t D) {
+    const int4* r4 = reinterpret_cast<const int4*>(row);
+    int4 t[ROW / 4];
+#pragma unroll
+    for (int i = 0; i < ROW / 4; i++) t[i] = r4[i];
+    bool hit = false;
+#pragma unroll
+    for (int i = 0; i < ROW / 4; i++) hit |= t[i].x == D || t[i].y == D || t[i].z == D || t[i].w == D;
+    return hit;
+}
+template <int ROW>
+__device__ __forceinline__ bool row_has(const uint8_t*, int32_t) { return true; }
+
 // Scalar control state of one batch; with a cluster it lives in the leader CTA's shared memory
 // and the other CTAs reach it through distributed shared memory.
 struct LsCtl {
@@ -243,7 +258,9 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
     int32_t* step_beg = W.step_beg + (int64_t)slot * W.cap_steps;
     uint32_t* bm = W.bm + (int64_t)slot * P.nb * W.bm_words;
     uint8_t* bflag = W.bflag + (int64_t)slot * P.nb;
-    double* bcs = W.bc_sum ? W.bc_sum + (int64_t)slot * W.cap_bc : nullptr;
+    // dependencies of the current batch (at most 32 * SPL terms per node) are added into bat with
+    // atomics; at the end of the batch they move into the slot's compensated sums
+    double* bat = W.bc_bat ? W.bc_bat + (int64_t)slot * W.cap_bc : nullptr;
 
     bool first = true;
     for (;;) {
@@ -322,6 +339,18 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                 for (int wi = gtid; wi < nwr; wi += GT) {
                     uint32_t x = wi < nwords ? bmD[wi] : 0u;
                     if (x) bmD[wi] = 0u;
+                    if constexpr (WEIGHTED) {
+                        // A mark goes stale when the lane it was made for improves to a smaller
+                        // distance (the node is then settled from that smaller bucket).  Keep only
+                        // nodes with some lane at D, so that a batch lists each node at most once
+                        // per distinct distance (at most 32 * SPL entries per node).
+                        uint32_t keep = 0u;
+                        for (uint32_t y = x; y; y &= y - 1) {
+                            const int b = __ffs(y) - 1;
+                            if (row_has<ROW>(d + ((int64_t)(wi * 32 + b) << SH), D)) keep |= 1u << b;
+                        }
+                        x = keep;
+                    }
                     const int c = __popc(x);
                     const int incl = warp_incl_scan(c, lane);
                     const int tot = __shfl_sync(FULL, incl, 31);
@@ -504,7 +533,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
             sync();
             if (leader) {
                 ctl->D = D + 1;
-                if (WEIGHTED || end > beg) ctl->nsteps++;
+                if (end > beg) ctl->nsteps++;        // steps without entries are not recorded
                 if (!WEIGHTED && end > beg) ctl->maxpush = D + 1;   // try the next level
             }
         }
@@ -603,7 +632,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                                 const DT sd = (DT)su[s];
                                 const DT delta = sd * acc[s];
                                 cl0[((uint32_t)u << SH) + s] = is_t ? acc[s] + recip_count(sd) : acc[s];
-                                if (u != my_src[s] && bcs && delta != (DT)0) atomicAdd(&bcs[ix], (double)delta);
+                                if (u != my_src[s] && bat && delta != (DT)0) atomicAdd(&bat[ix], (double)delta);
                             }
                         }
 
@@ -639,6 +668,38 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
             }
         }
 
+        if (bat && (P.mode == LS_BRANDES || P.mode == LS_SKEL)) {
+            // Neumaier step of every touched node's batch sum into the slot's (sum, compensation):
+            // the exchange hands each node's sum to exactly one of its entries (a node has one
+            // entry per step it was settled at) and leaves zero for the next batch
+            double* bcs = W.bc_sum + (int64_t)slot * W.cap_bc;
+            double* bcc = W.bc_cmp + (int64_t)slot * W.cap_bc;
+            constexpr int FK = 2;   // entries per thread and round, requested together
+            for (int e0 = gtid * FK; e0 < olen; e0 += GT * FK) {
+                int64_t ix[FK];
+                unsigned long long x[FK];
+#pragma unroll
+                for (int k = 0; k < FK; k++) {
+                    ix[k] = -1;
+                    if (e0 + k < olen) {
+                        const int32_t u = order[e0 + k].u;
+                        ix[k] = P.bc_map ? (int64_t)P.bc_map[base + u] : base + u;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < FK; k++)
+                    x[k] = ix[k] >= 0 ? atomicExch(reinterpret_cast<unsigned long long*>(bat + ix[k]), 0ull) : 0ull;
+#pragma unroll
+                for (int k = 0; k < FK; k++) {
+                    if (x[k]) {
+                        double s0 = bcs[ix[k]], c0 = bcc[ix[k]];
+                        neumaier_add(s0, c0, __longlong_as_double((long long)x[k]));
+                        bcs[ix[k]] = s0;
+                        bcc[ix[k]] = c0;
+                    }
+                }
+            }
+        }
         if (P.mode == LS_SKEL) {
             if (leader) {
                 W.hdr[slot * 4 + 0] = olen;

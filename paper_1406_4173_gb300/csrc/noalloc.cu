@@ -7,12 +7,14 @@
 // it needs in one file-scope static device array of fixed size, so such callers only pass
 // their inputs and output.
 //
-// The array is part of the library image: every GPU that loads the library holds it (about
-// 40 MB) until the process exits.  All calls share it and it keeps the last call's contents;
-// each call clears what must start at zero.  Calls whose work overlaps on the GPU (other
-// streams, other host threads) race on the array; serialize them.
-#include <mutex>
-
+// The array belongs to the library's device code: every GPU on which the library's module is
+// loaded holds it (about 43 MB) until the process exits.  CUDA loads modules lazily by
+// default, so the array is placed on a device at the first call there (the address lookup
+// loads the module), not when the library is opened; a host allocator that reserves the free
+// memory must come after that first call, or the process must set CUDA_MODULE_LOADING=EAGER.
+// All calls share the array and it keeps the last call's contents; each call clears what
+// must start at zero.  Calls whose work overlaps on the GPU (other streams, other host
+// threads) race on the array; serialize them.
 #include "common.cuh"
 #include "csr.cuh"
 #include "lockstep.cuh"
@@ -27,7 +29,8 @@ constexpr int32_t NA_MAX_W = BCPP_NOALLOC_MAX_WEIGHT;
 constexpr int NA_NB = NA_MAX_W + 1;
 constexpr int NA_SLOTS = 8;
 constexpr int64_t NA_CAP_ORDER = 32 * (int64_t)NA_NODES + 1024;
-constexpr int32_t NA_CAP_STEPS = 4 * (NA_NODES + 2) + 4096;
+// steps of a batch: at most one per distinct distance 0 .. NA_MAX_W * (NA_NODES - 1)
+constexpr int32_t NA_CAP_STEPS = NA_MAX_W * (NA_NODES - 1) + 2;
 constexpr int64_t NA_BM_WORDS = (NA_NODES + 31) / 32;
 constexpr int NA_MAX_ITEMS = (NA_NODES + LS_LANES - 1) / LS_LANES;
 
@@ -42,6 +45,7 @@ struct NaScratch {
     uint32_t bm[NA_SLOTS][NA_NB][NA_BM_WORDS];
     double bc_sum[NA_SLOTS][NA_NODES];
     double bc_cmp[NA_SLOTS][NA_NODES];
+    double bc_bat[NA_SLOTS][NA_NODES];
     int32_t hdr[NA_SLOTS][4];
     LsItem items[NA_MAX_ITEMS];
     int64_t node_off[2];
@@ -56,22 +60,17 @@ struct NaScratch {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NaScratch)];
 
-// per-device address of the array (host code may not use the symbol itself as an address)
-std::mutex g_na_mutex;
-NaScratch* g_na_ptr[64] = {};
-
-int na_scratch(int device, NaScratch** out) {
-    if (device < 0 || device >= 64) return BCPP_ECUDA;
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[device]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return BCPP_ECUDA;
-        }
-        g_na_ptr[device] = reinterpret_cast<NaScratch*>(p);
+// Device address of the array in the current context.  Host code may not use the symbol itself
+// as an address (it names a host-side stand-in), so every call looks the address up; the lookup
+// allocates nothing, and looking it up each time stays correct after a device reset or under
+// another context, where the module (and the array) are loaded again at a new address.
+int na_scratch(NaScratch** out) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return BCPP_ECUDA;
     }
-    *out = g_na_ptr[device];
+    *out = reinterpret_cast<NaScratch*>(p);
     return BCPP_OK;
 }
 
@@ -83,6 +82,7 @@ __global__ void na_prepare_kernel(NaScratch* s, int32_t n, int32_t ns, int nitem
     for (int64_t i = tid; i < (int64_t)NA_SLOTS * NA_NODES; i += stride) {
         (&s->bc_sum[0][0])[i] = 0.0;
         (&s->bc_cmp[0][0])[i] = 0.0;
+        (&s->bc_bat[0][0])[i] = 0.0;
     }
     for (int64_t i = tid; i < (int64_t)NA_SLOTS * NA_NB; i += stride) (&s->bflag[0][0])[i] = 0;
     for (int64_t i = tid; i < NA_SLOTS * 4; i += stride) (&s->hdr[0][0])[i] = 0;
@@ -112,10 +112,8 @@ extern "C" int bcpp_brandes_noalloc(const bcpp_graph* g, const int32_t* S, int32
     if (nS < 0 || nS > g->n || (nS > 0 && !S) || (g->n > 0 && !bc_out)) return BCPP_EINVAL;
     const cudaStream_t st = (cudaStream_t)cuda_stream;
     const int32_t n = g->n;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return BCPP_ECUDA; }
     NaScratch* s = nullptr;
-    int rc = na_scratch(dev, &s);
+    int rc = na_scratch(&s);
     if (rc) return rc;
 
     const int32_t ns = nS > 0 ? nS : n;
@@ -157,7 +155,8 @@ extern "C" int bcpp_brandes_noalloc(const bcpp_graph* g, const int32_t* S, int32
     // (nb = 2) the slots use a packed prefix of the array, which the prepare kernel cleared
     W.bm = &s->bm[0][0][0]; W.bm_words = NA_BM_WORDS;
     W.bflag = &s->bflag[0][0];
-    W.bc_sum = &s->bc_sum[0][0]; W.bc_cmp = &s->bc_cmp[0][0]; W.cap_bc = NA_NODES;
+    W.bc_sum = &s->bc_sum[0][0]; W.bc_cmp = &s->bc_cmp[0][0]; W.bc_bat = &s->bc_bat[0][0];
+    W.cap_bc = NA_NODES;
     W.hdr = &s->hdr[0][0];
     const int slots = nitems < NA_SLOTS ? nitems : NA_SLOTS;
     ls_launch(false, true, A, P, W, s->items, nitems, slots, st);

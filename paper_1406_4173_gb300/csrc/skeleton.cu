@@ -230,28 +230,10 @@ __global__ void gather_flags_kernel(int32_t N, const int32_t* sknode, const uint
     GRID_STRIDE(x, N) out[x] = in_s[sknode[x]];
 }
 
-// ordered compaction of targets that are skeleton nodes (single block, keeps S order)
-__global__ void target_ids_kernel(const int32_t* S, int32_t nS, const int32_t* skid, int32_t* out, int32_t* cnt) {
-    __shared__ int32_t base;
-    __shared__ int32_t wt[32];
-    if (threadIdx.x == 0) base = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int64_t c0 = 0; c0 < nS; c0 += blockDim.x) {
-        const int64_t j = c0 + threadIdx.x;
-        int32_t x = j < nS ? skid[S[j]] : -1;
-        const bool keep = x >= 0;
-        const unsigned m = __ballot_sync(FULL, keep);
-        if (lane == 0) wt[warp] = __popc(m);
-        __syncthreads();
-        int32_t pre = 0, tot = 0;
-        for (int w = 0; w < nw; w++) { if (w < warp) pre += wt[w]; tot += wt[w]; }
-        if (keep) out[base + pre + __popc(m & ((1u << lane) - 1u))] = x;
-        __syncthreads();
-        if (threadIdx.x == 0) base += tot;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *cnt = base;
+// targets as skeleton ids, position for position (-1 for a target that is no skeleton node: an
+// isolated node, whose lane then stays idle), so that shards of positions are shards of S
+__global__ void target_ids_kernel(const int32_t* S, int32_t nS, const int32_t* skid, int32_t* out) {
+    GRID_STRIDE(j, nS) out[j] = skid[S[j]];
 }
 
 // Tiled Centrality: one block (16 warps) per unit of up to 64 non-frontier nodes and one slot,
@@ -462,8 +444,8 @@ void sk_transpose(int32_t N, const int64_t* rp, const int32_t* col, const int32_
 void sk_gather_flags(int32_t N, const int32_t* sknode, const uint8_t* in_s, uint8_t* out, cudaStream_t st) {
     if (N > 0) gather_flags_kernel<<<grid_for(N, 256), 256, 0, st>>>(N, sknode, in_s, out);
 }
-void sk_target_ids(const int32_t* S, int32_t nS, const int32_t* skid, int32_t* out, int32_t* cnt, cudaStream_t st) {
-    target_ids_kernel<<<1, 1024, 0, st>>>(S, nS, skid, out, cnt);
+void sk_target_ids(const int32_t* S, int32_t nS, const int32_t* skid, int32_t* out, cudaStream_t st) {
+    if (nS > 0) target_ids_kernel<<<grid_for(nS, 256), 256, 0, st>>>(S, nS, skid, out);
 }
 
 void centrality_launch(bool fp32_delta, const CentralityUnit* units, int nunits, int nslots, SkTables T,

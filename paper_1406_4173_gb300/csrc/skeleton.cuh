@@ -48,8 +48,8 @@ void sk_transpose(int32_t N, const int64_t* rp, const int32_t* col, const int32_
                   int64_t* cursor, int32_t* tcol, int32_t* tw, uint64_t* tmu, int pass, cudaStream_t st);
 // gather: out[x] = in_s[sknode[x]]
 void sk_gather_flags(int32_t N, const int32_t* sknode, const uint8_t* in_s, uint8_t* out, cudaStream_t st);
-// targets that are skeleton nodes, as skeleton ids, in the given order; *cnt (device) = count
-void sk_target_ids(const int32_t* S, int32_t nS, const int32_t* skid, int32_t* out, int32_t* cnt, cudaStream_t st);
+// out[j] = skeleton id of target S[j], or -1 when it is no skeleton node (isolated)
+void sk_target_ids(const int32_t* S, int32_t nS, const int32_t* skid, int32_t* out, cudaStream_t st);
 
 // Centrality (Eq. 13) for the slots of one Brandes_SK chunk.
 struct CentralityUnit { int32_t part; int32_t v0; int32_t v1; int32_t pad; };

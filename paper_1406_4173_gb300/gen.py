@@ -24,7 +24,7 @@ import numpy as np
 __all__ = [
     "EdgeList", "rng_for", "path", "star", "cycle", "complete", "complete_bipartite",
     "grid", "erdos_renyi", "planted_partition", "powerlaw_sizes", "chung_lu_communities",
-    "er_batch", "sample_targets", "random_partition", "workload", "WORKLOADS",
+    "er_batch", "with_weights", "sample_targets", "random_partition", "workload", "WORKLOADS",
 ]
 
 
@@ -287,6 +287,14 @@ def er_batch(num_graphs: int, median: float, sigma: float, lo: int, hi: int, mea
     for g, n in enumerate(ns):
         out.append(erdos_renyi(int(n), mean_degree / (n - 1), seed=seed * 1000003 + g, stream=stream + 1))
     return out
+
+
+def with_weights(g: EdgeList, wmax: int, seed: int, stream: int = 9) -> EdgeList:
+    """A copy of ``g`` with integer edge weights drawn uniformly from [1, wmax]."""
+    rng = rng_for(seed, stream)
+    w = rng.integers(1, int(wmax) + 1, size=g.m, dtype=np.int64).astype(np.uint32)
+    return EdgeList(n=g.n, src=g.src.copy(), dst=g.dst.copy(), w=w, directed=g.directed,
+                    part=None if g.part is None else g.part.copy(), meta=dict(g.meta))
 
 
 def sample_targets(n: int, size: int, seed: int, stream: int = 7) -> np.ndarray:

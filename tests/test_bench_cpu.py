@@ -1,6 +1,6 @@
-"""CPU checks of bench.py's host logic: the traffic model behind the roofline, the rule that
-ties a committed DRAM figure to the kernel source it was measured on, and the JSON line of the
-reference arm (the CPU oracle), which needs no GPU."""
+"""CPU checks of bench.py's host logic: the traffic and operation models behind the rooflines,
+the rule that ties a committed DRAM figure to the kernel source it was measured on, and the JSON
+line of the reference arm (the CPU oracle on all host cores), which needs no GPU."""
 import json
 import os
 import subprocess
@@ -36,21 +36,44 @@ def test_model_bytes_terms():
     assert bench.model_bytes_per_source(0, 1, 0, 1, 8) == pytest.approx(16)
 
 
-def test_profiled_traffic_follows_kernel_source(monkeypatch):
-    """A committed DRAM figure is reported only while the kernel source hash recorded next to it
-    matches the current source."""
-    p = os.path.join(ROOT, "profiles", "ls_kernel_chunglu_50k.md")
-    rec = {}
-    for line in open(p).read().splitlines():
-        if line.startswith("- ") and ":" in line:
-            k, v = line[2:].split(":", 1)
-            rec[k.strip()] = v.strip()
-    assert "kernel_source_hash" in rec and "dram_bytes_per_launch" in rec
+def test_model_bytes_skeleton_terms():
+    """Brandes_SK adds, per arc and pass, 4 bytes of weight and 8 of multiplicity shared by the
+    batch's B sources; without weights or multiplicities it is the plain model."""
+    base = bench.model_bytes_per_source(10, 100, 30, 32, 8)
+    assert bench.model_bytes_per_source_skeleton(10, 100, 30, 32, 8, False, False) == pytest.approx(base)
+    assert bench.model_bytes_per_source_skeleton(10, 100, 30, 32, 8, True, False) == pytest.approx(
+        base + 100 * 2 * 4 / 32)
+    assert bench.model_bytes_per_source_skeleton(10, 100, 30, 32, 8, True, True) == pytest.approx(
+        base + 100 * 2 * 12 / 32)
+
+
+def test_centrality_ops_and_alu_peak():
+    """Centrality: 4 integer operations per (frontier, non-frontier node) entry and source; the
+    ALU peak is SMs x 4 schedulers x 32 lanes x clock (GB300: 152 SMs at 2,070 MHz = 40.3 T/s)."""
+    assert bench.centrality_ops_per_source(1000) == 4000
+    assert bench.alu_peak_ops(152, 2070.0) == pytest.approx(4.0274e13, rel=1e-4)
+
+
+def test_profiled_traffic_follows_kernel_source(monkeypatch, tmp_path):
+    """A committed DRAM figure (profiles/<kernel>_<workload>.json) is reported only while the
+    kernel source hash recorded with it matches the current source."""
+    (tmp_path / "profiles").mkdir()
+    rec = {"kernel_source_hash": "abcdef0123456789", "dram_bytes_per_launch": 123456789.0}
+    (tmp_path / "profiles" / "ls_kernel_w.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: rec["kernel_source_hash"])
-    assert bench.profiled_traffic("chunglu_50k") == float(rec["dram_bytes_per_launch"])
+    assert bench.profiled_traffic("ls_kernel", "w") == rec["dram_bytes_per_launch"]
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
-    assert bench.profiled_traffic("chunglu_50k") is None
-    assert bench.profiled_traffic("no_such_workload") is None
+    assert bench.profiled_traffic("ls_kernel", "w") is None
+    assert bench.profiled_traffic("ls_kernel", "no_such_workload") is None
+
+
+def test_committed_traffic_records_are_well_formed():
+    pdir = os.path.join(ROOT, "profiles")
+    for f in os.listdir(pdir):
+        if f.endswith(".json"):
+            rec = json.load(open(os.path.join(pdir, f)))
+            assert len(rec["kernel_source_hash"]) == 16 and float(rec["dram_bytes_per_launch"]) > 0, f
 
 
 def test_kernel_source_hash_is_stable():
@@ -80,6 +103,7 @@ def test_reference_arm_json_line():
     assert d["value"] > 0 and d["higher_is_better"] is True and d["vs_baseline"] is None
     assert d["config"]["workload"] == "planted_2k"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] == (os.cpu_count() or 1)
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
 
 

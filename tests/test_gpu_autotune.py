@@ -54,4 +54,4 @@ def test_autotune_directed_weighted(bc):
     assert (tuned["batch"], tuned["cluster"]) in bc.api.AUTOTUNE_CANDIDATES
     ref, _ = oracle.brandes(g, S)
     x = bc.brandes(G, S, precision="fp32", **tuned).cpu().numpy()
-    assert rel_err(x, ref) <= 2e-4
+    assert rel_err(x, ref) <= 2e-6       # FP32-delta: measured 1.1e-7

@@ -1,6 +1,6 @@
-"""GPU parity at the benchmark's full sizes (Chung-Lu n = 50,000, S = V; and the other
-workloads), on outputs the oracle can compute in seconds and on properties that hold at any
-size:
+"""GPU parity at the workloads' full sizes (Chung-Lu n = 1,000,000 with |S| = 4,096, the
+benchmark's; Chung-Lu n = 50,000 with S = V; and the other workloads), on outputs the oracle can
+compute in seconds and on properties that hold at any size:
 
 - bit-exact distances and path counts from sampled sources;
 - the partial betweenness of a shard of sources (the first |S|/R targets, all targets as
@@ -20,6 +20,10 @@ from paper_1406_4173_gb300 import gen
 
 pytestmark = pytest.mark.gpu
 FP64_TOL = 1e-12
+# FP32-delta bars: about 10x the measured errors (chunglu_50k shard of 250 sources: 8.8e-7;
+# chunglu_1m shard of 32 sources: 8.7e-7, all 4,096 sources: 6.0e-7 plain, 6.9e-7 Brandes++)
+FP32_TOL_C2 = 1e-5
+FP32_TOL_C5 = 1e-5
 INF32 = np.iinfo(np.int32).max
 
 
@@ -74,7 +78,7 @@ def test_c2_sampled_sssp_bit_exact(bc, c2):
         assert np.array_equal(dist[i], d_ref) and np.array_equal(sig[i], s_ref)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", 2e-4)])
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", FP32_TOL_C2)])
 def test_c2_shard_partial_vs_oracle(bc, c2, precision, tol):
     g, G = c2
     count = 200                                     # first 250 sources, all 50,000 targets
@@ -146,3 +150,47 @@ def test_er_batch_4096_sampled(bc):
     for i in list(range(0, 4096, 97)) + [int(np.argmax([g.n for g in gs]))]:
         ref, _ = oracle.brandes(gs[i])
         assert rel_err(got[off[i]:off[i + 1]], ref) < FP64_TOL, i
+
+
+# ----------------------------------------------------------------------------- chunglu_1m (the largest workload)
+@pytest.fixture(scope="module")
+def c5(bc):
+    g, S = gen.workload("chunglu_1m")
+    return g, S, bc.graph_from_edgelist(g)
+
+
+def test_c5_sampled_sssp_bit_exact(bc, c5):
+    g, S, G = c5
+    src = S[np.linspace(0, len(S) - 1, 16).astype(int)]
+    dist, sig = bc.sssp(G, src)
+    dist, sig = dist.cpu().numpy(), sig.cpu().numpy().view(np.uint64)
+    for i, s in enumerate(src):
+        d_ref, s_ref, _ = oracle.sssp(g, int(s))
+        assert np.array_equal(dist[i], d_ref) and np.array_equal(sig[i], s_ref), int(s)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", FP32_TOL_C5)])
+def test_c5_shard_partial_vs_oracle(bc, c5, precision, tol):
+    """The first 32 targets as sources (shard 0 of 128), all 4,096 targets as destinations."""
+    g, S, G = c5
+    count = 128
+    ns = len(S) // count
+    ref, _ = oracle.brandes(g, S, nsrc=ns, halve=False)
+    got = bc.brandes(G, S, halve=False, shard=(0, count), precision=precision, order_sources=False).cpu().numpy()
+    assert rel_err(got, ref) < tol
+    got_pp = bc.brandes_pp(G, S, g.part, halve=False, shard=(0, count), precision=precision,
+                           order_sources=False).cpu().numpy()
+    assert rel_err(got_pp, ref) < tol
+
+
+def test_c5_brandes_pp_equals_plain(bc, c5):
+    """The benchmark's configuration (128 batches: Brandes_SK and Centrality in two chunks of 64
+    four-CTA slots on 152 SMs): Brandes++ equals plain Brandes, FP64 and FP32-delta."""
+    g, S, G = c5
+    plain = bc.brandes(G, S).cpu().numpy()
+    pp = bc.brandes_pp(G, S, g.part).cpu().numpy()
+    assert rel_err(pp, plain) < FP64_TOL
+    pp32 = bc.brandes_pp(G, S, g.part, precision="fp32").cpu().numpy()
+    assert rel_err(pp32, plain) < FP32_TOL_C5
+    plain32 = bc.brandes(G, S, precision="fp32").cpu().numpy()
+    assert rel_err(plain32, plain) < FP32_TOL_C5

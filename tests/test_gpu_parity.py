@@ -15,9 +15,10 @@ from paper_1406_4173_gb300 import gen
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
-# FP32 dependencies: each delta(s|v) carries ~1e-7 relative rounding per DAG level; summed
-# over sources in FP64 the relative error stays well below this bound on these graphs.
-FP32_TOL = 2e-4
+# FP32-delta bar of the small parity graphs: 10x the largest error measured on them (1.96e-7,
+# `chunglu-u-hub` with S = V; the others 3.1e-8 to 1.4e-7).  The per-source dependencies are
+# formed in FP32 in a fixed order per lane, so the error does not vary from run to run.
+FP32_TOL = 2e-6
 INF32 = np.iinfo(np.int32).max
 
 

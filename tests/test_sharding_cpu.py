@@ -1,7 +1,12 @@
-"""Multi-GPU source sharding, exercised on CPU: world_size-2 gloo ranks each compute the
-partial betweenness of their shard of sources (targets stay all of S) with the oracle, one
-all-reduce sums the FP64 partials, and the sum must equal the unsharded result.  This is the
-host-side logic of the sharded multi-GPU layout (each rank a GPU, one sum-reduce of bc[n])."""
+"""Multi-GPU source sharding, exercised on CPU with world-size-2 and -3 gloo ranks.
+
+Each rank runs the package's sharded driver (``sharded.sharded_sum``) with the CPU oracle as
+its per-rank compute: the shard's sources come from the library's own shard rule
+(``bcpp_shard_bounds`` through the C ABI, which needs no GPU), the oracle computes their
+partial betweenness with all of S as targets, and the driver's FP64 all-reduce sums the
+partials.  Every rank must end up with the unsharded oracle result, for plain Brandes and for
+Brandes++.  On GPUs the same driver runs the library's sharded calls and reduces over NCCL.
+"""
 import os
 import socket
 
@@ -20,9 +25,15 @@ def _free_port():
     return p
 
 
-def shard_bounds(nsources, rank, world):
-    """Contiguous shard of the sources (the library's rule for shard_index/shard_count)."""
-    return nsources * rank // world, nsources * (rank + 1) // world
+def _oracle_shard(fn, g, S, r, R, **kw):
+    """The oracle's partial sum over the sources of shard r of R (positions in S's order,
+    bounds from the library), with all of S as targets."""
+    from paper_1406_4173_gb300 import api
+    s0, s1 = api.shard_bounds(len(S), r, R)
+    mine = S[s0:s1]
+    order = np.concatenate([mine, np.setdiff1d(S, mine)]).astype(np.int32)
+    out = fn(g, order, nsrc=len(mine), halve=False, **kw)
+    return torch.from_numpy(np.ascontiguousarray(out[0]))
 
 
 def _worker(rank, world, port, out_path):
@@ -30,36 +41,41 @@ def _worker(rank, world, port, out_path):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import oracle
-    from paper_1406_4173_gb300 import gen
-    g = gen.planted_partition(400, 4, 0.05, 0.004, seed=21)
+    from paper_1406_4173_gb300 import gen, sharded
+    g = gen.planted_partition(400, 4, 0.05, 0.004, seed=21, wmax=3)
     S = gen.sample_targets(g.n, 150, seed=21)
-    s0, s1 = shard_bounds(len(S), rank, world)
-    mine = S[s0:s1]
-    rest = np.setdiff1d(S, mine)
-    order = np.concatenate([mine, rest]).astype(np.int32)
-    part, _ = oracle.brandes(g, order, nsrc=len(mine), halve=False)
-    t = torch.from_numpy(part)
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    if rank == 0:
-        full, _ = oracle.brandes(g, S, halve=False)
-        np.save(out_path, np.stack([t.numpy(), full]))
+    plain = sharded.sharded_sum(lambda r, R: _oracle_shard(oracle.brandes, g, S, r, R))
+    pp = sharded.sharded_sum(lambda r, R: _oracle_shard(oracle.brandes_pp, g, S, r, R, part=g.part))
+    full, _ = oracle.brandes(g, S, halve=False)
+    np.save(out_path + f".{rank}.npy", np.stack([plain.numpy(), pp.numpy(), full]))
     dist.barrier()
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world", [2])
-def test_source_shards_sum_to_full(tmp_path, world):
-    out = str(tmp_path / "res.npy")
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_driver_sums_to_full(tmp_path, world):
+    out = str(tmp_path / "res")
     mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
-    got, full = np.load(out)
-    assert np.max(np.abs(got - full) / np.maximum(np.abs(full), 1.0)) < 1e-12
+    for r in range(world):
+        plain, pp, full = np.load(out + f".{r}.npy")
+        assert np.max(np.abs(plain - full) / np.maximum(np.abs(full), 1.0)) < 1e-12
+        assert np.max(np.abs(pp - full) / np.maximum(np.abs(full), 1.0)) < 1e-12
 
 
-def test_shard_bounds_cover_exactly():
-    for nb in (0, 1, 5, 63, 1563, 50000):
-        for world in (1, 2, 3, 8):
-            cov = []
+def test_library_shard_bounds_cover_exactly():
+    """The library's shard rule splits [0, n) into `count` contiguous, disjoint, covering
+    ranges whose sizes differ by at most one, and refuses invalid arguments."""
+    from paper_1406_4173_gb300 import api
+    for ns in (0, 1, 5, 63, 1563, 4096, 50000):
+        for world in (1, 2, 3, 7, 8):
+            cov, sizes = [], []
             for r in range(world):
-                a, b = shard_bounds(nb, r, world)
+                a, b = api.shard_bounds(ns, r, world)
                 cov.extend(range(a, b))
-            assert cov == list(range(nb))
+                sizes.append(b - a)
+            assert cov == list(range(ns))
+            assert max(sizes) - min(sizes) <= 1
+    assert api.shard_bounds(10, 0, 0) == (0, 10)
+    for bad in ((10, 2, 2), (10, -1, 2), (-1, 0, 1)):
+        with pytest.raises(api.BcppError):
+            api.shard_bounds(*bad)
