@@ -103,6 +103,10 @@ typedef struct {
     float ms_centrality;       /* Centrality step */
     float ms_total;            /* whole call, device time */
     int64_t kernel_launches;   /* kernels this call launched */
+    float ms_batch_forward;    /* shortest-path batches (plain Brandes, Brandes_SK): the time each batch
+                                * spent in its forward pass (Eq. 2 / Eq. 11), summed over the batches;
+                                * batches run concurrently, so this exceeds the kernel time */
+    float ms_batch_backward;   /* the same for the dependency pass (Eq. 7 / Eq. 12) */
 } bcpp_stats;
 
 /* Fill opts with the defaults listed above. */

@@ -47,7 +47,8 @@ class c_stats(ctypes.Structure):
                 ("k", ctypes.c_int32), ("lcs", ctypes.c_int32), ("table_entries", ctypes.c_int64),
                 ("ms_build_sk", ctypes.c_float), ("ms_brandes_sk", ctypes.c_float),
                 ("ms_centrality", ctypes.c_float), ("ms_total", ctypes.c_float),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("ms_batch_forward", ctypes.c_float),
+                ("ms_batch_backward", ctypes.c_float)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -28,8 +28,9 @@ struct bcpp_ctx {
     int device = 0;
     int num_sms = 0;
     std::vector<PoolBlock> pool;
-    uint32_t* flags = nullptr;       // device [FLAG_COUNT]
-    uint32_t* hflags = nullptr;      // pinned host copy
+    uint32_t* flags = nullptr;       // device [FLAG_COUNT], followed by the two phase timers
+    uint32_t* hflags = nullptr;      // pinned host copy (same layout)
+    unsigned long long* phase = nullptr;    // device [2]: forward / backward batch time (ns)
     int64_t launches = 0;
     int order_factor = 8;            // settled-entry capacity per node of a batch (retry: worst case)
     cudaEvent_t ev[8] = {};
@@ -130,15 +131,18 @@ struct Status {
         if (r__ != BCPP_OK) return r__;              \
     } while (0)
 
+// status flags and the two 64-bit phase timers behind them: one allocation, one copy
+constexpr size_t FLAG_BYTES = FLAG_COUNT * sizeof(uint32_t) + 2 * sizeof(unsigned long long);
+
 int sync_flags(bcpp_ctx* c) {
-    CK_CUDA(cudaMemcpyAsync(c->hflags, c->flags, FLAG_COUNT * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    CK_CUDA(cudaMemcpyAsync(c->hflags, c->flags, FLAG_BYTES, cudaMemcpyDeviceToHost, c->stream));
     CK_CUDA(cudaStreamSynchronize(c->stream));
     CK_CUDA(cudaGetLastError());
     return BCPP_OK;
 }
 
 int reset_flags(bcpp_ctx* c) {
-    CK_CUDA(cudaMemsetAsync(c->flags, 0, FLAG_COUNT * sizeof(uint32_t), c->stream));
+    CK_CUDA(cudaMemsetAsync(c->flags, 0, FLAG_BYTES, c->stream));
     return BCPP_OK;
 }
 
@@ -206,6 +210,22 @@ __global__ void part_flag_kernel(const int32_t* part, int32_t n, int32_t j, uint
         flag[i] = part[i] == j ? 1 : 0;
 }
 // (sum, comp) += x, Neumaier, element-wise
+// Brandes++All grouping: key = part (checked against [0, k)), value = node, and the part sizes
+__global__ void group_by_part_kernel(const int32_t* part, int32_t n, int32_t k, uint64_t* keys, uint32_t* vals,
+                                     int64_t* cnt, uint32_t* flags) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = part[v];
+        if (p < 0 || p >= k) {
+            flag_invalid(flags, WHY_PART);
+            keys[v] = 0;
+        } else {
+            keys[v] = (uint64_t)p;
+            atomicAdd(reinterpret_cast<unsigned long long*>(cnt + p), 1ull);
+        }
+        vals[v] = (uint32_t)v;
+    }
+}
+
 __global__ void accumulate_kernel(const double* x, int32_t n, double* sum, double* comp) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double s = sum[i], c = comp[i];
@@ -485,7 +505,12 @@ struct Timer {
 
 int finish_status(bcpp_ctx* c, bcpp_stats* st) {
     CK_RC(sync_flags(c));
-    if (st) st->sigma_overflow = c->hflags[FLAG_SIGMA_OVF] ? 1u : 0u;
+    if (st) {
+        st->sigma_overflow = c->hflags[FLAG_SIGMA_OVF] ? 1u : 0u;
+        const unsigned long long* hp = reinterpret_cast<const unsigned long long*>(c->hflags + FLAG_COUNT);
+        st->ms_batch_forward = (float)(hp[0] * 1e-6);
+        st->ms_batch_backward = (float)(hp[1] * 1e-6);
+    }
     if (c->hflags[FLAG_INVALID]) return BCPP_EINVAL;
     if (c->hflags[FLAG_CAPACITY]) return BCPP_ECAPACITY;
     if (c->hflags[FLAG_SIGMA_OVF]) return BCPP_EOVERFLOW_SIGMA;
@@ -887,6 +912,7 @@ int plain_prepare(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS
     P.items_static = 0;
     P.item_counter = r.ws.counter.p;
     P.flags = c->flags;
+    P.phase_ns = c->phase;
     return BCPP_OK;
 }
 
@@ -1322,6 +1348,7 @@ int pp_emit(bcpp_ctx* c, PpRun& r, Timer* tbr, Timer* tce) {
             P.bc_map = K.sknode.p;
             P.item_counter = r.ws.counter.p;
             P.flags = c->flags;
+            P.phase_ns = c->phase;
             if (tbr) tbr->start();
             ls_launch(fp32, !g->directed, r.A, P, r.ws.W, r.items.p, r.nitems, r.slots, c->stream, r.spl, r.cl,
                       r.ws.narrow);
@@ -1339,6 +1366,7 @@ int pp_emit(bcpp_ctx* c, PpRun& r, Timer* tbr, Timer* tce) {
             P.bc_map = K.sknode.p;
             P.items_static = 1;
             P.flags = c->flags;
+            P.phase_ns = c->phase;
             if (tbr) tbr->start();
             ls_launch(fp32, !g->directed, r.A, P, r.ws.W, r.items.p + c0, cn, cn, c->stream, 1, r.cl);
             c->launches++;
@@ -1580,26 +1608,34 @@ int brandes_pp_all_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* part, in
     uint64_t wmax = 1;
     CK_RC(validate_csr(c, g, &wmax));
     if (n == 0) return BCPP_OK;
-    std::vector<int32_t> hp(n);
-    CK_RC(to_host(c, hp.data(), part, n));
-    for (int32_t v = 0; v < n; v++)
-        if (hp[v] < 0 || hp[v] >= k) return BCPP_EINVAL;
-    // nodes grouped by part
+    // nodes grouped by part on the device (a stable radix sort keyed by part, so each part keeps
+    // increasing node ids) with the range check of the partition; the host reads only the k + 1
+    // part offsets, which it needs to enumerate the pairs
+    const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 8192);
+    DBuf<uint64_t> gkeys(c, n), gkb(c, n);
+    DBuf<uint32_t> gvals(c, n), gvb(c, n);
+    DBuf<int64_t> gcnt(c, (int64_t)k + 1), goff(c, (int64_t)k + 1), ghist(c, radix_hist_elems(n)),
+        gtmp(c, scan_tmp_elems(std::max<int64_t>(radix_hist_elems(n), (int64_t)k + 1)));
+    CK_ALLOC(gkeys); CK_ALLOC(gkb); CK_ALLOC(gvals); CK_ALLOC(gvb);
+    CK_ALLOC(gcnt); CK_ALLOC(goff); CK_ALLOC(ghist); CK_ALLOC(gtmp);
+    CK_CUDA(cudaMemsetAsync(gcnt.p, 0, ((size_t)k + 1) * sizeof(int64_t), c->stream));
+    group_by_part_kernel<<<blocks, 256, 0, c->stream>>>(part, n, k, gkeys.p, gvals.p, gcnt.p, c->flags);
+    c->launches++;
+    CK_RC(sync_flags(c));
+    if (c->hflags[FLAG_INVALID]) return BCPP_EINVAL;
+    radix_sort_pairs(gkeys.p, gvals.p, gkb.p, gvb.p, n, bits_for((uint64_t)k), ghist.p, gtmp.p, c->stream,
+                     c->launches);
+    exclusive_scan<int64_t>(gcnt.p, goff.p, (int64_t)k + 1, nullptr, gtmp.p, c->stream, c->launches);
     std::vector<int64_t> off((size_t)k + 1, 0);
-    for (int32_t v = 0; v < n; v++) off[hp[v] + 1]++;
-    for (int32_t i = 0; i < k; i++) off[i + 1] += off[i];
-    std::vector<int32_t> byp(n), fill(off.begin(), off.end() - 1);
-    for (int32_t v = 0; v < n; v++) byp[fill[hp[v]]++] = v;
-    DBuf<int32_t> dbyp(c, n);
+    CK_RC(to_host(c, off.data(), goff.p, (int64_t)k + 1));
+    const int32_t* dbyp = reinterpret_cast<const int32_t*>(gvals.p);   // node ids < 2^31
     DBuf<double> sum(c, n), comp(c, n);
-    CK_ALLOC(dbyp); CK_ALLOC(sum); CK_ALLOC(comp);
-    CK_RC(to_dev(c, dbyp.p, byp.data(), n));
+    CK_ALLOC(sum); CK_ALLOC(comp);
     CK_CUDA(cudaMemsetAsync(sum.p, 0, (size_t)n * sizeof(double), c->stream));
     CK_CUDA(cudaMemsetAsync(comp.p, 0, (size_t)n * sizeof(double), c->stream));
     InCsr Tin;
     if (g->directed) CK_RC(build_in_csr(c, g, Tin));
     Timer tb(c);
-    const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 8192);
     // Build_SK once on P: every pair reads the tables of the parts it keeps from it
     Skeleton K0;
     tb.start();
@@ -1641,10 +1677,10 @@ int brandes_pp_all_dev(bcpp_ctx* c, const bcpp_graph* g, const int32_t* part, in
             part_flag_kernel<<<blocks, 256, 0, lc->stream>>>(part, n, j, L.dflag.p);
             lc->launches++;
             // singletons: P_i followed by P_j (P_i alone when i == j)
-            CK_CUDA(cudaMemcpyAsync(L.pair.p, dbyp.p + off[i], (size_t)ni * 4, cudaMemcpyDeviceToDevice, lc->stream));
+            CK_CUDA(cudaMemcpyAsync(L.pair.p, dbyp + off[i], (size_t)ni * 4, cudaMemcpyDeviceToDevice, lc->stream));
             int32_t nsing = ni;
             if (i != j) {
-                CK_CUDA(cudaMemcpyAsync(L.pair.p + ni, dbyp.p + off[j], (size_t)nj * 4, cudaMemcpyDeviceToDevice,
+                CK_CUDA(cudaMemcpyAsync(L.pair.p + ni, dbyp + off[j], (size_t)nj * 4, cudaMemcpyDeviceToDevice,
                                         lc->stream));
                 nsing += nj;
             }
@@ -1764,6 +1800,7 @@ int batched_dev(bcpp_ctx* c, int32_t ngraphs, const int64_t* node_ptr_dev, const
     P.srcs = srcs.p;
     P.item_counter = ws.counter.p;
     P.flags = c->flags;
+    P.phase_ns = c->phase;
     tb.start();
     ls_launch(fp32, true, A, P, ws.W, items.p, nitems, slots, c->stream, spl, 1, ws.narrow);
     c->launches++;
@@ -2181,10 +2218,18 @@ int bcpp_create(bcpp_ctx** out, void* stream) {
     c->stream = (cudaStream_t)stream;
     if (cudaGetDevice(&c->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
-        cudaMalloc(&c->flags, FLAG_COUNT * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMallocHost(&c->hflags, FLAG_COUNT * sizeof(uint32_t)) != cudaSuccess) {
+        cudaMalloc(&c->flags, FLAG_BYTES) != cudaSuccess ||
+        cudaMallocHost(&c->hflags, FLAG_BYTES) != cudaSuccess) {
         cudaGetLastError();
         if (c->flags) cudaFree(c->flags);
+        delete c;
+        return BCPP_ECUDA;
+    }
+    c->phase = reinterpret_cast<unsigned long long*>(c->flags + FLAG_COUNT);
+    if (cudaMemset(c->flags, 0, FLAG_BYTES) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(c->flags);
+        cudaFreeHost(c->hflags);
         delete c;
         return BCPP_ECUDA;
     }

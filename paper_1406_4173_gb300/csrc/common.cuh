@@ -62,10 +62,23 @@ __device__ __forceinline__ void neumaier_add(double& s, double& c, double x) {
     s = t;
 }
 
-// a*b + acc on uint64 with overflow detection
+// a + acc on uint64 with overflow detection
+__device__ __forceinline__ uint64_t add_ck(uint64_t acc, uint64_t a, bool& ovf) {
+    const uint64_t t = acc + a;
+    if (t < acc) ovf = true;
+    return t;
+}
+
+// a*b + acc on uint64 with overflow detection; factors below 2^32 (the common case) take one
+// 32 x 32 -> 64-bit multiply, which cannot overflow
 __device__ __forceinline__ uint64_t madd_ck(uint64_t acc, uint64_t a, uint64_t b, bool& ovf) {
-    uint64_t p = a * b;
-    if (b != 1 && __umul64hi(a, b) != 0) ovf = true;
+    uint64_t p;
+    if (((a | b) >> 32) == 0) {
+        p = (uint64_t)(uint32_t)a * (uint32_t)b;
+    } else {
+        p = a * b;
+        if (__umul64hi(a, b) != 0) ovf = true;
+    }
     uint64_t t = acc + p;
     if (t < acc) ovf = true;
     return t;

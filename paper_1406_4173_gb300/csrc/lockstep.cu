@@ -22,6 +22,8 @@
 // the next entry is fetched while the current one is processed, a group of arcs issues all its
 // distance-row loads and then all its sigma (or c) loads together, bucket marks and
 // partial-sum updates are fire-and-forget atomics.
+#include <algorithm>
+
 #include "lockstep.cuh"
 
 namespace bcpp {
@@ -34,20 +36,16 @@ void ls_launch_f32(int spl, int cl, bool fused, bool weighted, bool mult, bool n
 
 namespace {
 
-__global__ void ls_reset_kernel(const LsSlots W) {
-    const int slot = blockIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int32_t* d = W.d + (int64_t)slot * W.cap_n * LS_LANES;
-    const LsEnt* order = W.order + (int64_t)slot * W.cap_order;
-    const int olen = W.hdr[slot * 4 + 0];
-    for (int e = warp; e < olen; e += blockDim.x / 32) d[(int64_t)order[e].u * LS_LANES + lane] = DINF;
-    __syncthreads();
-    if (threadIdx.x == 0) W.hdr[slot * 4 + 0] = 0;
-}
-
 __global__ void fill_i32_kernel(int32_t* p, int32_t v, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = v;
+}
+
+// 16-byte stores (p 16-byte aligned, n4 groups of four values)
+__global__ void fill_i32x4_kernel(int4* p, int32_t v, int64_t n4) {
+    const int4 q = make_int4(v, v, v, v);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = q;
 }
 
 }  // namespace
@@ -67,12 +65,21 @@ void ls_launch(bool fp32_delta, bool fused, const LsArena& A, const LsParams& P,
     else ls_launch_f64(spl, cl, fused, weighted, mult, narrow, A, P, W, items, nitems, slots, st);
 }
 
+// Every distance row of the first `slots` slots back to "unreached": a streaming fill of the
+// whole region (slots x cap_n rows of 128 bytes) costs a fraction of a scatter over the settled
+// entries, whose dependent loads of the order list leave the GPU latency-bound.
 void ls_reset_launch(const LsSlots& W, int slots, cudaStream_t st) {
-    if (slots > 0) ls_reset_kernel<<<slots, 512, 0, st>>>(W);
+    if (slots > 0) fill_i32(W.d, DINF, (int64_t)slots * W.cap_n * LS_LANES, st);
 }
 
 void fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t st) {
     if (n <= 0) return;
+    if ((reinterpret_cast<uintptr_t>(p) & 15) == 0 && (n & 3) == 0) {
+        const int64_t n4 = n / 4;
+        const int64_t blocks = std::min<int64_t>((n4 + 255) / 256, 152 * 16);
+        fill_i32x4_kernel<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<int4*>(p), v, n4);
+        return;
+    }
     int64_t blocks = (n + 255) / 256;
     if (blocks > 65536) blocks = 65536;
     fill_i32_kernel<<<(unsigned)blocks, 256, 0, st>>>(p, v, n);

@@ -67,6 +67,7 @@ struct LsParams {
     int items_static;            // 1: item index = slot
     int* item_counter;           // dynamic item counter (zeroed before launch)
     uint32_t* flags;
+    unsigned long long* phase_ns;   // nullptr or [2]: summed forward / backward time of the batches (ns)
 };
 
 // One settled (node, step) entry: the node and its out-arc range, read with one 16-byte load.
@@ -101,14 +102,14 @@ struct LsSlots {
 // only).  cl = CTAs per batch (1, 2 or 4; with 2 or 4 they form a thread-block cluster that
 // shares the batch's control state through distributed shared memory; spl = 1 only).
 // narrow: one-byte distance rows and 32-bit path-count rows (unit weights, LS_BRANDES only;
-// ignored otherwise), for slots whose distance rows start as 0xff bytes; a batch deeper than
-// 253 levels or with a count of 2^32 or more aborts with FLAG_DEPTH and FLAG_CAPACITY, and the
-// call reruns with int32 / uint64 rows.
+// ignored otherwise), for slots whose distance rows start as 0xff bytes; a batch reaching
+// distance 254 or a count of 2^32 or more aborts with FLAG_DEPTH and FLAG_CAPACITY, and the call
+// reruns with int32 / uint64 rows.
 void ls_launch(bool fp32_delta, bool fused, const LsArena& A, const LsParams& P, const LsSlots& W,
                const LsItem* items, int nitems, int slots, cudaStream_t st, int spl = 1, int cl = 1,
                bool narrow = false);
 
-// Restore the distance rows touched by LS_SKEL batches to "unreached".
+// Restore the distance rows of LS_SKEL slots to "unreached".
 void ls_reset_launch(const LsSlots& W, int slots, cudaStream_t st);
 
 // Fill helpers

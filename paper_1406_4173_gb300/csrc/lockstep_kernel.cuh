@@ -188,8 +188,15 @@ __device__ __forceinline__ bool row_has(const uint8_t*, int32_t) { return true; 
 // Scalar control state of one batch; with a cluster it lives in the leader CTA's shared memory
 // and the other CTAs reach it through distributed shared memory.
 struct LsCtl {
-    int item, pos, next, D, done, maxpush, nsteps, err, end;
+    int item, pos, next, D, done, maxpush, nsteps, err, end, iters;
+    unsigned long long t0, t1;   // batch start and end of its forward pass (global timer, ns)
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // Fetch the next entry index of the current step for this warp (dynamic scheduling).
 __device__ __forceinline__ int fetch_entry(int* next, int lane) {
@@ -298,21 +305,36 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
         }
         if (leader) {
             bflag[0] = 1;
-            ctl->pos = 0; ctl->D = 0; ctl->maxpush = 0; ctl->nsteps = 0; ctl->err = 0;
+            ctl->pos = 0; ctl->D = 0; ctl->maxpush = 0; ctl->nsteps = 0; ctl->err = 0; ctl->iters = 0;
+            if (P.phase_ns) ctl->t0 = global_ns();
         }
         sync();
 
         // ------------------------------------------------------------------ forward
         for (;;) {
             if (leader) {
-                // Integer weights: the next non-empty bucket up to the largest tentative distance.
-                // Unit weights: the levels are consecutive, and the step after the last level
-                // finds its bucket empty and leaves maxpush below D.
+                // Integer weights: the next non-empty bucket.  Every pending tentative distance
+                // lies in [D, D + max w] (a step at D' < D relaxes to at most D' + max w), so
+                // the nb = max w + 1 buckets from D hold all of them and the batch is done when
+                // none of them is flagged.  Unit weights: the levels are consecutive, and the
+                // step after the last level finds its bucket empty and leaves maxpush below D.
                 int D = ctl->D;
-                if constexpr (WEIGHTED)
-                    while (D <= ctl->maxpush && bflag[D % P.nb] == 0) D++;
+                if constexpr (WEIGHTED) {
+                    int i = 0;
+                    while (i < P.nb && bflag[(D + i) % P.nb] == 0) i++;
+                    D += i;
+                    ctl->done = i == P.nb || ctl->err;
+                } else {
+                    ctl->done = (D > ctl->maxpush) || ctl->err;
+                }
                 ctl->D = D;
-                ctl->done = (D > ctl->maxpush) || ctl->err;
+                // Bounded loop: a batch has at most one step per distinct distance, at most
+                // (nb - 1)(n - 1) + 1 of them; more would mean corrupted state, which ends the
+                // batch with the capacity flag instead of spinning.
+                if (!ctl->done && ++ctl->iters > (int64_t)(P.nb - 1) * n + 2) {
+                    ctl->err = 1;
+                    ctl->done = 1;
+                }
                 if (!ctl->done) {
                     if constexpr (WEIGHTED) bflag[D % P.nb] = 0;
                     if (ctl->nsteps >= W.cap_steps) {
@@ -437,8 +459,10 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                             for (int s = 0; s < SPL; s++)
                                 if constexpr (NARROW)
                                     acc[s] += sp[k][s];   // parents' counts < 2^32, fewer than 2^31 parents
-                                else if (sp[k][s])
-                                    acc[s] = madd_ck(acc[s], sp[k][s], MULT ? mk[k] : 1ull, ovf);
+                                else if (MULT)
+                                    acc[s] = madd_ck(acc[s], sp[k][s], mk[k], ovf);
+                                else
+                                    acc[s] = add_ck(acc[s], sp[k][s], ovf);
                     };
                     // relax the out-arcs: lower tentative distances, mark improved heads
                     auto relax_group = [&](auto tag, const int32_t* vv, const int32_t* ww, const int32_t (*dv)[SPL],
@@ -470,10 +494,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                                     int bk = dmod + ww[k];
                                     if (bk >= P.nb) bk -= P.nb;
                                     mark_head(bm + (int64_t)bk * W.bm_words, vv[k]);
-                                    if constexpr (WEIGHTED) {
-                                        bflag[bk] = 1;
-                                        atomicMax(&ctl->maxpush, nd);
-                                    }
+                                    if constexpr (WEIGHTED) bflag[bk] = 1;
                                 }
                             }
                         }
@@ -540,6 +561,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
         sync();
         const int nsteps = ctl->nsteps;
         const int olen = min(ctl->pos, (int)W.cap_order);
+        if (leader && P.phase_ns) ctl->t1 = global_ns();
         if (ctl->err) {
             // a list outgrew its bound: report it and leave the slot clean for the next batch
             if (leader) atomicOr(&P.flags[FLAG_CAPACITY], 1u);
@@ -668,6 +690,11 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
             }
         }
 
+        if (leader && P.phase_ns) {
+            const unsigned long long t2 = global_ns();
+            atomicAdd(&P.phase_ns[0], ctl->t1 - ctl->t0);
+            atomicAdd(&P.phase_ns[1], t2 - ctl->t1);
+        }
         if (bat && (P.mode == LS_BRANDES || P.mode == LS_SKEL)) {
             // Neumaier step of every touched node's batch sum into the slot's (sum, compensation):
             // the exchange hands each node's sum to exactly one of its entries (a node has one

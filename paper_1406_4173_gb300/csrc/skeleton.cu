@@ -237,16 +237,23 @@ __global__ void target_ids_kernel(const int32_t* S, int32_t nS, const int32_t* s
 }
 
 // Tiled Centrality: one block (16 warps) per unit of up to 64 non-frontier nodes and one slot,
-// each warp CTV nodes, lanes are the slot's sources.  The part's frontier state rows (d with
-// sigma in the forward pass, d with c in the backward pass) are staged in shared memory FT
-// frontiers at a time with coalesced loads, and each warp holds its nodes' table entries of
-// the tile in registers (lane = frontier) and broadcasts them by shuffle, so the inner loop over
-// (frontier, node) reads no global memory.  Forward: the distance and count of each node through
-// its entry frontiers; backward: the dependency through the exit frontiers that stay on a
-// shortest path (Eq. 13 with the tight-frontier tests).
+// each warp CTV nodes, lanes are the slot's sources.  The part's frontier state rows (d, with
+// sigma or c) are staged in shared memory FT frontiers at a time with coalesced loads, and each
+// warp holds its nodes' table entries of the tile in registers (lane = frontier) and broadcasts
+// them by shuffle, so the inner loop over (frontier, node) reads no global memory.
+//
+// Forward, in two sweeps over the entry frontiers: first the distance of each node, a pure
+// min-plus d(s,v) = min_f d(s,f) + d_i(f,v); then its path count, summed over the frontiers
+// that attain that minimum, sigma(s,v) = sum_f sigma(s,f) sigma_i(f,v), so that every count
+// product is a final one (no partial sums to reset when a smaller distance turns up).
+// Backward: the dependency through the exit frontiers that stay on a shortest path (Eq. 13
+// with the tight-frontier tests).  Distances are handled as uint32: real distances are below
+// DINF = 2^31 - 1, so a sum of two values never wraps, and a sum with an unreachable term is at
+// least DINF, above every real distance.
 constexpr int CTV = 4;          // nodes per warp
 constexpr int CT_WARPS = 16;    // warps per block: 64 nodes = one unit
 constexpr int FT = 32;          // frontiers per tile
+constexpr uint32_t CT_NONE = 0xffffffffu;   // "unreachable" after the min-plus sweep (no sum equals it)
 
 template <typename DT>
 __global__ void __launch_bounds__(CT_WARPS * 32)
@@ -254,7 +261,7 @@ centrality_tiled_kernel(const CentralityUnit* __restrict__ units, SkTables T, co
                         const int32_t* __restrict__ skbase, const int32_t* __restrict__ d_all,
                         const uint64_t* __restrict__ sg_all, const DT* __restrict__ dl_all, int64_t cap_n,
                         double* bc_sum, double* bc_cmp, int64_t cap_bc, uint32_t* flags, int slot_major) {
-    __shared__ int32_t s_d[FT][32];
+    __shared__ uint32_t s_d[FT][32];
     __shared__ uint64_t s_x[FT][32];      // sigma rows (forward) or c rows (backward, as DT bits)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const CentralityUnit U = units[slot_major ? blockIdx.y : blockIdx.x];
@@ -267,94 +274,121 @@ centrality_tiled_kernel(const CentralityUnit* __restrict__ units, SkTables T, co
     const int32_t vb = U.v0 + warp * CTV;
     int nv = U.v1 - vb;
     nv = nv < 0 ? 0 : (nv > CTV ? CTV : nv);
-    // distances as uint32: two finite distances are below 2^31, so their sum fits; "none" is
-    // 0xffffffff, above every sum
+    // ---- forward sweep 1: d(s,v) = min over entry frontiers of d(s,f) + d_i(f,v)
     uint32_t dv[CTV];
-    uint64_t sv[CTV];
 #pragma unroll
-    for (int j = 0; j < CTV; j++) { dv[j] = 0xffffffffu; sv[j] = 0; }
-    bool ovf = false;
-    // ---- forward: d(s,v) = min over entry frontiers, sigma(s,v) = sum over the tight ones
+    for (int j = 0; j < CTV; j++) dv[j] = CT_NONE;
     for (int32_t f0 = 0; f0 < nfi; f0 += FT) {
         const int nt = min(FT, nfi - f0);
         __syncthreads();
-        for (int x = threadIdx.x; x < nt * 32; x += CT_WARPS * 32) {
-            const int64_t o = fbase + (int64_t)(f0 + (x >> 5)) * 32 + (x & 31);
-            s_d[x >> 5][x & 31] = d_all[o];
-            s_x[x >> 5][x & 31] = sg_all[o];
-        }
-        int32_t tdv[CTV];
-        uint64_t tsv[CTV];
+        for (int x = threadIdx.x; x < nt * 32; x += CT_WARPS * 32)
+            s_d[x >> 5][x & 31] = (uint32_t)d_all[fbase + (int64_t)(f0 + (x >> 5)) * 32 + (x & 31)];
+        uint32_t tdv[CTV];
 #pragma unroll
-        for (int j = 0; j < CTV; j++) {
-            tdv[j] = DINF;
-            tsv[j] = 0;
-            if (j < nv && lane < nt) {
-                const int64_t o = t0 + (int64_t)(vb + j) * nfi + f0 + lane;
-                tdv[j] = T.td[o];
-                if (tdv[j] != DINF) tsv[j] = T.ts[o];
-            }
-        }
+        for (int j = 0; j < CTV; j++)
+            tdv[j] = (j < nv && lane < nt) ? (uint32_t)T.td[t0 + (int64_t)(vb + j) * nfi + f0 + lane] : (uint32_t)DINF;
         __syncthreads();
         for (int f = 0; f < nt; f++) {
-            const int32_t dsf = s_d[f][lane];
+            const uint32_t dsf = s_d[f][lane];
 #pragma unroll
             for (int j = 0; j < CTV; j++) {
-                const int32_t tdj = __shfl_sync(FULL, tdv[j], f);
-                if (tdj == DINF) continue;                     // warp-uniform
-                bool tight = false;
-                if (dsf != DINF) {
-                    const uint32_t c = (uint32_t)dsf + (uint32_t)tdj;
-                    if (c < dv[j]) { dv[j] = c; sv[j] = 0; }
-                    tight = c == dv[j];
+                const uint32_t tdj = __shfl_sync(FULL, tdv[j], f);
+                dv[j] = min(dv[j], dsf + tdj);
+            }
+        }
+    }
+    bool any_reach = false;
+#pragma unroll
+    for (int j = 0; j < CTV; j++) {
+        if (dv[j] >= (uint32_t)DINF) dv[j] = CT_NONE;
+        any_reach |= dv[j] != CT_NONE;
+    }
+    // ---- forward sweep 2: sigma(s,v) = sum over the entry frontiers that attain d(s,v)
+    uint64_t sv[CTV];
+#pragma unroll
+    for (int j = 0; j < CTV; j++) sv[j] = 0;
+    bool ovf = false;
+    if (__syncthreads_or(any_reach)) {
+        for (int32_t f0 = 0; f0 < nfi; f0 += FT) {
+            const int nt = min(FT, nfi - f0);
+            __syncthreads();
+            for (int x = threadIdx.x; x < nt * 32; x += CT_WARPS * 32) {
+                const int64_t o = fbase + (int64_t)(f0 + (x >> 5)) * 32 + (x & 31);
+                s_d[x >> 5][x & 31] = (uint32_t)d_all[o];
+                s_x[x >> 5][x & 31] = sg_all[o];
+            }
+            uint32_t tdv[CTV];
+            uint64_t tsv[CTV];
+#pragma unroll
+            for (int j = 0; j < CTV; j++) {
+                tdv[j] = (uint32_t)DINF;
+                tsv[j] = 0;
+                if (j < nv && lane < nt) {
+                    const int64_t o = t0 + (int64_t)(vb + j) * nfi + f0 + lane;
+                    tdv[j] = (uint32_t)T.td[o];
+                    if (tdv[j] != (uint32_t)DINF) tsv[j] = T.ts[o];
                 }
-                if (__any_sync(FULL, tight)) {
-                    const uint64_t tsj = shfl_u64(tsv[j], f);
-                    if (tight) sv[j] = madd_ck(sv[j], s_x[f][lane], tsj, ovf);
+            }
+            __syncthreads();
+            for (int f = 0; f < nt; f++) {
+                const uint32_t dsf = s_d[f][lane];
+#pragma unroll
+                for (int j = 0; j < CTV; j++) {
+                    const uint32_t tdj = __shfl_sync(FULL, tdv[j], f);
+                    const bool tight = dsf + tdj == dv[j];
+                    if (__any_sync(FULL, tight)) {
+                        const uint64_t tsj = shfl_u64(tsv[j], f);
+                        if (tight) sv[j] = madd_ck(sv[j], s_x[f][lane], tsj, ovf);
+                    }
                 }
             }
         }
     }
     // ---- backward: acc = sum over exit frontiers f on a shortest path of sigma_i(v,f) c(s,f)
     DT acc[CTV];
-    bool live = false;
+    bool live[CTV], any_live = false;
 #pragma unroll
     for (int j = 0; j < CTV; j++) {
         acc[j] = (DT)0;
-        live |= sv[j] != 0;
+        live[j] = sv[j] != 0;
+        any_live |= live[j];
     }
-    if (__syncthreads_or(live)) {
+    if (__syncthreads_or(any_live)) {
         for (int32_t f0 = 0; f0 < nfi; f0 += FT) {
             const int nt = min(FT, nfi - f0);
             __syncthreads();
             for (int x = threadIdx.x; x < nt * 32; x += CT_WARPS * 32) {
                 const int64_t o = fbase + (int64_t)(f0 + (x >> 5)) * 32 + (x & 31);
-                s_d[x >> 5][x & 31] = d_all[o];
+                s_d[x >> 5][x & 31] = (uint32_t)d_all[o];
                 DT cv = dl_all[o];
                 uint64_t bits = 0;
                 memcpy(&bits, &cv, sizeof(DT));
                 s_x[x >> 5][x & 31] = bits;
             }
-            int32_t tdv[CTV];
+            uint32_t tdv[CTV];
             uint64_t tsv[CTV];
 #pragma unroll
             for (int j = 0; j < CTV; j++) {
-                tdv[j] = DINF;
+                tdv[j] = (uint32_t)DINF;
                 tsv[j] = 0;
                 if (j < nv && lane < nt) {
                     const int64_t o = t0 + (int64_t)(vb + j) * nfi + f0 + lane;
-                    tdv[j] = T.tdr[o];
-                    if (tdv[j] != DINF) tsv[j] = T.tsr[o];
+                    tdv[j] = (uint32_t)T.tdr[o];
+                    if (tdv[j] != (uint32_t)DINF) tsv[j] = T.tsr[o];
                 }
             }
             __syncthreads();
             for (int f = 0; f < nt; f++) {
-                const int32_t dsf = s_d[f][lane];
+                const uint32_t dsf = s_d[f][lane];
+                const bool fin = dsf != (uint32_t)DINF;
 #pragma unroll
                 for (int j = 0; j < CTV; j++) {
-                    const int32_t tdj = __shfl_sync(FULL, tdv[j], f);
-                    if (tdj == DINF) continue;                 // warp-uniform
-                    const bool on = sv[j] != 0 && dsf != DINF && dv[j] + (uint32_t)tdj == (uint32_t)dsf;
+                    // a live node has a finite distance, and a sum with an unreachable exit
+                    // table entry exceeds every finite frontier distance.  (The shuffle is taken
+                    // by every lane before the test: a full-mask shuffle that some lanes skip
+                    // never completes.)
+                    const uint32_t tdj = __shfl_sync(FULL, tdv[j], f);
+                    const bool on = live[j] && fin && dv[j] + tdj == dsf;
                     if (__any_sync(FULL, on)) {
                         const uint64_t tsj = shfl_u64(tsv[j], f);
                         if (on) {

@@ -332,6 +332,12 @@ def _w_chunglu_1m(seed=0):
     return g, sample_targets(g.n, 4096, seed)
 
 
+def _w_chunglu_100k(seed=0):
+    sizes = np.full(100, 1000)
+    g = chung_lu_communities(100_000, sizes, 2.2, 16.0, 0.85, seed)
+    return g, sample_targets(g.n, 512, seed)
+
+
 def _w_chunglu_10k(seed=0):
     g = chung_lu_communities(10_000, np.full(10, 1000), 2.3, 10.0, 0.90, seed)
     return g, np.arange(g.n, dtype=np.int32)
@@ -360,6 +366,9 @@ WORKLOADS = {
     "planted_200k": (_w_planted_200k, "planted partition n=200,000, 100x2,000, p_in=0.005, p_out=9e-8 "
                                       "(about 1,800 inter-community edges), |S|=200: a small skeleton "
                                       "(N/n about 3%, M/m about 16%)"),
+    "chunglu_100k": (_w_chunglu_100k, "the chunglu_1m recipe at n=100,000: 100x1,000 communities, degree exp "
+                                      "2.2, mean 16, 85% intra, |S|=512 (the small case of full profiler "
+                                      "captures of Brandes_SK and Centrality)"),
     "chunglu_1m": (_w_chunglu_1m, "Chung-Lu n=1,000,000, 1,000x1,000 communities, degree exp 2.2, mean 16, "
                                   "85% intra, |S|=4,096"),
 }

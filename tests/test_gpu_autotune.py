@@ -55,3 +55,20 @@ def test_autotune_directed_weighted(bc):
     ref, _ = oracle.brandes(g, S)
     x = bc.brandes(G, S, precision="fp32", **tuned).cpu().numpy()
     assert rel_err(x, ref) <= 2e-6       # FP32-delta: measured 1.1e-7
+
+
+def test_autotune_batched_candidates_and_parity(bc):
+    """bcpp_autotune_batched times every (batch, CTAs per SM) candidate on the whole arena and
+    the tuned options give the oracle's betweenness for every graph."""
+    gs = [gen.erdos_renyi(int(n), min(1.0, 8.0 / max(n - 1, 1)), seed=300 + i) for i, n in
+          enumerate([64, 700, 1500, 2, 1, 300, 4096, 90, 129, 33, 650, 512])]
+    arena = bc.build_arena(gs)
+    tuned, times = bc.autotune_batched(arena)
+    assert (tuned["batch"], tuned["ctas_per_sm"]) in bc.api.AUTOTUNE_BATCHED_CANDIDATES
+    assert all(t > 0 for t in times.values()), times
+    assert times[(tuned["batch"], tuned["ctas_per_sm"])] == min(times.values())
+    got = bc.brandes_batched(arena, **tuned).cpu().numpy()
+    off = arena.node_ptr_host
+    for i, g in enumerate(gs):
+        ref, _ = oracle.brandes(g)
+        assert rel_err(got[off[i]:off[i + 1]], ref) <= 1e-12, i

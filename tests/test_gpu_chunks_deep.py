@@ -120,3 +120,26 @@ def test_weighted_grid_60x60_deep(bc):
     ref_s, _ = oracle.brandes(g, S)
     part = ((np.arange(g.n) // 60) // 12 * 5 + (np.arange(g.n) % 60) // 12).astype(np.int32)   # 5 x 5 tiles
     assert rel_err(bc.brandes_pp(G, S, part).cpu().numpy(), ref_s) < FP64_TOL
+
+
+def test_small_weights_long_distances(bc):
+    """Weights in [1, 4] on a 2,000-node path (distances up to about 5,000, thousands of steps per
+    batch with few distinct weights) and on a 40 x 40 grid, plain Brandes and Brandes++ in both
+    precisions."""
+    n = 2000
+    g = gen.with_weights(gen.path(n), 4, seed=96)
+    G = bc.graph_from_edgelist(g)
+    i = np.arange(n)
+    ref, _ = oracle.brandes(g)
+    assert rel_err(ref, i * (n - 1 - i)) < FP64_TOL
+    assert rel_err(bc.brandes(G).cpu().numpy(), ref) < FP64_TOL
+    assert rel_err(bc.brandes(G, precision="fp32").cpu().numpy(), ref) < FP32_TOL
+    _check_sssp(bc, G, g, np.array([0, 999, 1999], np.int32))
+    g2 = gen.with_weights(gen.grid(40, 40), 4, seed=97)
+    G2 = bc.graph_from_edgelist(g2)
+    S = gen.sample_targets(g2.n, 300, seed=98)
+    ref2, _ = oracle.brandes(g2, S)
+    assert rel_err(bc.brandes(G2, S).cpu().numpy(), ref2) < FP64_TOL
+    part = ((np.arange(g2.n) // 40) // 10 * 4 + (np.arange(g2.n) % 40) // 10).astype(np.int32)   # 4 x 4 tiles
+    assert rel_err(bc.brandes_pp(G2, S, part).cpu().numpy(), ref2) < FP64_TOL
+    assert rel_err(bc.brandes_pp(G2, S, part, precision="fp32").cpu().numpy(), ref2) < FP32_TOL
