@@ -89,6 +89,10 @@ typedef struct {
                                 * (targets stay all of S), so the shards' results add up to the
                                 * unsharded result (multi-GPU source sharding).  The order is the one
                                 * of order_sources (with order_sources = 0: S as given). */
+    int32_t pp_chunks;         /* Brandes++ with non-frontier nodes and more source batches than slots:
+                                * 0 (default) = one Brandes_SK launch over all batches with a set of
+                                * rows per batch for the Centrality step when device memory allows,
+                                * else static chunks of batches; 1 = static chunks (less memory) */
 } bcpp_opts;
 
 typedef struct {

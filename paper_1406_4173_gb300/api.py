@@ -39,7 +39,7 @@ class c_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("halve_undirected", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("validate", ctypes.c_int32), ("host_buffers", ctypes.c_int32),
                 ("order_sources", ctypes.c_int32), ("cluster", ctypes.c_int32), ("shard_index", ctypes.c_int32),
-                ("shard_count", ctypes.c_int32)]
+                ("shard_count", ctypes.c_int32), ("pp_chunks", ctypes.c_int32)]
 
 
 class c_stats(ctypes.Structure):
@@ -189,7 +189,7 @@ class Graph:
 
 
 def _opts(precision="fp64", halve=True, ctas_per_sm=0, host=False, order_sources=True, shard=None,
-          batch=0, cluster=0) -> c_opts:
+          batch=0, cluster=0, pp_chunks=0) -> c_opts:
     o = c_opts()
     load_library().bcpp_default_opts(ctypes.byref(o))
     o.precision = {"fp64": BCPP_FP64, "fp32": BCPP_FP32_DELTA, "fp32_delta": BCPP_FP32_DELTA}[precision]
@@ -201,6 +201,7 @@ def _opts(precision="fp64", halve=True, ctas_per_sm=0, host=False, order_sources
         o.shard_index, o.shard_count = int(shard[0]), int(shard[1])
     o.batch = int(batch)
     o.cluster = int(cluster)
+    o.pp_chunks = int(pp_chunks)
     return o
 
 
@@ -282,9 +283,11 @@ def brandes(G: Graph, S=None, precision: str = "fp64", halve: bool = True, ctx: 
 
 def brandes_pp(G: Graph, S, part, k: int | None = None, precision: str = "fp64", halve: bool = True,
                ctx: Context | None = None, ctas_per_sm: int = 0, order_sources: bool = True, out=None,
-               stats: bool = False, allow_overflow: bool = False, shard=None, batch: int = 0, cluster: int = 0):
+               stats: bool = False, allow_overflow: bool = False, shard=None, batch: int = 0, cluster: int = 0,
+               pp_chunks: int = 0):
     """Brandes++ (Build_SK, Brandes_SK, Centrality) for target set S (None = all nodes) and
-    node partition `part` with values in [0, k)."""
+    node partition `part` with values in [0, k).  pp_chunks=1 runs Brandes_SK in static chunks
+    of batches (less memory) instead of one pass with a set of rows per batch."""
     torch = _torch()
     ctx = ctx or default_context()
     dev = G.row_ptr.device
@@ -296,7 +299,8 @@ def brandes_pp(G: Graph, S, part, k: int | None = None, precision: str = "fp64",
     bc = out if out is not None else torch.empty(G.n, dtype=torch.float64, device=dev)
     st = c_stats()
     cg = G.c()
-    o = _opts(precision, halve, ctas_per_sm, order_sources=order_sources, shard=shard, batch=batch, cluster=cluster)
+    o = _opts(precision, halve, ctas_per_sm, order_sources=order_sources, shard=shard, batch=batch, cluster=cluster,
+              pp_chunks=pp_chunks)
     rc = load_library().bcpp_brandes_pp(ctx.handle, ctypes.byref(cg), None if nS == 0 else St.data_ptr(), nS,
                                         pt.data_ptr(), int(k), ctypes.byref(o), bc.data_ptr(), ctypes.byref(st))
     _check(rc, allow_overflow)

@@ -326,6 +326,8 @@ struct SlotWs {
     DBuf<int> counter;
     LsSlots W{};
     int slots = 0, nb = 0;
+    int row_states = 0;         // distance / count / dependency row sets (one per slot, or per item)
+    int sum_slots = 0;          // partial-sum sets (one per slot, or per item)
     int64_t rows = 0;
     bool narrow = false;        // one-byte distance rows (0xff = unreached)
 };
@@ -395,11 +397,11 @@ int choose_slots(bcpp_ctx* c, int nitems, int ctas_per_sm, int64_t per_slot, int
 int init_slots(bcpp_ctx* c, SlotWs& S) {
     const LsSlots& W = S.W;
     if (W.cap_bc > 0) {
-        CK_CUDA(cudaMemsetAsync(S.bcs.p, 0, (size_t)S.slots * W.cap_bc * sizeof(double), c->stream));
-        CK_CUDA(cudaMemsetAsync(S.bcc.p, 0, (size_t)S.slots * W.cap_bc * sizeof(double), c->stream));
-        CK_CUDA(cudaMemsetAsync(S.bcb.p, 0, (size_t)S.slots * W.cap_bc * sizeof(double), c->stream));
+        CK_CUDA(cudaMemsetAsync(S.bcs.p, 0, (size_t)S.sum_slots * W.cap_bc * sizeof(double), c->stream));
+        CK_CUDA(cudaMemsetAsync(S.bcc.p, 0, (size_t)S.sum_slots * W.cap_bc * sizeof(double), c->stream));
+        CK_CUDA(cudaMemsetAsync(S.bcb.p, 0, (size_t)S.sum_slots * W.cap_bc * sizeof(double), c->stream));
     }
-    fill_i32(S.d.p, S.narrow ? -1 : DINF, (int64_t)S.slots * S.rows * 32, c->stream);
+    fill_i32(S.d.p, S.narrow ? -1 : DINF, (int64_t)S.row_states * S.rows * 32, c->stream);
     c->launches++;
     CK_CUDA(cudaMemsetAsync(S.bm.p, 0, (size_t)S.slots * S.nb * W.bm_words * sizeof(uint32_t), c->stream));
     CK_CUDA(cudaMemsetAsync(S.bflag.p, 0, (size_t)S.slots * S.nb, c->stream));
@@ -408,16 +410,20 @@ int init_slots(bcpp_ctx* c, SlotWs& S) {
     return BCPP_OK;
 }
 
+// row_states / sum_slots: row sets and partial-sum sets when they differ from the slot count
+// (Brandes_SK with one row set per batch); 0 = one per slot.
 int alloc_slots(bcpp_ctx* c, SlotWs& S, int slots, int64_t cap_n, int nb, bool fp32, int64_t cap_bc, int spl,
-                int factor, bool init = true) {
+                int factor, bool init = true, int row_states = 0, int sum_slots = 0) {
     if (cap_n >= (1 << 25)) return BCPP_EINVAL;   // 32-bit row offsets inside a slot
     const int64_t cap_order = order_capacity(cap_n, factor, spl);
     const int64_t rows = cap_n * spl;              // rows of 32 values
     const int32_t cap_steps = step_capacity(cap_n, nb, cap_order);
     const int64_t bm_words = (cap_n + 31) / 32;
-    CK_ALLOC(S.d.alloc(c, (int64_t)slots * rows * 32));
-    CK_ALLOC(S.sg.alloc(c, (int64_t)slots * rows * 32));
-    CK_ALLOC(S.dl.alloc(c, (int64_t)slots * rows * 32 * (fp32 ? 4 : 8)));
+    if (row_states <= 0) row_states = slots;
+    if (sum_slots <= 0) sum_slots = slots;
+    CK_ALLOC(S.d.alloc(c, (int64_t)row_states * rows * 32));
+    CK_ALLOC(S.sg.alloc(c, (int64_t)row_states * rows * 32));
+    CK_ALLOC(S.dl.alloc(c, (int64_t)row_states * rows * 32 * (fp32 ? 4 : 8)));
     CK_ALLOC(S.order.alloc(c, (int64_t)slots * cap_order));
     CK_ALLOC(S.step_d.alloc(c, (int64_t)slots * cap_steps));
     CK_ALLOC(S.step_beg.alloc(c, (int64_t)slots * cap_steps));
@@ -426,11 +432,13 @@ int alloc_slots(bcpp_ctx* c, SlotWs& S, int slots, int64_t cap_n, int nb, bool f
     CK_ALLOC(S.bflag.alloc(c, (int64_t)slots * nb));
     CK_ALLOC(S.counter.alloc(c, 1));
     if (cap_bc > 0) {
-        CK_ALLOC(S.bcs.alloc(c, (int64_t)slots * cap_bc));
-        CK_ALLOC(S.bcc.alloc(c, (int64_t)slots * cap_bc));
-        CK_ALLOC(S.bcb.alloc(c, (int64_t)slots * cap_bc));
+        CK_ALLOC(S.bcs.alloc(c, (int64_t)sum_slots * cap_bc));
+        CK_ALLOC(S.bcc.alloc(c, (int64_t)sum_slots * cap_bc));
+        CK_ALLOC(S.bcb.alloc(c, (int64_t)sum_slots * cap_bc));
     }
     S.slots = slots;
+    S.row_states = row_states;
+    S.sum_slots = sum_slots;
     S.nb = nb;
     S.rows = rows;
     LsSlots& W = S.W;
@@ -1217,6 +1225,7 @@ struct PpRun {
     int32_t nt = 0;
     SlotWs ws;
     bool unit = true, mult = false;
+    bool rows_by_item = false;   // Brandes_SK in one dynamic pass with a row set per batch
     int nb = 2, spl = 1, nitems = 0, cl = 1, slots = 1;
     std::vector<CentralityUnit> hunits;
     DBuf<uint8_t> sk_in_s;
@@ -1276,14 +1285,32 @@ int pp_prepare(bcpp_ctx* c, const bcpp_graph* g, uint64_t wmax, const InCsr* Tin
     r.slots = r.nitems > 0 ? choose_slots(c, r.nitems, o.ctas_per_sm,
                                           slot_bytes(std::max(N, 1), r.nb, fp32, ef, r.spl), (int64_t)n * 24, r.cl)
                            : 1;
-    if (!r.hunits.empty() && r.nitems > 0) {
-        // with Centrality the batches run in static chunks of `slots`: make the chunks equal
-        // (128 batches on 76 slots run as 64 + 64 instead of 76 + 52)
-        const int chunks = div_up(r.nitems, r.slots);
-        r.slots = div_up(r.nitems, chunks);
+    if (!r.hunits.empty() && r.nitems > r.slots) {
+        // More batches than slots.  When memory allows, every batch gets its own set of distance,
+        // count and dependency rows (what the Centrality step reads) and its own partial sums, so
+        // Brandes_SK schedules all batches dynamically over the slots in one launch and one
+        // Centrality launch covers them all; otherwise the batches run in static chunks of
+        // `slots`, each followed by Centrality, with equal chunks (128 batches on 76 slots run as
+        // 64 + 64 instead of 76 + 52).
+        const int64_t Nc = std::max(N, 1);
+        const int64_t row_bytes = Nc * 32 * (4 + 8 + (fp32 ? 4 : 8));
+        const int64_t work_bytes = slot_bytes(Nc, r.nb, fp32, ef, 1) - row_bytes;
+        const int64_t need = (int64_t)r.nitems * (row_bytes + (int64_t)n * 24) + (int64_t)r.slots * work_bytes;
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        int64_t reusable = 0;
+        for (auto& b : c->pool)
+            if (!b.used) reusable += (int64_t)b.bytes;
+        if (!o.pp_chunks && need <= (int64_t)((double)(fr + reusable) * 0.80)) {
+            r.rows_by_item = true;
+        } else {
+            const int chunks = div_up(r.nitems, r.slots);
+            r.slots = div_up(r.nitems, chunks);
+        }
     }
-    // partial sums live in the lockstep slots; combine at the end
-    CK_RC(alloc_slots(c, r.ws, r.slots, std::max(N, 1), r.nb, fp32, n, r.spl, ef, false));
+    // partial sums live in the lockstep slots (or per batch); combine at the end
+    CK_RC(alloc_slots(c, r.ws, r.slots, std::max(N, 1), r.nb, fp32, n, r.spl, ef, false,
+                      r.rows_by_item ? r.nitems : 0, r.rows_by_item ? r.nitems : 0));
     r.ws.narrow = r.hunits.empty() && use_narrow(c, !r.unit);   // Centrality reads int32 rows
     if (r.nitems > 0) {
         CK_ALLOC(r.sk_in_s.alloc(c, N));
@@ -1356,7 +1383,33 @@ int pp_emit(bcpp_ctx* c, PpRun& r, Timer* tbr, Timer* tce) {
             if (tbr) tbr->stop();
             CK_CUDA(cudaGetLastError());
         }
-        for (int c0 = 0; c0 < r.nitems && !r.hunits.empty(); c0 += r.slots) {
+        if (!r.hunits.empty() && r.rows_by_item) {
+            // all batches in one dynamic Brandes_SK launch, each into its own rows, then one
+            // Centrality launch over all batches (row set and partial sums of batch i: index i)
+            LsParams P{};
+            P.mode = LS_SKEL;
+            P.nb = r.nb;
+            P.srcs = r.tsk.p;
+            P.in_s = r.sk_in_s.p;
+            P.bc_map = K.sknode.p;
+            P.item_counter = r.ws.counter.p;
+            P.rows_by_item = 1;
+            P.flags = c->flags;
+            P.phase_ns = c->phase;
+            if (tbr) tbr->start();
+            ls_launch(fp32, !g->directed, r.A, P, r.ws.W, r.items.p, r.nitems, r.slots, c->stream, 1, r.cl);
+            c->launches++;
+            if (tbr) tbr->stop();
+            CK_CUDA(cudaGetLastError());
+            if (tce) tce->start();
+            centrality_launch(fp32, r.units.p, (int)r.hunits.size(), r.nitems, T, K.pnodes.p, K.skbase.p, r.ws.W.d,
+                              r.ws.W.sg, r.ws.W.dl, r.ws.W.cap_n, r.ws.W.bc_sum, r.ws.W.bc_cmp, r.ws.W.cap_bc,
+                              c->flags, c->stream);
+            c->launches++;
+            if (tce) tce->stop();
+            CK_CUDA(cudaGetLastError());
+        }
+        for (int c0 = 0; c0 < r.nitems && !r.hunits.empty() && !r.rows_by_item; c0 += r.slots) {
             const int cn = std::min(r.slots, r.nitems - c0);
             LsParams P{};
             P.mode = LS_SKEL;
@@ -1383,7 +1436,7 @@ int pp_emit(bcpp_ctx* c, PpRun& r, Timer* tbr, Timer* tce) {
             c->launches++;
         }
     }
-    combine_launch(r.ws.W.bc_sum, r.ws.W.bc_cmp, r.slots, n, n, r.scale, r.bc_out, c->stream);
+    combine_launch(r.ws.W.bc_sum, r.ws.W.bc_cmp, r.ws.sum_slots, n, n, r.scale, r.bc_out, c->stream);
     c->launches++;
     CK_CUDA(cudaGetLastError());
     return BCPP_OK;
@@ -2188,6 +2241,7 @@ void bcpp_default_opts(bcpp_opts* o) {
     o->cluster = 0;
     o->shard_index = 0;
     o->shard_count = 0;
+    o->pp_chunks = 0;
 }
 
 int bcpp_shard_bounds(int64_t num_sources, int32_t index, int32_t count, int64_t* s0, int64_t* s1) {

@@ -65,6 +65,8 @@ struct LsParams {
     uint64_t* dbg_s;
     int64_t dbg_n;
     int items_static;            // 1: item index = slot
+    int rows_by_item;            // LS_SKEL: distance / count / dependency rows of item i in row state i
+                                 // (one per item), the rest of the slot state per slot
     int* item_counter;           // dynamic item counter (zeroed before launch)
     uint32_t* flags;
     unsigned long long* phase_ns;   // nullptr or [2]: summed forward / backward time of the batches (ns)

@@ -188,7 +188,7 @@ __device__ __forceinline__ bool row_has(const uint8_t*, int32_t) { return true; 
 // Scalar control state of one batch; with a cluster it lives in the leader CTA's shared memory
 // and the other CTAs reach it through distributed shared memory.
 struct LsCtl {
-    int item, pos, next, D, done, maxpush, nsteps, err, end, iters;
+    int item, pos, next, D, done, maxpush, nsteps, err, end;
     unsigned long long t0, t1;   // batch start and end of its forward pass (global timer, ns)
 };
 
@@ -253,13 +253,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
 
     using DD = typename DistT<NARROW>::T;
     constexpr DD DD_INF = DistT<NARROW>::INF;
-    DD* d = reinterpret_cast<DD*>(W.d) + (int64_t)slot * W.cap_n * ROW;
     using SG = typename DistT<NARROW>::S;
-    SG* sg = reinterpret_cast<SG*>(W.sg) + (int64_t)slot * W.cap_n * ROW;
-    DT* dlt = reinterpret_cast<DT*>(W.dl) + (int64_t)slot * W.cap_n * ROW;
-    DD* dl0 = d + lane * SPL;                     // this lane's slice: node v at dl0[v << SH]
-    SG* sl0 = sg + lane * SPL;
-    DT* cl0 = dlt + lane * SPL;
     LsEnt* order = W.order + (int64_t)slot * W.cap_order;
     int32_t* step_d = W.step_d + (int64_t)slot * W.cap_steps;
     int32_t* step_beg = W.step_beg + (int64_t)slot * W.cap_steps;
@@ -280,6 +274,14 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
         const int it = ctl->item;
         if (it >= nitems) break;
         const LsItem I = items[it];
+        // the batch's rows: the slot's, or the item's own row state (kept for the Centrality step)
+        const int64_t rb = P.rows_by_item ? (int64_t)it : (int64_t)slot;
+        DD* d = reinterpret_cast<DD*>(W.d) + rb * W.cap_n * ROW;
+        SG* sg = reinterpret_cast<SG*>(W.sg) + rb * W.cap_n * ROW;
+        DT* dlt = reinterpret_cast<DT*>(W.dl) + rb * W.cap_n * ROW;
+        DD* dl0 = d + lane * SPL;                 // this lane's slice: node v at dl0[v << SH]
+        SG* sl0 = sg + lane * SPL;
+        DT* cl0 = dlt + lane * SPL;
         const int64_t base = A.node_off[I.g];
         const int32_t n = (int32_t)(A.node_off[I.g + 1] - base);
         const int64_t* rp = A.rp + base;
@@ -305,7 +307,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
         }
         if (leader) {
             bflag[0] = 1;
-            ctl->pos = 0; ctl->D = 0; ctl->maxpush = 0; ctl->nsteps = 0; ctl->err = 0; ctl->iters = 0;
+            ctl->pos = 0; ctl->D = 0; ctl->maxpush = 0; ctl->nsteps = 0; ctl->err = 0;
             if (P.phase_ns) ctl->t0 = global_ns();
         }
         sync();
@@ -328,13 +330,6 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                     ctl->done = (D > ctl->maxpush) || ctl->err;
                 }
                 ctl->D = D;
-                // Bounded loop: a batch has at most one step per distinct distance, at most
-                // (nb - 1)(n - 1) + 1 of them; more would mean corrupted state, which ends the
-                // batch with the capacity flag instead of spinning.
-                if (!ctl->done && ++ctl->iters > (int64_t)(P.nb - 1) * n + 2) {
-                    ctl->err = 1;
-                    ctl->done = 1;
-                }
                 if (!ctl->done) {
                     if constexpr (WEIGHTED) bflag[D % P.nb] = 0;
                     if (ctl->nsteps >= W.cap_steps) {

@@ -1,11 +1,13 @@
 """GPU parity on paths that only many batches or deep weighted inputs reach.
 
-- Brandes_SK with Centrality runs its batches in static chunks of as many slots as fit, each
-  chunk followed by the Centrality step over its slots (Sec. 4, Eq. 11-13).  More than one
-  chunk happens only with more batches than slots: forced here on small graphs by fewer slots
-  (4-CTA clusters, one CTA per SM), and reached with the default launch shape by a target set
-  of 10,000 (313 batches of 32).  Brandes++ must equal the oracle's plain Brandes (the
-  method's exactness, Sec. 4).
+- Brandes_SK with Centrality (Sec. 4, Eq. 11-13), with more source batches than slots: by
+  default one Brandes_SK launch schedules all batches dynamically, each batch writing its own
+  set of rows, and one Centrality launch covers them all; with `pp_chunks=1` (the fallback when
+  memory is short) the batches run in static chunks of as many slots as fit, each chunk followed
+  by the Centrality step over its slots.  Both are reached here: on small graphs with fewer
+  slots (4-CTA clusters, one CTA per SM), and with the default launch shape by a target set of
+  10,000 (313 batches of 32).  Brandes++ must equal the oracle's plain Brandes (the method's
+  exactness, Sec. 4).
 - Integer weights (Sec. 3, Eq. 2): a batch records one step per distinct settled distance, so
   deep weighted graphs (a weighted path, a weighted grid) record tens of thousands of steps per
   batch.  Distances and path counts must match the oracle bit for bit and betweenness to
@@ -46,27 +48,30 @@ def chunk_graphs():
 
 
 @pytest.mark.parametrize("name,g", chunk_graphs(), ids=lambda x: x if isinstance(x, str) else "")
-def test_brandes_pp_forced_chunks(bc, name, g):
+@pytest.mark.parametrize("pp_chunks", [0, 1])
+def test_brandes_pp_many_batches(bc, name, g, pp_chunks):
     """2,000 targets = 63 batches; with 4-CTA clusters and one CTA per SM there are 38 slots on
-    152 SMs, so Brandes_SK + Centrality run in two chunks (32 + 31 batches)."""
+    152 SMs: one dynamic pass with a row set per batch (pp_chunks=0), or two static chunks of 32
+    and 31 batches (pp_chunks=1)."""
     S = gen.sample_targets(g.n, 2000, seed=82)
     G = bc.graph_from_edgelist(g)
     ref, _ = oracle.brandes(g, S)
     for cluster, cps in ((4, 1), (2, 1), (1, 1)):
-        got = bc.brandes_pp(G, S, g.part, cluster=cluster, ctas_per_sm=cps).cpu().numpy()
+        got = bc.brandes_pp(G, S, g.part, cluster=cluster, ctas_per_sm=cps, pp_chunks=pp_chunks).cpu().numpy()
         assert rel_err(got, ref) < FP64_TOL, (cluster, cps)
-    got32 = bc.brandes_pp(G, S, g.part, cluster=4, ctas_per_sm=1, precision="fp32").cpu().numpy()
+    got32 = bc.brandes_pp(G, S, g.part, cluster=4, ctas_per_sm=1, precision="fp32",
+                          pp_chunks=pp_chunks).cpu().numpy()
     assert rel_err(got32, ref) < FP32_TOL
-    # shards of the chunked run add up as well
-    half = [bc.brandes_pp(G, S, g.part, cluster=4, ctas_per_sm=1, shard=(r, 2), halve=False).cpu().numpy()
-            for r in range(2)]
+    # shards add up as well
+    half = [bc.brandes_pp(G, S, g.part, cluster=4, ctas_per_sm=1, shard=(r, 2), halve=False,
+                          pp_chunks=pp_chunks).cpu().numpy() for r in range(2)]
     ref_o, _ = oracle.brandes(g, S, halve=False)
     assert rel_err(half[0] + half[1], ref_o) < FP64_TOL
 
 
-def test_brandes_pp_default_chunks_many_targets(bc):
-    """10,000 targets = 313 batches, more than the 304 slots of two CTAs per SM: the default
-    launch shape runs two chunks of Brandes_SK + Centrality."""
+def test_brandes_pp_default_shape_many_targets(bc):
+    """10,000 targets = 313 batches, more than the 304 slots of two CTAs per SM, with the default
+    launch shape: one dynamic pass and static chunks."""
     g = gen.planted_partition(30000, 60, 0.012, 0.000005, seed=81)
     S = gen.sample_targets(g.n, 10000, seed=82)
     G = bc.graph_from_edgelist(g)
@@ -74,6 +79,7 @@ def test_brandes_pp_default_chunks_many_targets(bc):
     pp, st = bc.brandes_pp(G, S, g.part, stats=True)
     assert st["table_entries"] > 0            # non-frontier nodes exist: Centrality runs
     assert rel_err(pp.cpu().numpy(), ref) < FP64_TOL
+    assert rel_err(bc.brandes_pp(G, S, g.part, pp_chunks=1).cpu().numpy(), ref) < FP64_TOL
     assert rel_err(bc.brandes(G, S).cpu().numpy(), ref) < FP64_TOL
 
 

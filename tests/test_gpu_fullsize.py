@@ -184,12 +184,14 @@ def test_c5_shard_partial_vs_oracle(bc, c5, precision, tol):
 
 
 def test_c5_brandes_pp_equals_plain(bc, c5):
-    """The benchmark's configuration (128 batches: Brandes_SK and Centrality in two chunks of 64
-    four-CTA slots on 152 SMs): Brandes++ equals plain Brandes, FP64 and FP32-delta."""
+    """The benchmark's configuration (128 batches on 76 four-CTA slots: one dynamic Brandes_SK
+    pass with a row set per batch, and the static-chunk fallback, two chunks of 64): Brandes++
+    equals plain Brandes, FP64 and FP32-delta."""
     g, S, G = c5
     plain = bc.brandes(G, S).cpu().numpy()
     pp = bc.brandes_pp(G, S, g.part).cpu().numpy()
     assert rel_err(pp, plain) < FP64_TOL
+    assert rel_err(bc.brandes_pp(G, S, g.part, pp_chunks=1).cpu().numpy(), plain) < FP64_TOL
     pp32 = bc.brandes_pp(G, S, g.part, precision="fp32").cpu().numpy()
     assert rel_err(pp32, plain) < FP32_TOL_C5
     plain32 = bc.brandes(G, S, precision="fp32").cpu().numpy()
