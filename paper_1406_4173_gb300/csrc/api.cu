@@ -226,6 +226,18 @@ __global__ void group_by_part_kernel(const int32_t* part, int32_t n, int32_t k, 
     }
 }
 
+// largest finite value of a distance table (DINF = unreachable) into *out
+__global__ void table_max_kernel(const int32_t* t, int64_t n, unsigned* out) {
+    unsigned m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = t[i];
+        if (v != DINF && (unsigned)v > m) m = (unsigned)v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(FULL, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 __global__ void accumulate_kernel(const double* x, int32_t n, double* sum, double* comp) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double s = sum[i], c = comp[i];
@@ -975,6 +987,7 @@ struct Skeleton {
     int64_t arcs = 0, edges = 0, table_entries = 0;
     int32_t lcs = 0, k_nonempty = 0;
     uint64_t wmax_sk = 1, mmax_sk = 1;
+    uint32_t tdmax = 0;   // largest finite distance in the entry and exit tables
     DBuf<int32_t> partp, pstart, nf, loc, skid, sknode, skbase;
     DBuf<uint8_t> fr;
     DBuf<uint32_t> pnodes;
@@ -1179,6 +1192,24 @@ int build_sk(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS_eff,
             CK_RC(sync_flags(c));
             if (c->hflags[FLAG_CAPACITY]) return BCPP_ECAPACITY;
         }
+    }
+    // the largest finite table distance (the Centrality step takes a 16-bit path when it is small)
+    if (reuse) {
+        K.tdmax = reuse->tdmax;
+    } else if (K.table_entries > 0) {
+        DBuf<unsigned> tm(c, 1);
+        CK_ALLOC(tm);
+        CK_CUDA(cudaMemsetAsync(tm.p, 0, sizeof(unsigned), c->stream));
+        const unsigned blocks = (unsigned)std::min<int64_t>((K.table_entries + 255) / 256, 152 * 8);
+        table_max_kernel<<<blocks, 256, 0, c->stream>>>(K.td.p, K.table_entries, tm.p);
+        c->launches++;
+        if (K.tdr.p) {
+            table_max_kernel<<<blocks, 256, 0, c->stream>>>(K.tdr.p, K.table_entries, tm.p);
+            c->launches++;
+        }
+        unsigned h = 0;
+        CK_RC(to_host(c, &h, tm.p, 1));
+        K.tdmax = h;
     }
     // skeleton arcs: R with <w,1>, X_i with <d_i, sigma_i>
     {
@@ -1402,7 +1433,8 @@ int pp_emit(bcpp_ctx* c, PpRun& r, Timer* tbr, Timer* tce) {
             if (tbr) tbr->stop();
             CK_CUDA(cudaGetLastError());
             if (tce) tce->start();
-            centrality_launch(fp32, r.units.p, (int)r.hunits.size(), r.nitems, T, K.pnodes.p, K.skbase.p, r.ws.W.d,
+            centrality_launch(fp32, K.tdmax <= CT_H16_MAX, r.units.p, (int)r.hunits.size(), r.nitems, T, K.pnodes.p,
+                              K.skbase.p, r.ws.W.d,
                               r.ws.W.sg, r.ws.W.dl, r.ws.W.cap_n, r.ws.W.bc_sum, r.ws.W.bc_cmp, r.ws.W.cap_bc,
                               c->flags, c->stream);
             c->launches++;
@@ -1426,7 +1458,8 @@ int pp_emit(bcpp_ctx* c, PpRun& r, Timer* tbr, Timer* tce) {
             if (tbr) tbr->stop();
             CK_CUDA(cudaGetLastError());
             if (tce) tce->start();
-            centrality_launch(fp32, r.units.p, (int)r.hunits.size(), cn, T, K.pnodes.p, K.skbase.p, r.ws.W.d,
+            centrality_launch(fp32, K.tdmax <= CT_H16_MAX, r.units.p, (int)r.hunits.size(), cn, T, K.pnodes.p,
+                              K.skbase.p, r.ws.W.d,
                               r.ws.W.sg, r.ws.W.dl, r.ws.W.cap_n, r.ws.W.bc_sum, r.ws.W.bc_cmp, r.ws.W.cap_bc,
                               c->flags, c->stream);
             c->launches++;

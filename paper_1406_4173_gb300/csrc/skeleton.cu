@@ -1,5 +1,7 @@
 // Build_SK steps (Sec. 3 "The skeleton graph", Sec. 4 Alg. 1-2), the Centrality step
 // (Sec. 4, Eq. 13) and the combination of partial betweenness.
+#include <cuda_fp16.h>
+
 #include "skeleton.cuh"
 
 namespace bcpp {
@@ -250,18 +252,37 @@ __global__ void target_ids_kernel(const int32_t* S, int32_t nS, const int32_t* s
 // with the tight-frontier tests).  Distances are handled as uint32: real distances are below
 // DINF = 2^31 - 1, so a sum of two values never wraps, and a sum with an unreachable term is at
 // least DINF, above every real distance.
+//
+// 16-bit path: when every finite table distance (h16, from the host) and every finite frontier
+// distance of the block's slot and part (checked while the first sweep stages them) is at most
+// CT_H16_MAX = 1023, the distance arithmetic runs on pairs of nodes packed in binary16 halves
+// (one shuffle, one packed add and one packed min or compare for two nodes).  Integers up to
+// 2048 are exact in binary16, so every sum of two such values is exact and the min-plus and the
+// tight tests decide as in integers; a backward sum above 2048 can round but stays above every
+// frontier distance, so it cannot test equal.  Unreachable is +inf in the sums and NaN where a
+// value must equal nothing.  A block that finds a larger frontier distance redoes the first
+// sweep in 32 bits and stays there.
 constexpr int CTV = 4;          // nodes per warp
+constexpr int CT_NP = CTV / 2;  // node pairs per warp (16-bit path)
 constexpr int CT_WARPS = 16;    // warps per block: 64 nodes = one unit
 constexpr int FT = 32;          // frontiers per tile
 constexpr uint32_t CT_NONE = 0xffffffffu;   // "unreachable" after the min-plus sweep (no sum equals it)
+
+__device__ __forceinline__ __half ct_h(uint32_t x) {
+    return x >= (uint32_t)DINF ? __ushort_as_half((unsigned short)0x7c00) : __uint2half_rn(x);
+}
+__device__ __forceinline__ __half ct_h_or_nan(uint32_t x) {
+    return x >= (uint32_t)DINF ? __ushort_as_half((unsigned short)0x7e00) : __uint2half_rn(x);
+}
 
 template <typename DT>
 __global__ void __launch_bounds__(CT_WARPS * 32)
 centrality_tiled_kernel(const CentralityUnit* __restrict__ units, SkTables T, const uint32_t* __restrict__ pnodes,
                         const int32_t* __restrict__ skbase, const int32_t* __restrict__ d_all,
                         const uint64_t* __restrict__ sg_all, const DT* __restrict__ dl_all, int64_t cap_n,
-                        double* bc_sum, double* bc_cmp, int64_t cap_bc, uint32_t* flags, int slot_major) {
+                        double* bc_sum, double* bc_cmp, int64_t cap_bc, uint32_t* flags, int slot_major, int h16) {
     __shared__ uint32_t s_d[FT][32];
+    __shared__ __half2 s_h[FT][32];       // 16-bit path: the frontier distance in both halves
     __shared__ uint64_t s_x[FT][32];      // sigma rows (forward) or c rows (backward, as DT bits)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const CentralityUnit U = units[slot_major ? blockIdx.y : blockIdx.x];
@@ -274,26 +295,69 @@ centrality_tiled_kernel(const CentralityUnit* __restrict__ units, SkTables T, co
     const int32_t vb = U.v0 + warp * CTV;
     int nv = U.v1 - vb;
     nv = nv < 0 ? 0 : (nv > CTV ? CTV : nv);
+    // entry-table distance of node j of this warp for frontier f0 + lane (DINF past the end)
+    auto td_at = [&](const int32_t* tab, int j, int32_t f0, int nt) -> uint32_t {
+        return (j < nv && lane < nt) ? (uint32_t)tab[t0 + (int64_t)(vb + j) * nfi + f0 + lane] : (uint32_t)DINF;
+    };
     // ---- forward sweep 1: d(s,v) = min over entry frontiers of d(s,f) + d_i(f,v)
     uint32_t dv[CTV];
 #pragma unroll
     for (int j = 0; j < CTV; j++) dv[j] = CT_NONE;
-    for (int32_t f0 = 0; f0 < nfi; f0 += FT) {
-        const int nt = min(FT, nfi - f0);
-        __syncthreads();
-        for (int x = threadIdx.x; x < nt * 32; x += CT_WARPS * 32)
-            s_d[x >> 5][x & 31] = (uint32_t)d_all[fbase + (int64_t)(f0 + (x >> 5)) * 32 + (x & 31)];
-        uint32_t tdv[CTV];
+    bool use16 = h16 != 0;
+    if (use16) {
+        __half2 dv2[CT_NP];
 #pragma unroll
-        for (int j = 0; j < CTV; j++)
-            tdv[j] = (j < nv && lane < nt) ? (uint32_t)T.td[t0 + (int64_t)(vb + j) * nfi + f0 + lane] : (uint32_t)DINF;
-        __syncthreads();
-        for (int f = 0; f < nt; f++) {
-            const uint32_t dsf = s_d[f][lane];
+        for (int q = 0; q < CT_NP; q++) dv2[q] = __half2half2(ct_h(DINF));
+        bool big = false;
+        for (int32_t f0 = 0; f0 < nfi; f0 += FT) {
+            const int nt = min(FT, nfi - f0);
+            __syncthreads();
+            for (int x = threadIdx.x; x < nt * 32; x += CT_WARPS * 32) {
+                const uint32_t v = (uint32_t)d_all[fbase + (int64_t)(f0 + (x >> 5)) * 32 + (x & 31)];
+                big |= v != (uint32_t)DINF && v > CT_H16_MAX;
+                s_h[x >> 5][x & 31] = __half2half2(ct_h(v));
+            }
+            __half2 th[CT_NP];
 #pragma unroll
-            for (int j = 0; j < CTV; j++) {
-                const uint32_t tdj = __shfl_sync(FULL, tdv[j], f);
-                dv[j] = min(dv[j], dsf + tdj);
+            for (int q = 0; q < CT_NP; q++)
+                th[q] = __halves2half2(ct_h(td_at(T.td, 2 * q, f0, nt)), ct_h(td_at(T.td, 2 * q + 1, f0, nt)));
+            __syncthreads();
+            for (int f = 0; f < nt; f++) {
+                const __half2 dh = s_h[f][lane];
+#pragma unroll
+                for (int q = 0; q < CT_NP; q++) {
+                    const __half2 t = __shfl_sync(FULL, th[q], f);
+                    dv2[q] = __hmin2(dv2[q], __hadd2(dh, t));
+                }
+            }
+        }
+        use16 = !__syncthreads_or(big);
+        if (use16) {
+#pragma unroll
+            for (int q = 0; q < CT_NP; q++) {
+                const __half lo = __low2half(dv2[q]), hi = __high2half(dv2[q]);
+                dv[2 * q] = __hisinf(lo) ? CT_NONE : __half2uint_rn(lo);
+                dv[2 * q + 1] = __hisinf(hi) ? CT_NONE : __half2uint_rn(hi);
+            }
+        }
+    }
+    if (!use16) {
+        for (int32_t f0 = 0; f0 < nfi; f0 += FT) {
+            const int nt = min(FT, nfi - f0);
+            __syncthreads();
+            for (int x = threadIdx.x; x < nt * 32; x += CT_WARPS * 32)
+                s_d[x >> 5][x & 31] = (uint32_t)d_all[fbase + (int64_t)(f0 + (x >> 5)) * 32 + (x & 31)];
+            uint32_t tdv[CTV];
+#pragma unroll
+            for (int j = 0; j < CTV; j++) tdv[j] = td_at(T.td, j, f0, nt);
+            __syncthreads();
+            for (int f = 0; f < nt; f++) {
+                const uint32_t dsf = s_d[f][lane];
+#pragma unroll
+                for (int j = 0; j < CTV; j++) {
+                    const uint32_t tdj = __shfl_sync(FULL, tdv[j], f);
+                    dv[j] = min(dv[j], dsf + tdj);
+                }
             }
         }
     }
@@ -309,36 +373,60 @@ centrality_tiled_kernel(const CentralityUnit* __restrict__ units, SkTables T, co
     for (int j = 0; j < CTV; j++) sv[j] = 0;
     bool ovf = false;
     if (__syncthreads_or(any_reach)) {
+        __half2 dvh[CT_NP];   // 16-bit path: the node distances, NaN when unreachable
+#pragma unroll
+        for (int q = 0; q < CT_NP; q++) dvh[q] = __halves2half2(ct_h_or_nan(dv[2 * q]), ct_h_or_nan(dv[2 * q + 1]));
         for (int32_t f0 = 0; f0 < nfi; f0 += FT) {
             const int nt = min(FT, nfi - f0);
             __syncthreads();
             for (int x = threadIdx.x; x < nt * 32; x += CT_WARPS * 32) {
                 const int64_t o = fbase + (int64_t)(f0 + (x >> 5)) * 32 + (x & 31);
-                s_d[x >> 5][x & 31] = (uint32_t)d_all[o];
+                const uint32_t v = (uint32_t)d_all[o];
+                if (use16) s_h[x >> 5][x & 31] = __half2half2(ct_h(v));
+                else s_d[x >> 5][x & 31] = v;
                 s_x[x >> 5][x & 31] = sg_all[o];
             }
             uint32_t tdv[CTV];
             uint64_t tsv[CTV];
 #pragma unroll
             for (int j = 0; j < CTV; j++) {
-                tdv[j] = (uint32_t)DINF;
-                tsv[j] = 0;
-                if (j < nv && lane < nt) {
-                    const int64_t o = t0 + (int64_t)(vb + j) * nfi + f0 + lane;
-                    tdv[j] = (uint32_t)T.td[o];
-                    if (tdv[j] != (uint32_t)DINF) tsv[j] = T.ts[o];
-                }
+                tdv[j] = td_at(T.td, j, f0, nt);
+                tsv[j] = tdv[j] != (uint32_t)DINF ? T.ts[t0 + (int64_t)(vb + j) * nfi + f0 + lane] : 0ull;
             }
             __syncthreads();
-            for (int f = 0; f < nt; f++) {
-                const uint32_t dsf = s_d[f][lane];
+            if (use16) {
+                __half2 th[CT_NP];
 #pragma unroll
-                for (int j = 0; j < CTV; j++) {
-                    const uint32_t tdj = __shfl_sync(FULL, tdv[j], f);
-                    const bool tight = dsf + tdj == dv[j];
-                    if (__any_sync(FULL, tight)) {
-                        const uint64_t tsj = shfl_u64(tsv[j], f);
-                        if (tight) sv[j] = madd_ck(sv[j], s_x[f][lane], tsj, ovf);
+                for (int q = 0; q < CT_NP; q++) th[q] = __halves2half2(ct_h(tdv[2 * q]), ct_h(tdv[2 * q + 1]));
+                for (int f = 0; f < nt; f++) {
+                    const __half2 dh = s_h[f][lane];
+#pragma unroll
+                    for (int q = 0; q < CT_NP; q++) {
+                        const __half2 t = __shfl_sync(FULL, th[q], f);
+                        const unsigned m = __heq2_mask(__hadd2(dh, t), dvh[q]);
+                        if (__any_sync(FULL, m != 0u)) {
+#pragma unroll
+                            for (int h = 0; h < 2; h++) {
+                                const bool tight = ((m >> (16 * h)) & 0xffffu) != 0u;
+                                if (__any_sync(FULL, tight)) {
+                                    const uint64_t tsj = shfl_u64(tsv[2 * q + h], f);
+                                    if (tight) sv[2 * q + h] = madd_ck(sv[2 * q + h], s_x[f][lane], tsj, ovf);
+                                }
+                            }
+                        }
+                    }
+                }
+            } else {
+                for (int f = 0; f < nt; f++) {
+                    const uint32_t dsf = s_d[f][lane];
+#pragma unroll
+                    for (int j = 0; j < CTV; j++) {
+                        const uint32_t tdj = __shfl_sync(FULL, tdv[j], f);
+                        const bool tight = dsf + tdj == dv[j];
+                        if (__any_sync(FULL, tight)) {
+                            const uint64_t tsj = shfl_u64(tsv[j], f);
+                            if (tight) sv[j] = madd_ck(sv[j], s_x[f][lane], tsj, ovf);
+                        }
                     }
                 }
             }
@@ -354,12 +442,20 @@ centrality_tiled_kernel(const CentralityUnit* __restrict__ units, SkTables T, co
         any_live |= live[j];
     }
     if (__syncthreads_or(any_live)) {
+        __half2 lvh[CT_NP];   // 16-bit path: distances of live nodes, NaN otherwise
+#pragma unroll
+        for (int q = 0; q < CT_NP; q++)
+            lvh[q] = __halves2half2(ct_h_or_nan(live[2 * q] ? dv[2 * q] : CT_NONE),
+                                    ct_h_or_nan(live[2 * q + 1] ? dv[2 * q + 1] : CT_NONE));
         for (int32_t f0 = 0; f0 < nfi; f0 += FT) {
             const int nt = min(FT, nfi - f0);
             __syncthreads();
             for (int x = threadIdx.x; x < nt * 32; x += CT_WARPS * 32) {
                 const int64_t o = fbase + (int64_t)(f0 + (x >> 5)) * 32 + (x & 31);
-                s_d[x >> 5][x & 31] = (uint32_t)d_all[o];
+                const uint32_t v = (uint32_t)d_all[o];
+                // an unreachable frontier must equal no sum: NaN on the 16-bit path
+                if (use16) s_h[x >> 5][x & 31] = __half2half2(ct_h_or_nan(v));
+                else s_d[x >> 5][x & 31] = v;
                 DT cv = dl_all[o];
                 uint64_t bits = 0;
                 memcpy(&bits, &cv, sizeof(DT));
@@ -369,33 +465,57 @@ centrality_tiled_kernel(const CentralityUnit* __restrict__ units, SkTables T, co
             uint64_t tsv[CTV];
 #pragma unroll
             for (int j = 0; j < CTV; j++) {
-                tdv[j] = (uint32_t)DINF;
-                tsv[j] = 0;
-                if (j < nv && lane < nt) {
-                    const int64_t o = t0 + (int64_t)(vb + j) * nfi + f0 + lane;
-                    tdv[j] = (uint32_t)T.tdr[o];
-                    if (tdv[j] != (uint32_t)DINF) tsv[j] = T.tsr[o];
-                }
+                tdv[j] = td_at(T.tdr, j, f0, nt);
+                tsv[j] = tdv[j] != (uint32_t)DINF ? T.tsr[t0 + (int64_t)(vb + j) * nfi + f0 + lane] : 0ull;
             }
             __syncthreads();
-            for (int f = 0; f < nt; f++) {
-                const uint32_t dsf = s_d[f][lane];
-                const bool fin = dsf != (uint32_t)DINF;
+            if (use16) {
+                __half2 th[CT_NP];
 #pragma unroll
-                for (int j = 0; j < CTV; j++) {
-                    // a live node has a finite distance, and a sum with an unreachable exit
-                    // table entry exceeds every finite frontier distance.  (The shuffle is taken
-                    // by every lane before the test: a full-mask shuffle that some lanes skip
-                    // never completes.)
-                    const uint32_t tdj = __shfl_sync(FULL, tdv[j], f);
-                    const bool on = live[j] && fin && dv[j] + tdj == dsf;
-                    if (__any_sync(FULL, on)) {
-                        const uint64_t tsj = shfl_u64(tsv[j], f);
-                        if (on) {
-                            DT cf;
-                            const uint64_t bits = s_x[f][lane];
-                            memcpy(&cf, &bits, sizeof(DT));
-                            acc[j] += (DT)tsj * cf;
+                for (int q = 0; q < CT_NP; q++) th[q] = __halves2half2(ct_h(tdv[2 * q]), ct_h(tdv[2 * q + 1]));
+                for (int f = 0; f < nt; f++) {
+                    const __half2 dh = s_h[f][lane];
+#pragma unroll
+                    for (int q = 0; q < CT_NP; q++) {
+                        const __half2 t = __shfl_sync(FULL, th[q], f);
+                        const unsigned m = __heq2_mask(__hadd2(lvh[q], t), dh);
+                        if (__any_sync(FULL, m != 0u)) {
+#pragma unroll
+                            for (int h = 0; h < 2; h++) {
+                                const bool on = ((m >> (16 * h)) & 0xffffu) != 0u;
+                                if (__any_sync(FULL, on)) {
+                                    const uint64_t tsj = shfl_u64(tsv[2 * q + h], f);
+                                    if (on) {
+                                        DT cf;
+                                        const uint64_t bits = s_x[f][lane];
+                                        memcpy(&cf, &bits, sizeof(DT));
+                                        acc[2 * q + h] += (DT)tsj * cf;
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+            } else {
+                for (int f = 0; f < nt; f++) {
+                    const uint32_t dsf = s_d[f][lane];
+                    const bool fin = dsf != (uint32_t)DINF;
+#pragma unroll
+                    for (int j = 0; j < CTV; j++) {
+                        // a live node has a finite distance, and a sum with an unreachable exit
+                        // table entry exceeds every finite frontier distance.  (The shuffle is
+                        // taken by every lane before the test: a full-mask shuffle that some lanes
+                        // skip never completes.)
+                        const uint32_t tdj = __shfl_sync(FULL, tdv[j], f);
+                        const bool on = live[j] && fin && dv[j] + tdj == dsf;
+                        if (__any_sync(FULL, on)) {
+                            const uint64_t tsj = shfl_u64(tsv[j], f);
+                            if (on) {
+                                DT cf;
+                                const uint64_t bits = s_x[f][lane];
+                                memcpy(&cf, &bits, sizeof(DT));
+                                acc[j] += (DT)tsj * cf;
+                            }
                         }
                     }
                 }
@@ -482,7 +602,7 @@ void sk_target_ids(const int32_t* S, int32_t nS, const int32_t* skid, int32_t* o
     if (nS > 0) target_ids_kernel<<<grid_for(nS, 256), 256, 0, st>>>(S, nS, skid, out);
 }
 
-void centrality_launch(bool fp32_delta, const CentralityUnit* units, int nunits, int nslots, SkTables T,
+void centrality_launch(bool fp32_delta, bool h16, const CentralityUnit* units, int nunits, int nslots, SkTables T,
                        const uint32_t* pnodes, const int32_t* skbase, const int32_t* d, const uint64_t* sg,
                        const void* dl, int64_t cap_n, double* bc_sum, double* bc_cmp, int64_t cap_bc,
                        uint32_t* flags, cudaStream_t st) {
@@ -492,11 +612,11 @@ void centrality_launch(bool fp32_delta, const CentralityUnit* units, int nunits,
     if (fp32_delta)
         centrality_tiled_kernel<float><<<grid, CT_WARPS * 32, 0, st>>>(units, T, pnodes, skbase, d, sg,
                                                                       (const float*)dl, cap_n, bc_sum, bc_cmp,
-                                                                      cap_bc, flags, slot_major);
+                                                                      cap_bc, flags, slot_major, h16 ? 1 : 0);
     else
         centrality_tiled_kernel<double><<<grid, CT_WARPS * 32, 0, st>>>(units, T, pnodes, skbase, d, sg,
                                                                        (const double*)dl, cap_n, bc_sum, bc_cmp,
-                                                                       cap_bc, flags, slot_major);
+                                                                       cap_bc, flags, slot_major, h16 ? 1 : 0);
 }
 
 void combine_launch(const double* bc_sum, const double* bc_cmp, int nslots, int64_t cap_bc, int64_t n, double scale,

@@ -53,7 +53,9 @@ void sk_target_ids(const int32_t* S, int32_t nS, const int32_t* skid, int32_t* o
 
 // Centrality (Eq. 13) for the slots of one Brandes_SK chunk.
 struct CentralityUnit { int32_t part; int32_t v0; int32_t v1; int32_t pad; };
-void centrality_launch(bool fp32_delta, const CentralityUnit* units, int nunits, int nslots, SkTables T,
+// h16: every finite table distance is at most CT_H16_MAX (the 16-bit distance path may run)
+constexpr uint32_t CT_H16_MAX = 1023;
+void centrality_launch(bool fp32_delta, bool h16, const CentralityUnit* units, int nunits, int nslots, SkTables T,
                        const uint32_t* pnodes, const int32_t* skbase, const int32_t* d, const uint64_t* sg,
                        const void* dl, int64_t cap_n, double* bc_sum, double* bc_cmp, int64_t cap_bc,
                        uint32_t* flags, cudaStream_t st);

@@ -131,7 +131,7 @@ def test_weighted_grid_60x60_deep(bc):
 def test_small_weights_long_distances(bc):
     """Weights in [1, 4] on a 2,000-node path (distances up to about 5,000, thousands of steps per
     batch with few distinct weights) and on a 40 x 40 grid, plain Brandes and Brandes++ in both
-    precisions."""
+    precisions (the Centrality step's distances in 16 bits where they fit, else in 32)."""
     n = 2000
     g = gen.with_weights(gen.path(n), 4, seed=96)
     G = bc.graph_from_edgelist(g)
@@ -141,6 +141,13 @@ def test_small_weights_long_distances(bc):
     assert rel_err(bc.brandes(G).cpu().numpy(), ref) < FP64_TOL
     assert rel_err(bc.brandes(G, precision="fp32").cpu().numpy(), ref) < FP32_TOL
     _check_sssp(bc, G, g, np.array([0, 999, 1999], np.int32))
+    # parts of 10 consecutive nodes: table distances at most 36, distances from the sources to the
+    # frontiers up to about 5,000 (the Centrality step's 16-bit path must fall back to 32 bits)
+    S1 = gen.sample_targets(n, 100, seed=99)
+    ref1, _ = oracle.brandes(g, S1)
+    blocks = (np.arange(n) // 10).astype(np.int32)
+    for prec, tol in (("fp64", FP64_TOL), ("fp32", FP32_TOL)):
+        assert rel_err(bc.brandes_pp(G, S1, blocks, precision=prec).cpu().numpy(), ref1) < tol, prec
     g2 = gen.with_weights(gen.grid(40, 40), 4, seed=97)
     G2 = bc.graph_from_edgelist(g2)
     S = gen.sample_targets(g2.n, 300, seed=98)
