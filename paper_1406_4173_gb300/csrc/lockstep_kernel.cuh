@@ -119,17 +119,22 @@ __device__ __forceinline__ void ld_row(const float* p, float (&x)[SPL]) {
 // group are loaded before the group is handed to f (with its size as a compile-time tag), so
 // f can issue its own dependent loads for the whole group at once.  Positions past the row's
 // end get distance DINF, which is never a parent's or a successor's distance.
-template <int U, int SPL, bool WEIGHTED, bool MULT, typename DD, class F>
-__device__ __forceinline__ void arc_group(int32_t mv, int32_t mw, uint64_t mm, int j, int cnt, const DD* dl0,
-                                          F&& f) {
+// broadcast of a multiplicity: exact uint64 (path counts) or converted once per chunk to the
+// dependency type (the backward pass's products)
+__device__ __forceinline__ uint64_t shfl_mult(uint64_t x, int src) { return shfl_u64(x, src); }
+__device__ __forceinline__ double shfl_mult(double x, int src) { return __shfl_sync(FULL, x, src); }
+__device__ __forceinline__ float shfl_mult(float x, int src) { return __shfl_sync(FULL, x, src); }
+
+template <int U, int SPL, bool WEIGHTED, bool MULT, typename MT, typename DD, class F>
+__device__ __forceinline__ void arc_group(int32_t mv, int32_t mw, MT mm, int j, int cnt, const DD* dl0, F&& f) {
     constexpr int SH = SPL == 1 ? 5 : 6;
     int32_t vv[U], ww[U], dv[U][SPL];
-    uint64_t mk[U];
+    MT mk[U];
 #pragma unroll
     for (int k = 0; k < U; k++) {
         vv[k] = __shfl_sync(FULL, mv, (j + k) & 31);
         ww[k] = WEIGHTED ? __shfl_sync(FULL, mw, (j + k) & 31) : 1;
-        mk[k] = MULT ? shfl_u64(mm, (j + k) & 31) : 1ull;
+        mk[k] = MULT ? shfl_mult(mm, (j + k) & 31) : (MT)1;
     }
 #pragma unroll
     for (int k = 0; k < U; k++) {
@@ -145,25 +150,27 @@ __device__ __forceinline__ void arc_group(int32_t mv, int32_t mw, uint64_t mm, i
 
 // Visit the arcs [a0, a0 + deg) of one row: 32 heads per coalesced load, then groups of
 // UNROLL arcs, or of UNROLL / 2 when at most that many are left (low-degree rows waste less).
-template <int UNROLL, int SPL, bool WEIGHTED, bool MULT, typename DD, class F>
+// MT: the type the multiplicities are handed to f in (uint64_t, or the dependency type, converted
+// once per chunk of 32 arcs instead of once per use).
+template <int UNROLL, int SPL, bool WEIGHTED, bool MULT, typename MT = uint64_t, typename DD, class F>
 __device__ __forceinline__ void for_arc_groups(const int32_t* __restrict__ col, const int32_t* __restrict__ w,
                                                const uint64_t* __restrict__ mu, int64_t a0, int32_t deg,
                                                const DD* dl0, int lane, F&& f) {
     for (int32_t c0 = 0; c0 < deg; c0 += 32) {
         const int cnt = min(32, deg - c0);
         int32_t mv = 0, mw = 1;
-        uint64_t mm = 1;
+        MT mm = (MT)1;
         if (lane < cnt) {
             mv = __ldg(col + a0 + c0 + lane);
             if (WEIGHTED) mw = __ldg(w + a0 + c0 + lane);
-            if (MULT) mm = __ldg(mu + a0 + c0 + lane);
+            if (MULT) mm = (MT)__ldg(mu + a0 + c0 + lane);
         }
         for (int j = 0; j < cnt;) {
             if (cnt - j > UNROLL / 2) {
-                arc_group<UNROLL, SPL, WEIGHTED, MULT>(mv, mw, mm, j, cnt, dl0, f);
+                arc_group<UNROLL, SPL, WEIGHTED, MULT, MT>(mv, mw, mm, j, cnt, dl0, f);
                 j += UNROLL;
             } else {
-                arc_group<UNROLL / 2, SPL, WEIGHTED, MULT>(mv, mw, mm, j, cnt, dl0, f);
+                arc_group<UNROLL / 2, SPL, WEIGHTED, MULT, MT>(mv, mw, mm, j, cnt, dl0, f);
                 j += UNROLL / 2;
             }
         }
@@ -603,8 +610,8 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                         DT acc[SPL];
 #pragma unroll
                         for (int s = 0; s < SPL; s++) acc[s] = (DT)0;
-                        for_arc_groups<UNROLL, SPL, WEIGHTED, MULT>(A.col, A.w, A.mu, cur.a0, cur.deg, dl0, lane,
-                            [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t* mk,
+                        for_arc_groups<UNROLL, SPL, WEIGHTED, MULT, DT>(A.col, A.w, A.mu, cur.a0, cur.deg, dl0, lane,
+                            [&](auto tag, const int32_t* vv, const int32_t* ww, const DT* mk,
                                 const int32_t (*dv)[SPL], int) {
                                 constexpr int U = decltype(tag)::value;
                                 DT cv[U][SPL];
@@ -632,7 +639,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                                     if (!std::is_same<DT, double>::value || (used & (1u << k)))
 #pragma unroll
                                         for (int s = 0; s < SPL; s++)
-                                            acc[s] += MULT ? (DT)mk[k] * cv[k][s] : cv[k][s];
+                                            acc[s] += MULT ? mk[k] * cv[k][s] : cv[k][s];
                             });
                         uint64_t su[SPL];
                         ld_row<SPL>(sl0 + ((uint32_t)u << SH), su);
