@@ -326,6 +326,12 @@ def _w_directed_100k(seed=0):
     return g, sample_targets(g.n, 2000, seed)
 
 
+def _w_directed_20k(seed=0):
+    sizes = np.full(40, 500)
+    g = chung_lu_communities(20_000, sizes, 2.3, 12.0, 0.90, seed, directed=True, wmax=16)
+    return g, sample_targets(g.n, 400, seed)
+
+
 def _w_chunglu_1m(seed=0):
     sizes = np.full(1000, 1000)
     g = chung_lu_communities(1_000_000, sizes, 2.2, 16.0, 0.85, seed)
@@ -366,6 +372,9 @@ WORKLOADS = {
     "planted_200k": (_w_planted_200k, "planted partition n=200,000, 100x2,000, p_in=0.005, p_out=9e-8 "
                                       "(about 1,800 inter-community edges), |S|=200: a small skeleton "
                                       "(N/n about 3%, M/m about 16%)"),
+    "directed_20k": (_w_directed_20k, "the directed_100k recipe at n=20,000: 40x500 communities, out-degree 12, "
+                                      "exp 2.3, 90% intra, w~U[1,16], |S|=400 (the small case of full profiler "
+                                      "captures of the integer-weight passes)"),
     "chunglu_100k": (_w_chunglu_100k, "the chunglu_1m recipe at n=100,000: 100x1,000 communities, degree exp "
                                       "2.2, mean 16, 85% intra, |S|=512 (the small case of full profiler "
                                       "captures of Brandes_SK and Centrality)"),

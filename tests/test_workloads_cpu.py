@@ -22,6 +22,7 @@ def _simple(g):
     ("chunglu_50k", 50_000, 250_000, False, None, 50, None),
     ("directed_100k", 100_000, 1_200_000, True, 2000, 200, (1, 16)),
     ("chunglu_100k", 100_000, 800_000, False, 512, 100, None),
+    ("directed_20k", 20_000, 240_000, True, 400, 40, (1, 16)),
     ("planted_200k", 200_000, None, False, 200, 100, None),
 ])
 def test_single_graph_workloads(name, n, m, directed, nS, k, wrange):
