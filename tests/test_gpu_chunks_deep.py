@@ -156,3 +156,37 @@ def test_small_weights_long_distances(bc):
     part = ((np.arange(g2.n) // 40) // 10 * 4 + (np.arange(g2.n) % 40) // 10).astype(np.int32)   # 4 x 4 tiles
     assert rel_err(bc.brandes_pp(G2, S, part).cpu().numpy(), ref2) < FP64_TOL
     assert rel_err(bc.brandes_pp(G2, S, part, precision="fp32").cpu().numpy(), ref2) < FP32_TOL
+
+
+def _active_lane_counts(g, srcs):
+    """Per (node, distance) of one 32-source batch: how many of its sources reach the node at
+    that distance (the lanes an entry of that step is active on), from the oracle's distances."""
+    d = np.stack([oracle.sssp(g, int(s))[0] for s in srcs], axis=1)
+    counts = []
+    for row in d:
+        r = row[row != np.iinfo(np.int32).max]
+        if r.size:
+            counts.extend(np.unique(r, return_counts=True)[1].tolist())
+    return np.asarray(counts)
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_weighted_entries_few_and_many_lanes(bc, directed):
+    """Integer weights visit an entry one of two ways: a lane per source when more than 16 of
+    the batch's 32 sources are at the step's distance, else (arc, source) pairs over the lanes.
+    Weights in {1, 2} give entries of both kinds in the same batch (checked on the first batch
+    from the oracle's distances); unsorted sources keep the batches as given."""
+    g = gen.chung_lu_communities(1500, [300] * 5, 2.3, 12.0 if directed else 8.0, 0.85, seed=101,
+                                 directed=directed, wmax=2)
+    S = np.arange(g.n, dtype=np.int32)
+    cnt = _active_lane_counts(g, S[:32])
+    assert (cnt <= 16).any() and (cnt > 16).any()
+    G = bc.graph_from_edgelist(g)
+    _check_sssp(bc, G, g, S[:32])
+    ref, _ = oracle.brandes(g)
+    for order in (False, True):
+        assert rel_err(bc.brandes(G, None, order_sources=order).cpu().numpy(), ref) < FP64_TOL, order
+    assert rel_err(bc.brandes(G, None, precision="fp32").cpu().numpy(), ref) < FP32_TOL
+    T = gen.sample_targets(g.n, 500, seed=102)
+    ref_t, _ = oracle.brandes(g, T)
+    assert rel_err(bc.brandes_pp(G, T, g.part).cpu().numpy(), ref_t) < FP64_TOL
