@@ -192,18 +192,24 @@ __device__ __forceinline__ bool row_has(const int32_t* row, int32_t D) {
 template <int ROW>
 __device__ __forceinline__ bool row_has(const uint8_t*, int32_t) { return true; }
 
-// Sparse-lane visits (integer weights, 32-source rows).  With integer weights a node is listed
-// once per distinct distance among its 32 sources, so most entries have only a few lanes at the
-// step's distance (about 16 listings per node with 2 active lanes on average on the directed
-// Chung-Lu workloads), and a lane per source leaves most of the warp idle on every arc.  For such
-// an entry the warp spreads (arc, active source) pairs over its lanes instead: with A' lanes per
-// arc (A' the power of two at or above the active count a), lane L takes source index
-// i = L mod A' and arc slot j = L / A' of each chunk of 32 / A' arcs; sums per source are
-// combined by a butterfly over the lanes of equal i.
+// Sparse-lane visits (32-source rows).  A node is listed once per distinct distance among its
+// batch's 32 sources, so many entries have only a few lanes at the step's distance: with integer
+// weights about 16 listings per node with 2 active lanes on average on the directed Chung-Lu
+// workloads, with unit weights about 3 listings per node with 11 active lanes on the undirected
+// ones.  A lane per source then leaves most of the warp idle on every arc.  For such an entry the
+// warp spreads (arc, active source) pairs over its lanes instead: with A' lanes per arc (A' the
+// power of two at or above the active count a), lane L takes source index i = L mod A' and arc
+// slot j = L / A' of each chunk of 32 / A' arcs; sums per source are combined by a butterfly
+// over the lanes of equal i.
 #ifndef BCPP_LS_SPARSE_MAX
 #define BCPP_LS_SPARSE_MAX 16
 #endif
-constexpr int LS_SPARSE_MAX = BCPP_LS_SPARSE_MAX;   // most active lanes an entry takes the sparse visit with
+#ifndef BCPP_LS_SPARSE_UNIT
+#define BCPP_LS_SPARSE_UNIT 16
+#endif
+// most active lanes an entry takes the sparse visit with: integer weights, unit weights
+constexpr int LS_SPARSE_MAX = BCPP_LS_SPARSE_MAX;
+constexpr int LS_SPARSE_UNIT = BCPP_LS_SPARSE_UNIT;
 
 struct SparseLanes {
     int lg;       // log2 A'
@@ -265,7 +271,7 @@ __global__ void __launch_bounds__(LS_THREADS, LS_MIN_CTAS)
 ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __restrict__ items, int nitems) {
     // CL CTAs (a thread-block cluster when CL > 1) share one batch and one slot
     __shared__ LsCtl s_ctl;
-    __shared__ int s_scr[LS_THREADS / 32][LS_SPARSE_MAX];   // sparse-lane visits: active lanes by rank
+    __shared__ int s_scr[LS_THREADS / 32][32];   // sparse-lane visits: active lanes by rank
     LsCtl* ctl = &s_ctl;
     int crank = 0;
     if constexpr (CL > 1) {
@@ -299,6 +305,8 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
     // to 5% faster with one CTA per batch and on weighted graphs, slower in the clustered
     // unit-weight instances (one more live register there costs more than the skip saves).
     constexpr bool LEAVES = CL == 1 || WEIGHTED;
+    // entries with at most SMAX lanes at the step's distance take the sparse-lane visit
+    constexpr int SMAX = SPL != 1 ? 0 : WEIGHTED ? LS_SPARSE_MAX : LS_SPARSE_UNIT;
 
     using DD = typename DistT<NARROW>::T;
     constexpr DD DD_INF = DistT<NARROW>::INF;
@@ -473,40 +481,45 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                 }
                 const unsigned am = __ballot_sync(FULL, any);
                 bool sparse = false;
-                if constexpr (WEIGHTED && SPL == 1 && !NARROW) {
-                    if (am != 0u && __popc(am) <= LS_SPARSE_MAX) {
+                if constexpr (SPL == 1 && SMAX > 0) {
+                    if (am != 0u && __popc(am) <= SMAX) {
                         // few lanes at D: (arc, active source) pairs over the lanes
                         sparse = true;
                         const SparseLanes L = sparse_lanes(am, lane, s_scr[threadIdx.x >> 5]);
                         const int K = 32 >> L.lg;   // arcs per chunk
-                        int32_t* drow = reinterpret_cast<int32_t*>(d) + L.s;
-                        uint64_t* srow = reinterpret_cast<uint64_t*>(sg) + L.s;
+                        DD* drow = d + L.s;
+                        SG* srow = sg + L.s;
                         const bool pl = D > 0;
                         bool ovf = false, cand = false;
                         uint64_t acc = 0;
                         // v is a parent of u on source i: d(v) + w(v,u) = D (and, for the tables,
                         // v is not a frontier other than the source)
                         auto sp_pull = [&](int32_t v, int32_t dv, int32_t w, uint64_t m) {
-                            if (dv < D && dv + w == D && (v >= nf || dv == 0)) {
+                            const bool tight = WEIGHTED ? dv < D && dv + w == D : dv == D - 1;
+                            if (tight && (v >= nf || dv == 0)) {
                                 const uint64_t t = srow[(uint32_t)v << 5];
-                                acc = MULT ? madd_ck(acc, t, m, ovf) : add_ck(acc, t, ovf);
+                                if constexpr (NARROW)
+                                    acc += t;   // parents' counts < 2^32, fewer than 2^31 parents
+                                else
+                                    acc = MULT ? madd_ck(acc, t, m, ovf) : add_ck(acc, t, ovf);
                             }
                         };
                         // relax u -> v on source i; warp-collective (every lane calls it)
                         auto sp_relax = [&](int32_t v, int32_t dv, int32_t w, bool ok) {
                             const int64_t nd64 = (int64_t)D + w;
-                            const int32_t nd = nd64 < DINF ? (int32_t)nd64 : DINF;
+                            const int32_t nd = !WEIGHTED ? D + 1 : nd64 < DINF ? (int32_t)nd64 : DINF;
                             const bool imp = ok && nd < dv;
-                            cand |= ok && nd <= dv;
+                            if constexpr (LEAVES) cand |= ok && nd <= dv;
                             const unsigned im = __ballot_sync(FULL, imp);
                             if (imp) {
-                                atomicMin(drow + ((uint32_t)v << 5), nd);
+                                if constexpr (WEIGHTED) atomicMin(reinterpret_cast<int32_t*>(drow) + ((uint32_t)v << 5), nd);
+                                else drow[(uint32_t)v << 5] = (DD)nd;
                                 // the arc's first improving lane marks the head
                                 if (((im >> (L.j << L.lg)) & ((1u << L.i) - 1u)) == 0u) {
                                     int bk = dmod + w;
                                     if (bk >= P.nb) bk -= P.nb;
                                     mark_head(bm + (int64_t)bk * W.bm_words, v);
-                                    bflag[bk] = 1;
+                                    if constexpr (WEIGHTED) bflag[bk] = 1;
                                 }
                             }
                         };
@@ -516,16 +529,16 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                             for (int c0 = 0; c0 < cur.deg; c0 += 2 * K) {
                                 const int k1 = c0 + L.j, k2 = k1 + K;
                                 const bool ok1 = L.valid && k1 < cur.deg, ok2 = L.valid && k2 < cur.deg;
-                                int32_t v1 = 0, w1 = 0, d1 = DINF, v2 = 0, w2 = 0, d2 = DINF;
+                                int32_t v1 = 0, w1 = 1, d1 = DINF, v2 = 0, w2 = 1, d2 = DINF;
                                 uint64_t m1 = 1, m2 = 1;
                                 if (ok1) {
                                     v1 = __ldg(A.col + cur.a0 + k1);
-                                    w1 = __ldg(A.w + cur.a0 + k1);
+                                    if (WEIGHTED) w1 = __ldg(A.w + cur.a0 + k1);
                                     if (MULT) m1 = __ldg(A.mu + cur.a0 + k1);
                                 }
                                 if (ok2) {
                                     v2 = __ldg(A.col + cur.a0 + k2);
-                                    w2 = __ldg(A.w + cur.a0 + k2);
+                                    if (WEIGHTED) w2 = __ldg(A.w + cur.a0 + k2);
                                     if (MULT) m2 = __ldg(A.mu + cur.a0 + k2);
                                 }
                                 if (ok1) d1 = drow[(uint32_t)v1 << 5];
@@ -548,16 +561,16 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                             for (int c0 = 0; c0 < span; c0 += K) {
                                 const int k = c0 + L.j;
                                 const bool okp = L.valid && k < ideg, ok = L.valid && k < cur.deg;
-                                int32_t pv = 0, pw = 0, pd = DINF, v = 0, w = 0, dv = DINF;
+                                int32_t pv = 0, pw = 1, pd = DINF, v = 0, w = 1, dv = DINF;
                                 uint64_t pm = 1;
                                 if (okp) {
                                     pv = __ldg(A.icol + i0 + k);
-                                    pw = __ldg(A.iw + i0 + k);
+                                    if (WEIGHTED) pw = __ldg(A.iw + i0 + k);
                                     if (MULT) pm = __ldg(A.imu + i0 + k);
                                 }
                                 if (ok) {
                                     v = __ldg(A.col + cur.a0 + k);
-                                    w = __ldg(A.w + cur.a0 + k);
+                                    if (WEIGHTED) w = __ldg(A.w + cur.a0 + k);
                                 }
                                 if (okp) pd = drow[(uint32_t)pv << 5];
                                 if (ok) dv = drow[(uint32_t)v << 5];
@@ -571,14 +584,23 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                                 if (o >= (1 << L.lg)) acc = add_ck(acc, shfl_xor_u64(acc, o), ovf);
                         }
                         const bool head = L.valid && L.j == 0;
-                        if ((P.mode == LS_BRANDES || P.mode == LS_SKEL) && !__any_sync(FULL, cand)) {
-                            const bool tgt = P.in_s ? P.in_s[base + u] != 0 : true;
-                            if (head)
-                                dlt[((uint32_t)u << 5) + L.s] = tgt ? recip_count((DT)(pl ? acc : 1ull)) : (DT)0;
-                            if (lane == 0) order[e].deg = cur.deg | INT32_MIN;
+                        if constexpr (LEAVES) {
+                            if ((P.mode == LS_BRANDES || P.mode == LS_SKEL) && !__any_sync(FULL, cand)) {
+                                const bool tgt = P.in_s ? P.in_s[base + u] != 0 : true;
+                                if (head)
+                                    dlt[((uint32_t)u << 5) + L.s] = tgt ? recip_count((DT)(pl ? acc : 1ull)) : (DT)0;
+                                if (lane == 0) order[e].deg = cur.deg | INT32_MIN;
+                            }
                         }
-                        if (pl && head) srow[(uint32_t)u << 5] = acc;
+                        if (pl && head) srow[(uint32_t)u << 5] = (SG)acc;
                         if (__any_sync(FULL, ovf) && lane == 0) atomicOr(&P.flags[FLAG_SIGMA_OVF], 1u);
+                        if constexpr (NARROW) {
+                            // a count past 32 bits: abort the batch, the call reruns with 64-bit rows
+                            if (__any_sync(FULL, pl && head && (acc >> 32) != 0) && lane == 0) {
+                                atomicOr(&P.flags[FLAG_DEPTH], 1u);
+                                atomicExch(&ctl->err, 1);
+                            }
+                        }
                     }
                 }
                 if (am != 0u && !sparse) {
@@ -757,34 +779,37 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                     }
                     const unsigned am = __ballot_sync(FULL, any);
                     bool sparse = false;
-                    if constexpr (WEIGHTED && SPL == 1 && !NARROW) {
-                        if (am != 0u && __popc(am) <= LS_SPARSE_MAX) {
+                    if constexpr (SPL == 1 && SMAX > 0) {
+                        if (am != 0u && __popc(am) <= SMAX) {
                             // few lanes at D: (arc, active source) pairs over the lanes
                             sparse = true;
                             const SparseLanes L = sparse_lanes(am, lane, s_scr[threadIdx.x >> 5]);
                             const int K = 32 >> L.lg;
-                            const int32_t* drow = reinterpret_cast<const int32_t*>(d) + L.s;
+                            const DD* drow = d + L.s;
                             DT* crow = dlt + L.s;
                             DT acc = (DT)0;
                             // successors v of u on source i: d(v) = D + w(u,v)
+                            auto succ = [&](int32_t dv, int32_t w) {
+                                return WEIGHTED ? dv != DINF && (int64_t)dv == (int64_t)D + w : dv == D + 1;
+                            };
                             // two arcs per lane and iteration (overlapping load chains)
                             for (int k1 = L.j; L.valid && k1 < cur.deg; k1 += 2 * K) {
                                 const int k2 = k1 + K;
                                 const bool two = k2 < cur.deg;
                                 const int32_t v1 = __ldg(A.col + cur.a0 + k1);
-                                const int32_t w1 = __ldg(A.w + cur.a0 + k1);
-                                int32_t v2 = 0, w2 = 0;
+                                const int32_t w1 = WEIGHTED ? __ldg(A.w + cur.a0 + k1) : 1;
+                                int32_t v2 = 0, w2 = 1;
                                 if (two) {
                                     v2 = __ldg(A.col + cur.a0 + k2);
-                                    w2 = __ldg(A.w + cur.a0 + k2);
+                                    if (WEIGHTED) w2 = __ldg(A.w + cur.a0 + k2);
                                 }
                                 const int32_t d1 = drow[(uint32_t)v1 << 5];
-                                const int32_t d2 = two ? drow[(uint32_t)v2 << 5] : DINF;
-                                if (d1 != DINF && (int64_t)d1 == (int64_t)D + w1) {
+                                const int32_t d2 = two ? (int32_t)drow[(uint32_t)v2 << 5] : DINF;
+                                if (succ(d1, w1)) {
                                     const DT cv = crow[(uint32_t)v1 << 5];
                                     acc += MULT ? (DT)__ldg(A.mu + cur.a0 + k1) * cv : cv;
                                 }
-                                if (d2 != DINF && (int64_t)d2 == (int64_t)D + w2) {
+                                if (two && succ(d2, w2)) {
                                     const DT cv = crow[(uint32_t)v2 << 5];
                                     acc += MULT ? (DT)__ldg(A.mu + cur.a0 + k2) * cv : cv;
                                 }
@@ -793,7 +818,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                             for (int o = 1; o < 32; o <<= 1)
                                 if (o >= (1 << L.lg)) acc += __shfl_xor_sync(FULL, acc, o);
                             if (L.valid && L.j == 0) {
-                                const DT sd = (DT)reinterpret_cast<const uint64_t*>(sg)[((uint32_t)u << 5) + L.s];
+                                const DT sd = (DT)sg[((uint32_t)u << 5) + L.s];
                                 const DT delta = sd * acc;
                                 const bool is_t = P.in_s ? P.in_s[base + u] != 0 : true;
                                 const int64_t ix = P.bc_map ? (int64_t)P.bc_map[base + u] : base + u;
