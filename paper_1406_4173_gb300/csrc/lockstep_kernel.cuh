@@ -205,7 +205,7 @@ __device__ __forceinline__ bool row_has(const uint8_t*, int32_t) { return true; 
 #define BCPP_LS_SPARSE_MAX 16
 #endif
 #ifndef BCPP_LS_SPARSE_UNIT
-#define BCPP_LS_SPARSE_UNIT 16
+#define BCPP_LS_SPARSE_UNIT 32
 #endif
 // most active lanes an entry takes the sparse visit with: integer weights, unit weights
 constexpr int LS_SPARSE_MAX = BCPP_LS_SPARSE_MAX;

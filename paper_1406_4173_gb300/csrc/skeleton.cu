@@ -268,6 +268,16 @@ constexpr int CT_WARPS = 16;    // warps per block: 64 nodes = one unit
 constexpr int FT = 32;          // frontiers per tile
 constexpr uint32_t CT_NONE = 0xffffffffu;   // "unreachable" after the min-plus sweep (no sum equals it)
 
+// four or two packed half2 values, read from shared memory with one vector load
+union H2x4 {
+    uint4 u;
+    __half2 h[4];
+};
+union H2x2 {
+    uint2 u;
+    __half2 h[2];
+};
+
 __device__ __forceinline__ __half ct_h(uint32_t x) {
     return x >= (uint32_t)DINF ? __ushort_as_half((unsigned short)0x7c00) : __uint2half_rn(x);
 }
@@ -284,6 +294,11 @@ centrality_tiled_kernel(const CentralityUnit* __restrict__ units, SkTables T, co
     __shared__ uint32_t s_d[FT][32];
     __shared__ __half2 s_h[FT][32];       // 16-bit path: the frontier distance in both halves
     __shared__ uint64_t s_x[FT][32];      // sigma rows (forward) or c rows (backward, as DT bits)
+    // 16-bit path: each warp's table tile, read with one broadcast load per frontier instead of a
+    // shuffle per node pair: distances s_t[warp][f][q] (node pair q), counts s_c[warp][j][f]
+    // (uint64 path counts forward, converted to DT backward)
+    __shared__ __align__(16) __half2 s_t[CT_WARPS][FT][CT_NP];
+    __shared__ __align__(16) uint64_t s_c[CT_WARPS][CTV][FT];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const CentralityUnit U = units[slot_major ? blockIdx.y : blockIdx.x];
     const int slot = slot_major ? blockIdx.x : blockIdx.y;
@@ -305,9 +320,9 @@ centrality_tiled_kernel(const CentralityUnit* __restrict__ units, SkTables T, co
     for (int j = 0; j < CTV; j++) dv[j] = CT_NONE;
     bool use16 = h16 != 0;
     if (use16) {
-        __half2 dv2[CT_NP];
+        __half2 dv2[CT_NP], dv2b[CT_NP];
 #pragma unroll
-        for (int q = 0; q < CT_NP; q++) dv2[q] = __half2half2(ct_h(DINF));
+        for (int q = 0; q < CT_NP; q++) dv2[q] = dv2b[q] = __half2half2(ct_h(DINF));
         bool big = false;
         for (int32_t f0 = 0; f0 < nfi; f0 += FT) {
             const int nt = min(FT, nfi - f0);
@@ -317,20 +332,30 @@ centrality_tiled_kernel(const CentralityUnit* __restrict__ units, SkTables T, co
                 big |= v != (uint32_t)DINF && v > CT_H16_MAX;
                 s_h[x >> 5][x & 31] = __half2half2(ct_h(v));
             }
-            __half2 th[CT_NP];
 #pragma unroll
             for (int q = 0; q < CT_NP; q++)
-                th[q] = __halves2half2(ct_h(td_at(T.td, 2 * q, f0, nt)), ct_h(td_at(T.td, 2 * q + 1, f0, nt)));
+                s_t[warp][lane][q] = __halves2half2(ct_h(td_at(T.td, 2 * q, f0, nt)), ct_h(td_at(T.td, 2 * q + 1, f0, nt)));
             __syncthreads();
-            for (int f = 0; f < nt; f++) {
-                const __half2 dh = s_h[f][lane];
+            // two frontiers per iteration into two running minima (independent chains)
+            int f = 0;
+            for (; f + 1 < nt; f += 2) {
+                const __half2 dha = s_h[f][lane], dhb = s_h[f + 1][lane];
+                H2x4 tt;
+                tt.u = *reinterpret_cast<const uint4*>(&s_t[warp][f][0]);
 #pragma unroll
                 for (int q = 0; q < CT_NP; q++) {
-                    const __half2 t = __shfl_sync(FULL, th[q], f);
-                    dv2[q] = __hmin2(dv2[q], __hadd2(dh, t));
+                    dv2[q] = __hmin2(dv2[q], __hadd2(dha, tt.h[q]));
+                    dv2b[q] = __hmin2(dv2b[q], __hadd2(dhb, tt.h[CT_NP + q]));
                 }
             }
+            if (f < nt) {
+                const __half2 dh = s_h[f][lane];
+#pragma unroll
+                for (int q = 0; q < CT_NP; q++) dv2[q] = __hmin2(dv2[q], __hadd2(dh, s_t[warp][f][q]));
+            }
         }
+#pragma unroll
+        for (int q = 0; q < CT_NP; q++) dv2[q] = __hmin2(dv2[q], dv2b[q]);
         use16 = !__syncthreads_or(big);
         if (use16) {
 #pragma unroll
@@ -393,27 +418,31 @@ centrality_tiled_kernel(const CentralityUnit* __restrict__ units, SkTables T, co
                 tdv[j] = td_at(T.td, j, f0, nt);
                 tsv[j] = tdv[j] != (uint32_t)DINF ? T.ts[t0 + (int64_t)(vb + j) * nfi + f0 + lane] : 0ull;
             }
+            if (use16) {
+#pragma unroll
+                for (int q = 0; q < CT_NP; q++) s_t[warp][lane][q] = __halves2half2(ct_h(tdv[2 * q]), ct_h(tdv[2 * q + 1]));
+#pragma unroll
+                for (int j = 0; j < CTV; j++) s_c[warp][j][lane] = tsv[j];
+            }
             __syncthreads();
             if (use16) {
-                __half2 th[CT_NP];
-#pragma unroll
-                for (int q = 0; q < CT_NP; q++) th[q] = __halves2half2(ct_h(tdv[2 * q]), ct_h(tdv[2 * q + 1]));
                 for (int f = 0; f < nt; f++) {
                     const __half2 dh = s_h[f][lane];
+                    H2x2 tt;
+                    tt.u = *reinterpret_cast<const uint2*>(&s_t[warp][f][0]);
+                    unsigned m[CT_NP], any = 0u;
 #pragma unroll
                     for (int q = 0; q < CT_NP; q++) {
-                        const __half2 t = __shfl_sync(FULL, th[q], f);
-                        const unsigned m = __heq2_mask(__hadd2(dh, t), dvh[q]);
-                        if (__any_sync(FULL, m != 0u)) {
+                        m[q] = __heq2_mask(__hadd2(dh, tt.h[q]), dvh[q]);
+                        any |= m[q];
+                    }
+                    if (__any_sync(FULL, any != 0u)) {
+                        // lanes take their own tight nodes (no shuffles below: the counts are in
+                        // shared memory)
+                        const uint64_t xs = s_x[f][lane];
 #pragma unroll
-                            for (int h = 0; h < 2; h++) {
-                                const bool tight = ((m >> (16 * h)) & 0xffffu) != 0u;
-                                if (__any_sync(FULL, tight)) {
-                                    const uint64_t tsj = shfl_u64(tsv[2 * q + h], f);
-                                    if (tight) sv[2 * q + h] = madd_ck(sv[2 * q + h], s_x[f][lane], tsj, ovf);
-                                }
-                            }
-                        }
+                        for (int j = 0; j < CTV; j++)
+                            if ((m[j >> 1] >> (16 * (j & 1))) & 0xffffu) sv[j] = madd_ck(sv[j], xs, s_c[warp][j][f], ovf);
                     }
                 }
             } else {
@@ -468,32 +497,33 @@ centrality_tiled_kernel(const CentralityUnit* __restrict__ units, SkTables T, co
                 tdv[j] = td_at(T.tdr, j, f0, nt);
                 tsv[j] = tdv[j] != (uint32_t)DINF ? T.tsr[t0 + (int64_t)(vb + j) * nfi + f0 + lane] : 0ull;
             }
+            if (use16) {
+#pragma unroll
+                for (int q = 0; q < CT_NP; q++) s_t[warp][lane][q] = __halves2half2(ct_h(tdv[2 * q]), ct_h(tdv[2 * q + 1]));
+                DT* cd = reinterpret_cast<DT*>(&s_c[warp][0][0]);   // [j][f] as DT
+#pragma unroll
+                for (int j = 0; j < CTV; j++) cd[j * FT + lane] = (DT)tsv[j];
+            }
             __syncthreads();
             if (use16) {
-                __half2 th[CT_NP];
-#pragma unroll
-                for (int q = 0; q < CT_NP; q++) th[q] = __halves2half2(ct_h(tdv[2 * q]), ct_h(tdv[2 * q + 1]));
+                const DT* cd = reinterpret_cast<const DT*>(&s_c[warp][0][0]);
                 for (int f = 0; f < nt; f++) {
                     const __half2 dh = s_h[f][lane];
+                    H2x2 tt;
+                    tt.u = *reinterpret_cast<const uint2*>(&s_t[warp][f][0]);
+                    unsigned m[CT_NP], any = 0u;
 #pragma unroll
                     for (int q = 0; q < CT_NP; q++) {
-                        const __half2 t = __shfl_sync(FULL, th[q], f);
-                        const unsigned m = __heq2_mask(__hadd2(lvh[q], t), dh);
-                        if (__any_sync(FULL, m != 0u)) {
+                        m[q] = __heq2_mask(__hadd2(lvh[q], tt.h[q]), dh);
+                        any |= m[q];
+                    }
+                    if (__any_sync(FULL, any != 0u)) {
+                        DT cf;
+                        const uint64_t bits = s_x[f][lane];
+                        memcpy(&cf, &bits, sizeof(DT));
 #pragma unroll
-                            for (int h = 0; h < 2; h++) {
-                                const bool on = ((m >> (16 * h)) & 0xffffu) != 0u;
-                                if (__any_sync(FULL, on)) {
-                                    const uint64_t tsj = shfl_u64(tsv[2 * q + h], f);
-                                    if (on) {
-                                        DT cf;
-                                        const uint64_t bits = s_x[f][lane];
-                                        memcpy(&cf, &bits, sizeof(DT));
-                                        acc[2 * q + h] += (DT)tsj * cf;
-                                    }
-                                }
-                            }
-                        }
+                        for (int j = 0; j < CTV; j++)
+                            if ((m[j >> 1] >> (16 * (j & 1))) & 0xffffu) acc[j] += cd[j * FT + f] * cf;
                     }
                 }
             } else {
