@@ -389,6 +389,31 @@ int choose_cluster(const bcpp_ctx* c, int nitems, const bcpp_opts& o) {
     return 1;
 }
 
+// Batches in flight at most: resident CTAs / CTAs per batch.
+int64_t slot_capacity(const bcpp_ctx* c, const bcpp_opts& o, int cl) {
+    const int cps = o.ctas_per_sm > 0 ? o.ctas_per_sm : LS_MIN_CTAS;
+    return std::max<int64_t>(1, (int64_t)cps * c->num_sms / cl);
+}
+
+// Source-batch width when 32-source batches would leave slots idle: a call with fewer batches
+// than slots (one round) spreads its sources over all of them, since a batch costs about in
+// proportion to its active lanes (entries with few active lanes are visited by (arc, source)
+// pairs) and otherwise the idle slots' SMs wait.  Measured on one box: 200 sources on 76 slots
+// (`planted_200k` plain) 107 -> 46 ms, 512 sources 34 -> 22 ms, 2,000 sources 198 -> 179 ms.
+// Not for two or more rounds: 4,096 sources as 152 batches of 27 instead of 128 of 32 on 76
+// slots was slower (724 -> 933 ms; narrower batches of well-ordered sources save little per
+// batch, and both rounds then run full).
+#ifndef BCPP_BALANCE_MAX_ROUNDS
+#define BCPP_BALANCE_MAX_ROUNDS 1
+#endif
+int balanced_width(int64_t ns, int64_t slots_cap, int lanes) {
+    if (ns <= 0 || slots_cap <= 0) return lanes;
+    const int64_t rounds = (ns + (int64_t)lanes * slots_cap - 1) / ((int64_t)lanes * slots_cap);
+    if (rounds > BCPP_BALANCE_MAX_ROUNDS) return lanes;
+    const int64_t b = (ns + rounds * slots_cap - 1) / (rounds * slots_cap);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(lanes, b));
+}
+
 // Choose how many slots (batches in flight, cl CTAs each) to run, within the memory budget.
 int choose_slots(bcpp_ctx* c, int nitems, int ctas_per_sm, int64_t per_slot, int64_t per_slot_bc, int cl = 1) {
     int cps = ctas_per_sm > 0 ? ctas_per_sm : LS_MIN_CTAS;
@@ -902,6 +927,11 @@ int plain_prepare(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS
     shard_sources(o, r.ns, s0, s1);
     r.spl = choose_spl(c, s1 - s0, o);
     std::vector<LsItem> hitems = make_items(0, s0, s1, 32 * r.spl);
+    r.cl = r.spl == 1 ? choose_cluster(c, (int)hitems.size(), o) : 1;
+    if (r.spl == 1) {
+        const int b = balanced_width(s1 - s0, slot_capacity(c, o, r.cl), 32);
+        if (b < 32) hitems = make_items(0, s0, s1, b);
+    }
     r.nitems = (int)hitems.size();
     if (r.nitems <= 0) return BCPP_OK;
     CK_ALLOC(r.items.alloc(c, r.nitems));
@@ -910,7 +940,6 @@ int plain_prepare(bcpp_ctx* c, const bcpp_graph* g, const int32_t* S, int32_t nS
     const int64_t hoff[2] = {0, n};
     CK_RC(to_dev(c, r.node_off.p, hoff, 2));
     r.nb = g->w ? (int)r.wmax + 1 : 2;
-    r.cl = r.spl == 1 ? choose_cluster(c, r.nitems, o) : 1;
     const int ef = entry_factor(c, g->w != nullptr, r.spl);
     r.slots = choose_slots(c, r.nitems, o.ctas_per_sm, slot_bytes(n, r.nb, fp32, ef, r.spl), (int64_t)n * 24, r.cl);
     CK_RC(alloc_slots(c, r.ws, r.slots, n, r.nb, fp32, n, r.spl, ef, false));
@@ -1310,8 +1339,13 @@ int pp_prepare(bcpp_ctx* c, const bcpp_graph* g, uint64_t wmax, const InCsr* Tin
     // without non-frontier nodes Brandes_SK runs alone and may use 64-source batches
     r.spl = r.hunits.empty() ? choose_spl(c, s1 - s0, o) : 1;
     std::vector<LsItem> hitems = make_items(0, s0, s1, 32 * r.spl);
+    r.cl = (!hitems.empty() && r.spl == 1) ? choose_cluster(c, (int)hitems.size(), o) : 1;
+    if (r.spl == 1 && r.hunits.empty()) {
+        // without a Centrality step (whose cost grows with the batch count, not their width)
+        const int b = balanced_width(s1 - s0, slot_capacity(c, o, r.cl), 32);
+        if (b < 32) hitems = make_items(0, s0, s1, b);
+    }
     r.nitems = (int)hitems.size();
-    r.cl = (r.nitems > 0 && r.spl == 1) ? choose_cluster(c, r.nitems, o) : 1;
     const int ef = entry_factor(c, !r.unit, r.spl);
     r.slots = r.nitems > 0 ? choose_slots(c, r.nitems, o.ctas_per_sm,
                                           slot_bytes(std::max(N, 1), r.nb, fp32, ef, r.spl), (int64_t)n * 24, r.cl)
