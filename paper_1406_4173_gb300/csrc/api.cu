@@ -1292,6 +1292,7 @@ struct PpRun {
     DBuf<int64_t> irp, icnt, itmp;
     DBuf<int32_t> icol, iw;
     DBuf<uint64_t> imu;
+    DBuf<double> mud;   // skeleton multiplicities as the dependency type (float in the first half in FP32-delta)
     DBuf<int64_t> node_off;
     DBuf<CentralityUnit> units;
     DBuf<LsItem> items;
@@ -1394,6 +1395,12 @@ int pp_prepare(bcpp_ctx* c, const bcpp_graph* g, uint64_t wmax, const InCsr* Tin
         A.rp = K.skrp.p; A.col = K.skcol.p;
         A.w = r.unit ? nullptr : K.skw.p;
         A.mu = r.mult ? K.skmu.p : nullptr;
+        if (r.mult) {
+            CK_ALLOC(r.mud.alloc(c, K.arcs));
+            convert_mult(K.skmu.p, K.arcs, r.o.precision == BCPP_FP32_DELTA, r.mud.p, c->stream);
+            c->launches++;
+            A.mud = r.mud.p;
+        }
         if (g->directed) {
             A.irp = r.irp.p; A.icol = r.icol.p; A.iw = r.unit ? nullptr : r.iw.p; A.imu = r.mult ? r.imu.p : nullptr;
         } else {

@@ -58,6 +58,8 @@ void ls_launch(bool fp32_delta, bool fused, const LsArena& A, const LsParams& P,
     const bool mult = A.mu != nullptr;
     const bool weighted = A.w != nullptr;
     if (mult && !weighted) return;
+    // the backward pass reads the multiplicities in the dependency type
+    if (mult && !A.mud && (P.mode == LS_BRANDES || P.mode == LS_SKEL)) return;
     if (spl == 2 && P.mode != LS_BRANDES) return;   // 64-source rows: Brandes passes only
     if (cl != 1 && cl != 2 && cl != 4) return;
     narrow = narrow && !weighted && P.mode == LS_BRANDES;
@@ -70,6 +72,19 @@ void ls_launch(bool fp32_delta, bool fused, const LsArena& A, const LsParams& P,
 // entries, whose dependent loads of the order list leave the GPU latency-bound.
 void ls_reset_launch(const LsSlots& W, int slots, cudaStream_t st) {
     if (slots > 0) fill_i32(W.d, DINF, (int64_t)slots * W.cap_n * LS_LANES, st);
+}
+
+template <typename T>
+__global__ void convert_mult_kernel(const uint64_t* __restrict__ mu, int64_t m, T* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (T)mu[i];
+}
+
+void convert_mult(const uint64_t* mu, int64_t m, bool fp32, void* out, cudaStream_t st) {
+    if (m <= 0) return;
+    const int64_t blocks = std::min<int64_t>((m + 255) / 256, 152 * 16);
+    if (fp32) convert_mult_kernel<float><<<(unsigned)blocks, 256, 0, st>>>(mu, m, (float*)out);
+    else convert_mult_kernel<double><<<(unsigned)blocks, 256, 0, st>>>(mu, m, (double*)out);
 }
 
 void fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t st) {

@@ -42,6 +42,7 @@ struct LsArena {
     const int32_t* iw;
     const uint64_t* imu;
     const int64_t* node_off;
+    const void* mud;         // mu converted to the dependency type (the backward pass's products); nullptr = none
 };
 
 struct LsItem {
@@ -116,5 +117,7 @@ void ls_reset_launch(const LsSlots& W, int slots, cudaStream_t st);
 
 // Fill helpers
 void fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t st);
+// out[i] = (double or float) mu[i], i < m
+void convert_mult(const uint64_t* mu, int64_t m, bool fp32, void* out, cudaStream_t st);
 
 }  // namespace bcpp

@@ -150,11 +150,12 @@ __device__ __forceinline__ void arc_group(int32_t mv, int32_t mw, MT mm, int j, 
 
 // Visit the arcs [a0, a0 + deg) of one row: 32 heads per coalesced load, then groups of
 // UNROLL arcs, or of UNROLL / 2 when at most that many are left (low-degree rows waste less).
-// MT: the type the multiplicities are handed to f in (uint64_t, or the dependency type, converted
-// once per chunk of 32 arcs instead of once per use).
-template <int UNROLL, int SPL, bool WEIGHTED, bool MULT, typename MT = uint64_t, typename DD, class F>
+// MT: the type the multiplicities are handed to f in (uint64_t, or the dependency type); MP: the
+// type they are stored in (uint64_t, or already the dependency type).
+template <int UNROLL, int SPL, bool WEIGHTED, bool MULT, typename MT = uint64_t, typename MP = uint64_t,
+          typename DD, class F>
 __device__ __forceinline__ void for_arc_groups(const int32_t* __restrict__ col, const int32_t* __restrict__ w,
-                                               const uint64_t* __restrict__ mu, int64_t a0, int32_t deg,
+                                               const MP* __restrict__ mu, int64_t a0, int32_t deg,
                                                const DD* dl0, int lane, F&& f) {
     for (int32_t c0 = 0; c0 < deg; c0 += 32) {
         const int cnt = min(32, deg - c0);
@@ -319,6 +320,8 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
     // dependencies of the current batch (at most 32 * SPL terms per node) are added into bat with
     // atomics; at the end of the batch they move into the slot's compensated sums
     double* bat = W.bc_bat ? W.bc_bat + (int64_t)slot * W.cap_bc : nullptr;
+    // multiplicities in the dependency type for the backward pass (set whenever MULT)
+    const DT* mud = reinterpret_cast<const DT*>(A.mud);
 
     bool first = true;
     for (;;) {
@@ -690,7 +693,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                                 [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t* mk,
                                     const int32_t (*dv)[SPL], int) { pull_group(tag, vv, ww, mk, dv); });
                         }
-                        for_arc_groups<UNROLL, SPL, WEIGHTED, false>(A.col, A.w, nullptr, cur.a0, cur.deg, dl0, lane,
+                        for_arc_groups<UNROLL, SPL, WEIGHTED, false>(A.col, A.w, (const uint64_t*)nullptr, cur.a0, cur.deg, dl0, lane,
                             [&](auto tag, const int32_t* vv, const int32_t* ww, const uint64_t*,
                                 const int32_t (*dv)[SPL], int left) { relax_group(tag, vv, ww, dv, left); });
                     }
@@ -807,11 +810,11 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                                 const int32_t d2 = two ? (int32_t)drow[(uint32_t)v2 << 5] : DINF;
                                 if (succ(d1, w1)) {
                                     const DT cv = crow[(uint32_t)v1 << 5];
-                                    acc += MULT ? (DT)__ldg(A.mu + cur.a0 + k1) * cv : cv;
+                                    acc += MULT ? __ldg(mud + cur.a0 + k1) * cv : cv;
                                 }
                                 if (two && succ(d2, w2)) {
                                     const DT cv = crow[(uint32_t)v2 << 5];
-                                    acc += MULT ? (DT)__ldg(A.mu + cur.a0 + k2) * cv : cv;
+                                    acc += MULT ? __ldg(mud + cur.a0 + k2) * cv : cv;
                                 }
                             }
 #pragma unroll
@@ -835,7 +838,7 @@ ls_kernel(const LsArena A, const LsParams P, const LsSlots W, const LsItem* __re
                         DT acc[SPL];
 #pragma unroll
                         for (int s = 0; s < SPL; s++) acc[s] = (DT)0;
-                        for_arc_groups<UNROLL, SPL, WEIGHTED, MULT, DT>(A.col, A.w, A.mu, cur.a0, cur.deg, dl0, lane,
+                        for_arc_groups<UNROLL, SPL, WEIGHTED, MULT, DT>(A.col, A.w, mud, cur.a0, cur.deg, dl0, lane,
                             [&](auto tag, const int32_t* vv, const int32_t* ww, const DT* mk,
                                 const int32_t (*dv)[SPL], int) {
                                 constexpr int U = decltype(tag)::value;
