@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_model_bytes_chunglu_50k():
-    """The per-source traffic model on the default workload (n = 50,000, A = 500,000 arcs, 133,029
+    """The per-source traffic model on `chunglu_50k` (n = 50,000, A = 500,000 arcs, 133,029
     tight arcs per source on average): 8.743 MB per source with FP64 dependencies, 8.011 MB with
     FP32, 437.1 GB for the 50,000 sources of one launch."""
     n, A, D = 50_000, 500_000, 133_029.0625
@@ -74,6 +74,42 @@ def test_committed_traffic_records_are_well_formed():
         if f.endswith(".json"):
             rec = json.load(open(os.path.join(pdir, f)))
             assert len(rec["kernel_source_hash"]) == 16 and float(rec["dram_bytes_per_launch"]) > 0, f
+
+
+def _fake_smi(tmp_path, lines, period=0.05):
+    """An nvidia-smi stand-in on PATH that prints the given CSV lines in a loop."""
+    script = tmp_path / "nvidia-smi"
+    body = "".join(f'  echo "{l}"; sleep {period}\n' for l in lines)
+    script.write_text("#!/bin/bash\nwhile true; do\n" + body + "done\n")
+    script.chmod(0o755)
+    return str(tmp_path)
+
+
+def test_clock_sampler_waits_for_first_sample(monkeypatch, tmp_path):
+    """The sampler starts nvidia-smi and returns only after its first sample (its start-up must
+    not overlap the timed steps); the median SM clock and the active throttle reasons are read
+    from the samples taken after that."""
+    ok = "0, 2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active"
+    capped = "0, 1980, 2070, 1400.0, 0x4, Not Active, Not Active, Not Active, Active"
+    monkeypatch.setenv("PATH", _fake_smi(tmp_path, [ok, capped, ok]) + os.pathsep + os.environ["PATH"])
+    c = bench.Clocks(0)
+    c.start()
+    assert c.first >= 1 and len(c.lines) >= 1
+    import time
+    time.sleep(0.4)
+    r = c.stop()
+    assert r["sm_max_mhz"] == 2070.0
+    assert r["sm_mhz"] in (2070.0, 1980.0)
+    assert r["reasons"] == ["sw_power_cap"]
+    assert r["samples"] >= 2
+
+
+def test_clock_sampler_without_nvidia_smi(monkeypatch, tmp_path):
+    """No nvidia-smi on PATH: no clock record, and no error."""
+    monkeypatch.setenv("PATH", str(tmp_path))
+    c = bench.Clocks(0)
+    c.start()
+    assert c.stop() is None
 
 
 def test_kernel_source_hash_is_stable():
