@@ -112,6 +112,20 @@ def test_clock_sampler_without_nvidia_smi(monkeypatch, tmp_path):
     assert c.stop() is None
 
 
+def test_batch_oracle_sample_on_all_cores():
+    """The batch workload's CPU baseline: a spawned pool over the graphs in order gives the same
+    per-graph results as the oracle called directly, and reports the host's core count."""
+    import numpy as np
+    import oracle
+    from paper_1406_4173_gb300 import gen
+    graphs = [gen.erdos_renyi(40 + 7 * i, 0.1, seed=i) for i in range(12)]
+    refs, done, rate, cores = bench.batch_oracle_sample(graphs, seconds=0.0, chunk=2)
+    assert cores == (os.cpu_count() or 1)
+    assert done == min(len(graphs), 2 * cores) and rate > 0
+    for gi, r in zip(graphs[:done], refs):
+        np.testing.assert_array_equal(r, oracle.brandes(gi)[0])
+
+
 def test_kernel_source_hash_is_stable():
     h = bench.kernel_source_hash()
     assert len(h) == 16 and int(h, 16) >= 0
